@@ -1,0 +1,152 @@
+/*
+ * swepi.h -- C ABI of libswepi.so: the GB300 (sm_103a) hot path of the
+ * high-order shallow-water method of Gaudreault, Charron, Dallerit and Tokman
+ * (arXiv 2101.05617): complex-step Jacobian-vector products of the direct-flux-
+ * reconstruction (DFR) right-hand side on the rotated cubed sphere, taken at
+ * every Krylov iteration of the phi-function solver inside every multistep
+ * exponential propagation iterative (EPI) step.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * State layout ("canonical"): FP64, contiguous, index
+ *     [var][panel][e2][e1][k2][k1]
+ * var 0 = sqrt(g) H, var i = sqrt(g) H u^i (i = 1, 2): the tensor density q^mu
+ * of App. D (Eq. 136) in the angular cubed-sphere coordinates x^i in
+ * [-pi/4, pi/4] of Eq. (1)-(2); panel 0..5, elements e1, e2 in 0..n_e-1,
+ * Gauss-Legendre points k1, k2 in 0..p (N_s = p + 1 per direction, Sec. 3.1).
+ * n = 3 * 6 * n_e^2 * N_s^2 unknowns.
+ *
+ * Memory: every vector argument named *_dev is a device pointer owned by the
+ * caller (e.g. a torch tensor), 8-byte aligned, at least n doubles; the library
+ * never frees caller memory.  Host pointers are named *_host.  The library owns
+ * its workspace (metric tables, Krylov basis, Hessenberg matrix, EPI history),
+ * allocated in sw_init / on first use and released by sw_free.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  Calls enqueue their kernels on it and return; results are valid
+ * after the stream is synchronised.  Calls that return statistics (kiops,
+ * epi) synchronise the stream internally because the adaptive controller reads
+ * small device scalars between Krylov batches.
+ *
+ * Errors: every int-returning call returns SW_OK (0) or a negative status;
+ * no exception crosses the ABI; sw_status_str() names the status.  A context
+ * is used by one host thread at a time.
+ */
+#ifndef SWEPI_H
+#define SWEPI_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SW_OK 0
+#define SW_EINVAL (-1)      /* bad argument: size, pointer, order, option */
+#define SW_ENOMEM (-2)      /* device or host allocation failed */
+#define SW_ECUDA (-3)       /* a CUDA runtime call or kernel launch failed */
+#define SW_EKRYLOV (-4)     /* phi-function solver hit its substep/rejection cap */
+#define SW_ETIMEOUT (-5)    /* a bounded device-side wait gave up */
+#define SW_ENONFINITE (-6)  /* NaN/Inf met where a finite value is required */
+
+typedef struct sw_ctx* sw_ctx_t;
+
+/* Physical constants and grid rotation (App. B: panel 0 centred at longitude
+ * lambda0, latitude phi0, rotated by alpha0; the other five panels follow the
+ * cube, Eq. 81-95).  precision: 0 = FP64 throughout (the only value accepted). */
+typedef struct {
+  double radius;   /* a, m */
+  double gravity;  /* g_r, m s^-2 (Eq. 51) */
+  double omega;    /* Omega, s^-1 */
+  double lambda0, phi0, alpha0;
+  int precision;
+} sw_params;
+
+/* Options of the adaptive Krylov phi-function solver (Eq. 29).  tol is relative
+ * to the 2-norm of the initial augmented vector; m_* bound the Krylov size;
+ * iop is the incomplete-orthogonalisation window; tau_init <= 0 means "start
+ * with the whole interval". */
+typedef struct {
+  double tol;
+  int m_init, m_min, m_max, iop;
+  double tau_init;
+} sw_kiops_opts;
+
+typedef struct {
+  int substeps, rejects, krylov_iters, m_final;
+  double tau_final, err_last;
+} sw_kiops_stats;
+
+/* Build the grid of 6 x n_e x n_e elements of degree p (N_s = p + 1 points per
+ * direction, Sec. 3.1-3.2): panel frames, Gauss-Legendre points, DFR matrices
+ * (Eq. 8, 13), metric and Christoffel tables at nodes (Eq. 67-80) and at
+ * interface points, the panel connectivity with the App. C transforms.
+ * 1 <= n_e <= 1024, 1 <= p <= 7.  Selects the current CUDA device for the
+ * context.  *out receives the context (NULL on failure). */
+int sw_init(int n_e, int p, const sw_params* params, sw_ctx_t* out);
+
+/* Release the context and all library-owned device memory. NULL is a no-op. */
+void sw_free(sw_ctx_t ctx);
+
+/* n (number of unknowns), nodes per variable, and grid sizes. */
+long long sw_num_unknowns(sw_ctx_t ctx);
+int sw_grid_info(sw_ctx_t ctx, int* n_e, int* p, double* dx);
+
+/* Unit position vectors of the nodes, host array [3][nodes] in canonical node
+ * order (used to evaluate initial fields). */
+int sw_node_xyz(sw_ctx_t ctx, double* xyz_host);
+
+/* State from fields at the nodes (host arrays, canonical node order):
+ * free-surface height h, bottom height hB, Cartesian wind V[3][nodes] (m/s).
+ * Writes q_host[3][nodes] with q^0 = sqrt(g)(h - hB), q^i = q^0 u^i,
+ * u^i = h^{ij} (V . d r / d x^j), and stores hB in the context as by
+ * sw_set_bottom. */
+int sw_state_from_fields(sw_ctx_t ctx, const double* h_host, const double* hB_host,
+                         const double* V_host, double* q_host);
+
+/* Bottom height h_B at the nodes (host array, canonical node order): the
+ * topography source of Eq. (2) uses its element-local collocation gradient. */
+int sw_set_bottom(sw_ctx_t ctx, const double* hB_host);
+
+/* F(q): the DFR right-hand side of Eq. (1)-(2) (Sec. 3, Eq. 14 per direction,
+ * AUSM interface flux of App. D).  q_dev, F_dev: n doubles, may not alias. */
+int sw_rhs(sw_ctx_t ctx, const double* q_dev, double* F_dev, void* stream);
+
+/* Complex-step Jacobian-vector product, Eq. (28): Jv = Im F(q + i eps v) / eps.
+ * eps > 0 (1e-30 is typical).  Jv_dev may not alias q_dev or v_dev. */
+int sw_jvp(sw_ctx_t ctx, const double* q_dev, const double* v_dev, double eps,
+           double* Jv_dev, void* stream);
+
+/* w = sum_{k=0}^{nb-1} tau_out^k phi_k(tau_out dt J(q_lin)) b_k (Eq. 29), J by
+ * the complex-step product above.  b_dev_host: host array of nb device
+ * pointers (1 <= nb <= 8); a NULL entry means a zero vector.  w_dev: n
+ * doubles, may alias none of the inputs.  opts NULL = defaults (tol 1e-10,
+ * m 10/10/128, iop 2).  st may be NULL.  Synchronises `stream`. */
+int sw_kiops_phi(sw_ctx_t ctx, const double* q_lin_dev, double dt, double tau_out, int nb,
+                 const double* const* b_dev_host, const sw_kiops_opts* opts, double* w_dev,
+                 sw_kiops_stats* st, void* stream);
+
+/* One multistep EPI step of order 2..6 (Eq. 25, 30, 34-38) advancing q_dev in
+ * place by dt.  The context keeps the history (q_{n-i}, F(q_{n-i})); while it
+ * holds fewer than P entries the step is taken by 8 EPI2 substeps of dt/8
+ * (Sec. 4 start-up).  The KIOPS size warm-starts from the previous call.
+ * st (may be NULL) accumulates the step's KIOPS statistics.  Synchronises. */
+int sw_epi_step(sw_ctx_t ctx, int order, double dt, double* q_dev, const sw_kiops_opts* opts,
+                sw_kiops_stats* st, void* stream);
+
+/* Seed history entry i (1 = most recent) with (q_{n-i}, F(q_{n-i})) device
+ * vectors (copied); F_dev NULL computes it.  i <= 4. */
+int sw_epi_set_history(sw_ctx_t ctx, int i, const double* q_dev, const double* F_dev, void* stream);
+
+/* Forget the EPI history and the KIOPS warm start. */
+int sw_epi_reset(sw_ctx_t ctx);
+
+/* Number of kernels the library launched since the context was created. */
+long long sw_kernel_launches(sw_ctx_t ctx);
+
+/* Human-readable name of a status code (static storage). */
+const char* sw_status_str(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWEPI_H */

@@ -1,0 +1,319 @@
+// C ABI of libswepi (declared in include/swepi.h): argument checking, context
+// life cycle and the multistep EPI driver (Eq. 25, 30, 34-38).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "swepi_internal.h"
+
+using namespace swepi;
+
+struct sw_ctx : public Ctx {};
+
+namespace {
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// EPI coefficient matrices: rows phi_1..phi_M, columns q_{n-1}..q_{n-P}
+// (Eq. 30 for order 3, Eq. 36-38 for orders 4-6).
+struct Coefs {
+  int M, P;
+  double a[4][4];
+};
+const Coefs kEpi3 = {2, 1, {{0.0}, {2.0 / 3.0}}};
+const Coefs kEpi4 = {3, 2, {{0.0, 0.0}, {-3.0 / 10.0, 3.0 / 40.0}, {32.0 / 5.0, -11.0 / 10.0}}};
+const Coefs kEpi5 = {4, 3,
+                     {{0.0, 0.0, 0.0}, {-4.0 / 5.0, 2.0 / 5.0, -4.0 / 45.0}, {12.0, -9.0 / 2.0, 8.0 / 9.0},
+                      {3.0, 0.0, -1.0 / 3.0}}};
+const Coefs kEpi6 = {4, 4,
+                     {{0.0, 0.0, 0.0, 0.0},
+                      {-49.0 / 60.0, 351.0 / 560.0, -359.0 / 1260.0, 367.0 / 6720.0},
+                      {92.0 / 7.0, -99.0 / 14.0, 176.0 / 63.0, -1.0 / 2.0},
+                      {485.0 / 21.0, -151.0 / 14.0, 23.0 / 9.0, -31.0 / 168.0}}};
+const Coefs* coefs_for(int order) {
+  switch (order) {
+    case 3: return &kEpi3;
+    case 4: return &kEpi4;
+    case 5: return &kEpi5;
+    case 6: return &kEpi6;
+    default: return nullptr;
+  }
+}
+constexpr int kStartupSubsteps = 8;
+constexpr double kEpsJvp = 1e-30;
+
+sw_kiops_opts default_opts() {
+  sw_kiops_opts o;
+  o.tol = 1e-10;
+  o.m_init = 10;
+  o.m_min = 10;
+  o.m_max = 128;
+  o.iop = 2;
+  o.tau_init = 0.0;
+  return o;
+}
+
+int alloc_vec(double*& p, long long n) {
+  if (p) return SW_OK;
+  return cudaMalloc(&p, sizeof(double) * n) == cudaSuccess ? SW_OK : SW_ENOMEM;
+}
+
+int ensure_epi(Ctx& c) {
+  int rc;
+  if ((rc = alloc_vec(c.d_Fn, c.n)) || (rc = alloc_vec(c.d_tmp, c.n)) || (rc = alloc_vec(c.d_tmp2, c.n))) return rc;
+  for (int i = 0; i < MAX_HIST; ++i)
+    if ((rc = alloc_vec(c.d_R[i], c.n)) || (rc = alloc_vec(c.d_hq[i], c.n)) || (rc = alloc_vec(c.d_hF[i], c.n)))
+      return rc;
+  for (int i = 0; i < 4; ++i)
+    if ((rc = alloc_vec(c.d_b[i], c.n))) return rc;
+  return SW_OK;
+}
+
+// history entry i (1 = most recent) lives in slot (head - (i - 1)) mod MAX_HIST
+int hist_slot(const Ctx& c, int i) { return ((c.hist_head - (i - 1)) % MAX_HIST + MAX_HIST) % MAX_HIST; }
+
+int push_history(Ctx& c, const double* q, const double* F, cudaStream_t s) {
+  c.hist_head = (c.hist_head + 1) % MAX_HIST;
+  int slot = c.hist_head;
+  if (cudaMemcpyAsync(c.d_hq[slot], q, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(c.d_hF[slot], F, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return SW_ECUDA;
+  if (c.hist_count < MAX_HIST) c.hist_count++;
+  return SW_OK;
+}
+
+void add_stats(sw_kiops_stats* acc, const sw_kiops_stats& s) {
+  if (!acc) return;
+  acc->substeps += s.substeps;
+  acc->rejects += s.rejects;
+  acc->krylov_iters += s.krylov_iters;
+  acc->m_final = s.m_final;
+  acc->tau_final = s.tau_final;
+  acc->err_last = s.err_last;
+}
+
+int phi_call(Ctx& c, const double* q, double dt, int nb, const double* const* b, const sw_kiops_opts& o0, double* w,
+             sw_kiops_stats* acc, cudaStream_t s) {
+  sw_kiops_opts o = o0;
+  if (c.m_warm > 0) o.m_init = c.m_warm;
+  sw_kiops_stats st{};
+  int rc = kiops_run(c, q, dt, 1.0, nb, b, o, w, &st, s);
+  if (rc) return rc;
+  c.m_warm = st.m_final;
+  add_stats(acc, st);
+  return SW_OK;
+}
+
+// one exponential-Euler step (Eq. 25) of size h on q in place; F = F(q) given
+int epi2_inplace(Ctx& c, double* q, const double* F, double h, const sw_kiops_opts& o, sw_kiops_stats* acc,
+                 cudaStream_t s) {
+  int rc;
+  const double* xs[1] = {F};
+  double cf[1] = {h};
+  if ((rc = launch_lincomb(c, c.d_b[0], c.n, 1, xs, cf, s))) return rc;
+  const double* b[2] = {nullptr, c.d_b[0]};
+  if ((rc = phi_call(c, q, h, 2, b, o, c.d_tmp, acc, s))) return rc;
+  const double* ys[2] = {q, c.d_tmp};
+  double one[2] = {1.0, 1.0};
+  return launch_lincomb(c, q, c.n, 2, ys, one, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sw_status_str(int status) {
+  switch (status) {
+    case SW_OK: return "ok";
+    case SW_EINVAL: return "invalid argument";
+    case SW_ENOMEM: return "out of memory";
+    case SW_ECUDA: return "CUDA error";
+    case SW_EKRYLOV: return "Krylov solver substep or rejection limit reached";
+    case SW_ETIMEOUT: return "bounded device wait timed out";
+    case SW_ENONFINITE: return "non-finite value";
+    default: return "unknown status";
+  }
+}
+
+int sw_init(int n_e, int p, const sw_params* prm, sw_ctx_t* out) {
+  if (!out) return SW_EINVAL;
+  *out = nullptr;
+  if (!prm || n_e < 1 || n_e > 1024 || p < 0 || p > MAX_NS - 1 || prm->precision != 0 || !(prm->radius > 0) ||
+      !(prm->gravity > 0) || !std::isfinite(prm->omega))
+    return SW_EINVAL;
+  sw_ctx* c = new (std::nothrow) sw_ctx();
+  if (!c) return SW_ENOMEM;
+  cudaGetDevice(&c->device);
+  c->ne = n_e;
+  c->ns = p + 1;
+  c->prm = *prm;
+  int rc = build_tables(*c);
+  if (rc) {
+    sw_free(c);
+    return rc;
+  }
+  *out = c;
+  return SW_OK;
+}
+
+void sw_free(sw_ctx_t c) {
+  if (!c) return;
+  double* ptrs[] = {c->d_node_coef, c->d_face_coef, c->d_fb, c->d_V, c->d_X, c->d_H, c->d_F, c->d_expm_ws,
+                    c->d_partials, c->d_scal, c->d_Fn, c->d_tmp, c->d_tmp2};
+  for (double* p : ptrs)
+    if (p) cudaFree(p);
+  for (int i = 0; i < MAX_HIST; ++i) {
+    if (c->d_R[i]) cudaFree(c->d_R[i]);
+    if (c->d_hq[i]) cudaFree(c->d_hq[i]);
+    if (c->d_hF[i]) cudaFree(c->d_hF[i]);
+  }
+  for (int i = 0; i < 4; ++i)
+    if (c->d_b[i]) cudaFree(c->d_b[i]);
+  if (c->d_lines) cudaFree(c->d_lines);
+  if (c->d_flags) cudaFree(c->d_flags);
+  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  delete c;
+}
+
+long long sw_num_unknowns(sw_ctx_t c) { return c ? c->n : -1; }
+
+int sw_grid_info(sw_ctx_t c, int* n_e, int* p, double* dx) {
+  if (!c) return SW_EINVAL;
+  if (n_e) *n_e = c->ne;
+  if (p) *p = c->ns - 1;
+  if (dx) *dx = c->dx;
+  return SW_OK;
+}
+
+int sw_node_xyz(sw_ctx_t c, double* xyz) {
+  if (!c || !xyz) return SW_EINVAL;
+  node_unit_xyz(*c, xyz);
+  return SW_OK;
+}
+
+int sw_set_bottom(sw_ctx_t c, const double* hB) {
+  if (!c || !hB) return SW_EINVAL;
+  return bottom_coefficients(*c, hB);
+}
+
+int sw_state_from_fields(sw_ctx_t c, const double* h, const double* hB, const double* V, double* q) {
+  if (!c || !h || !hB || !V || !q) return SW_EINVAL;
+  int rc = bottom_coefficients(*c, hB);
+  if (rc) return rc;
+  return fields_to_state(*c, h, hB, V, q);
+}
+
+int sw_rhs(sw_ctx_t c, const double* q, double* F, void* stream) {
+  if (!c || !q || !F || q == F) return SW_EINVAL;
+  return launch_rhs(*c, q, F, as_stream(stream));
+}
+
+int sw_jvp(sw_ctx_t c, const double* q, const double* v, double eps, double* Jv, void* stream) {
+  if (!c || !q || !v || !Jv || Jv == q || Jv == v || !(eps > 0) || !std::isfinite(eps)) return SW_EINVAL;
+  AugEpilogue ep;
+  return launch_jvp(*c, q, v, eps, Jv, ep, as_stream(stream));
+}
+
+int sw_kiops_phi(sw_ctx_t c, const double* q_lin, double dt, double tau_out, int nb, const double* const* b,
+                 const sw_kiops_opts* opts, double* w, sw_kiops_stats* st, void* stream) {
+  if (!c || !q_lin || !w || !b || nb < 1 || nb > MAX_NB || !std::isfinite(dt) || !(tau_out > 0)) return SW_EINVAL;
+  for (int k = 0; k < nb; ++k)
+    if (b[k] == w) return SW_EINVAL;
+  if (w == q_lin) return SW_EINVAL;
+  sw_kiops_opts o = opts ? *opts : default_opts();
+  int rc = kiops_run(*c, q_lin, dt, tau_out, nb, b, o, w, st, as_stream(stream));
+  return rc;
+}
+
+int sw_epi_reset(sw_ctx_t c) {
+  if (!c) return SW_EINVAL;
+  c->hist_count = 0;
+  c->hist_head = 0;
+  c->m_warm = 0;
+  return SW_OK;
+}
+
+int sw_epi_set_history(sw_ctx_t c, int i, const double* q, const double* F, void* stream) {
+  if (!c || !q || i < 1 || i > MAX_HIST) return SW_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  int rc = ensure_epi(*c);
+  if (rc) return rc;
+  // seeding addresses entries relative to head = 0: entry i lives in slot (0 - (i-1)) mod MAX_HIST
+  c->hist_head = 0;
+  int slot = hist_slot(*c, i);
+  if (cudaMemcpyAsync(c->d_hq[slot], q, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return SW_ECUDA;
+  if (F) {
+    if (cudaMemcpyAsync(c->d_hF[slot], F, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return SW_ECUDA;
+  } else if ((rc = launch_rhs(*c, c->d_hq[slot], c->d_hF[slot], s))) {
+    return rc;
+  }
+  if (c->hist_count < i) c->hist_count = i;
+  return SW_OK;
+}
+
+int sw_epi_step(sw_ctx_t c, int order, double dt, double* q, const sw_kiops_opts* opts, sw_kiops_stats* st,
+                void* stream) {
+  if (!c || !q || order < 2 || order > 6 || !std::isfinite(dt) || !(dt > 0)) return SW_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  sw_kiops_opts o = opts ? *opts : default_opts();
+  int rc = ensure_epi(*c);
+  if (rc) return rc;
+  if (st) std::memset(st, 0, sizeof(*st));
+  const long long n = c->n;
+  if ((rc = launch_rhs(*c, q, c->d_Fn, s))) return rc;
+  if (order == 2) {
+    rc = epi2_inplace(*c, q, c->d_Fn, dt, o, st, s);
+    if (rc) return rc;
+    return cuda_status(cudaStreamSynchronize(s));
+  }
+  const Coefs* A = coefs_for(order);
+  const int P = A->P, M = A->M;
+  if (c->hist_count < P) {
+    // start-up: EPI2 with N_sub smaller steps (Sec. 4)
+    if ((rc = push_history(*c, q, c->d_Fn, s))) return rc;
+    const double h = dt / kStartupSubsteps;
+    for (int k = 0; k < kStartupSubsteps; ++k) {
+      if (k > 0 && (rc = launch_rhs(*c, q, c->d_Fn, s))) return rc;
+      if ((rc = epi2_inplace(*c, q, c->d_Fn, h, o, st, s))) return rc;
+    }
+    return cuda_status(cudaStreamSynchronize(s));
+  }
+  // remainders R(q_{n-i}) = F(q_{n-i}) - F_n - J_n (q_{n-i} - q_n)  (Eq. 33)
+  for (int i = 1; i <= P; ++i) {
+    int slot = hist_slot(*c, i);
+    const double* d1[2] = {c->d_hq[slot], q};
+    double c1[2] = {1.0, -1.0};
+    if ((rc = launch_lincomb(*c, c->d_tmp, n, 2, d1, c1, s))) return rc;
+    AugEpilogue ep;
+    if ((rc = launch_jvp(*c, q, c->d_tmp, kEpsJvp, c->d_tmp2, ep, s))) return rc;
+    const double* d2[3] = {c->d_hF[slot], c->d_Fn, c->d_tmp2};
+    double c2[3] = {1.0, -1.0, -1.0};
+    if ((rc = launch_lincomb(*c, c->d_R[i - 1], n, 3, d2, c2, s))) return rc;
+  }
+  // b_1 = dt F_n + v_1, b_m = v_m with v_m = sum_i alpha_{m,i} dt R_i  (Eq. 34-35)
+  for (int m = 0; m < M; ++m) {
+    const double* xs[MAX_HIST + 1];
+    double cf[MAX_HIST + 1];
+    int k = 0;
+    if (m == 0) { xs[k] = c->d_Fn; cf[k] = dt; ++k; }
+    for (int i = 0; i < P; ++i) { xs[k] = c->d_R[i]; cf[k] = A->a[m][i] * dt; ++k; }
+    if ((rc = launch_lincomb(*c, c->d_b[m], n, k, xs, cf, s))) return rc;
+  }
+  const double* b[MAX_NB] = {nullptr};
+  for (int m = 0; m < M; ++m) b[m + 1] = c->d_b[m];
+  if ((rc = phi_call(*c, q, dt, M + 1, b, o, c->d_tmp, st, s))) return rc;
+  if ((rc = push_history(*c, q, c->d_Fn, s))) return rc;
+  const double* ys[2] = {q, c->d_tmp};
+  double one[2] = {1.0, 1.0};
+  if ((rc = launch_lincomb(*c, q, n, 2, ys, one, s))) return rc;
+  return cuda_status(cudaStreamSynchronize(s));
+}
+
+long long sw_kernel_launches(sw_ctx_t c) { return c ? c->launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,261 @@
+// Adaptive Krylov phi-function solver (Eq. 29) with incomplete
+// orthogonalisation and substepping, and the multistep EPI driver (Eq. 25, 30,
+// 34-38).  Host control code: every vector operation is a kernel of this
+// library; the host only reads a handful of device scalars once per substep
+// attempt to take the accept/reject and step-size decisions.
+//
+// Controller reading (the paper defers the algorithm to its reference [10]):
+//  * augmentation with nu = 2^-ceil(log2 max_k ||b_k||_1), mu = 1/nu: the
+//    operator [x; y] -> [dt J x + nu (y_1 b_p + .. + y_p b_1); (y_2, .., y_p, 0)]
+//    and the start vector [b_0; 0, .., 0, mu];
+//  * each substep builds a fresh basis from the current augmented vector; the
+//    new vector is orthogonalised against the last `iop` basis vectors
+//    (modified Gram-Schmidt, oldest first); ||z|| < tol is a happy breakdown,
+//    after which the projection is exact and the rest of the interval is taken;
+//  * err = beta h_{j+1,j} |F[j-1, j]| with F = exp(tau [[H_j, e_1], [0, 0]]),
+//    omega = (tau_end / tau) err / (tol beta_0), beta_0 = ||[b_0; mu e_p]||;
+//  * accept when omega <= 1.2; new tau from the order estimate (j/4, or
+//    measured from two tries at equal m), new m from the growth estimate (2, or
+//    measured from two tries at equal tau), safety factor 0.8, tau in
+//    [tau/5, 5 tau], m in [max(m_min, floor(3m/4)), min(m_max, ceil(4m/3))];
+//    change whichever of tau or m costs fewer projected products, tau on ties
+//    or when j == m_max.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "swepi_internal.h"
+
+namespace swepi {
+
+namespace {
+constexpr double kDelta = 1.2;
+constexpr double kGamma = 0.8;
+constexpr int kMaxSubsteps = 100000;
+constexpr int kMaxRejects = 100000;
+constexpr double kEpsJvp = 1e-30;
+
+// device scalar slots (d_scal)
+constexpr int S_BETA = 0, S_BETA0 = 1, S_STAT = 8, S_NORMB = 16;
+
+int read_back(Ctx& c, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(c.h_pinned, c.d_scal, sizeof(double) * 32, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return SW_ECUDA;
+  e = cudaMemcpyAsync(c.h_pinned + 32, c.d_flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return SW_ECUDA;
+  return cuda_status(cudaStreamSynchronize(s));
+}
+const int* pinned_flags(const Ctx& c) { return reinterpret_cast<const int*>(c.h_pinned + 32); }
+
+void free_ptr(double*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+}  // namespace
+
+int ensure_krylov(Ctx& c, int m_max) {
+  if (c.vcap >= m_max + 1 && c.d_V) return SW_OK;
+  free_ptr(c.d_V);
+  free_ptr(c.d_X);
+  free_ptr(c.d_H);
+  free_ptr(c.d_F);
+  free_ptr(c.d_expm_ws);
+  c.ldv = ((c.n + MAX_NB + 31) / 32) * 32;
+  c.vcap = m_max + 1;
+  c.ldh = m_max + 2;
+  if (cudaMalloc(&c.d_V, sizeof(double) * c.ldv * c.vcap) != cudaSuccess) return SW_ENOMEM;
+  if (cudaMalloc(&c.d_X, sizeof(double) * c.ldv) != cudaSuccess) return SW_ENOMEM;
+  if (cudaMalloc(&c.d_H, sizeof(double) * c.ldh * c.ldh) != cudaSuccess) return SW_ENOMEM;
+  if (cudaMalloc(&c.d_F, sizeof(double) * c.ldh * c.ldh) != cudaSuccess) return SW_ENOMEM;
+  if (cudaMalloc(&c.d_expm_ws, sizeof(double) * 8 * 160 * 160) != cudaSuccess) return SW_ENOMEM;
+  if (!c.d_partials && cudaMalloc(&c.d_partials, sizeof(double) * RED_BLOCKS) != cudaSuccess) return SW_ENOMEM;
+  if (!c.d_scal && cudaMalloc(&c.d_scal, sizeof(double) * 64) != cudaSuccess) return SW_ENOMEM;
+  if (!c.d_flags) {
+    if (cudaMalloc(&c.d_flags, sizeof(int) * 16) != cudaSuccess) return SW_ENOMEM;
+    if (cudaMemset(c.d_flags, 0, sizeof(int) * 16) != cudaSuccess) return SW_ECUDA;
+  }
+  if (!c.h_pinned && cudaMallocHost(&c.h_pinned, sizeof(double) * 64) != cudaSuccess) return SW_ENOMEM;
+  if (cudaMemset(c.d_V, 0, sizeof(double) * c.ldv * c.vcap) != cudaSuccess) return SW_ECUDA;
+  return SW_OK;
+}
+
+int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, const double* const* b,
+              const sw_kiops_opts& o, double* w, sw_kiops_stats* st, cudaStream_t s) {
+  if (nb < 1 || nb > MAX_NB || !(tau_out > 0) || o.m_min < 1 || o.m_max < o.m_min || o.m_max > 150 || o.iop < 1 ||
+      !(o.tol > 0))
+    return SW_EINVAL;
+  int rc = ensure_krylov(c, o.m_max);
+  if (rc) return rc;
+  const long long n = c.n;
+  int p = nb - 1;
+  const double* bk[MAX_NB + 1] = {};
+  for (int k = 0; k < nb; ++k) bk[k] = b[k];
+  if (p == 0) { p = 1; bk[1] = nullptr; }
+  const long long N = n + p;
+
+  // scaling of the augmented operator
+  for (int k = 1; k <= p; ++k) {
+    if (bk[k]) {
+      if ((rc = launch_norm1(c, bk[k], n, c.d_scal + S_NORMB + k, s))) return rc;
+    } else if (cudaMemsetAsync(c.d_scal + S_NORMB + k, 0, sizeof(double), s) != cudaSuccess) {
+      return SW_ECUDA;
+    }
+  }
+  // X = [b_0; 0 .. 0 mu]
+  if (bk[0]) {
+    if (cudaMemcpyAsync(c.d_X, bk[0], sizeof(double) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return SW_ECUDA;
+  } else if (cudaMemsetAsync(c.d_X, 0, sizeof(double) * n, s) != cudaSuccess) {
+    return SW_ECUDA;
+  }
+  if ((rc = read_back(c, s))) return rc;
+  double normb = 0.0;
+  for (int k = 1; k <= p; ++k) normb = std::max(normb, c.h_pinned[S_NORMB + k]);
+  if (!std::isfinite(normb)) return SW_ENONFINITE;
+  double nu = 1.0, mu = 1.0;
+  if (normb > 0) {
+    int ex = (int)std::ceil(std::log2(normb));
+    nu = std::ldexp(1.0, -ex);
+    mu = std::ldexp(1.0, ex);
+  }
+  double tail[MAX_NB] = {};
+  tail[p - 1] = mu;
+  if ((rc = launch_set_tail(c, c.d_X, n, p, tail, s))) return rc;
+  if ((rc = launch_norm2(c, c.d_X, N, c.d_scal + S_BETA0, 0.0, nullptr, 0, nullptr, s))) return rc;
+  if ((rc = read_back(c, s))) return rc;
+  const double beta0 = c.h_pinned[S_BETA0];
+  if (!std::isfinite(beta0)) return SW_ENONFINITE;
+
+  AugEpilogue ep;
+  ep.scale = dt;
+  ep.nu = nu;
+  ep.p = p;
+  for (int l = 0; l < p; ++l) ep.b[l] = bk[p - l];
+  ep.skip = c.d_flags;
+
+  const double tau_end = tau_out;
+  double tau_now = 0.0;
+  double tau = (o.tau_init > 0) ? std::min(o.tau_init, tau_end) : tau_end;
+  int m = std::min(std::max(o.m_init, o.m_min), o.m_max);
+  int j = 0;
+  bool have_prev = false;
+  int prev_m = 0;
+  double prev_tau = 0.0, prev_omega = 0.0;
+  int krylov = 0, substeps = 0, rejects = 0;
+  double last_err = 0.0;
+  double* V = c.d_V;
+  const long long ldv = c.ldv;
+
+  while (tau_now < tau_end) {
+    if (j == 0) {
+      if ((rc = launch_norm2(c, c.d_X, N, c.d_scal + S_BETA, 0.0, nullptr, 0, nullptr, s))) return rc;
+      if ((rc = launch_scale_inv(c, V, c.d_X, c.d_scal + S_BETA, N, nullptr, s))) return rc;
+      if (cudaMemsetAsync(c.d_flags, 0, sizeof(int) * 2, s) != cudaSuccess) return SW_ECUDA;
+      if (cudaMemsetAsync(c.d_H, 0, sizeof(double) * c.ldh * c.ldh, s) != cudaSuccess) return SW_ECUDA;
+    }
+    for (int it = j; it < m; ++it) {
+      double* Vi = V + it * ldv;
+      double* Vn = V + (it + 1) * ldv;
+      ep.tail_in = Vi + n;
+      ep.tail_out = Vn + n;
+      if ((rc = launch_jvp(c, q_lin, Vi, kEpsJvp, Vn, ep, s))) return rc;
+      for (int i = std::max(0, it - o.iop + 1); i <= it; ++i) {
+        double* h = c.d_H + (long long)i * c.ldh + it;
+        if ((rc = launch_dot(c, V + i * ldv, Vn, N, h, c.d_flags, s))) return rc;
+        if ((rc = launch_axpy_dev(c, Vn, V + i * ldv, h, N, c.d_flags, s))) return rc;
+      }
+      double* hs = c.d_H + (long long)(it + 1) * c.ldh + it;
+      if ((rc = launch_norm2(c, Vn, N, hs, o.tol, c.d_flags, it + 1, c.d_flags, s))) return rc;
+      if ((rc = launch_scale_inv(c, Vn, Vn, hs, N, c.d_flags, s))) return rc;
+    }
+    if ((rc = launch_expm_hess(c, m, tau, tau_end - tau_now, s))) return rc;
+    if ((rc = read_back(c, s))) return rc;
+    const int* fl = pinned_flags(c);
+    const bool happy = fl[0] != 0;
+    const int jnew = happy ? fl[1] : m;
+    krylov += jnew - j;
+    j = jnew;
+    const double beta = c.h_pinned[S_BETA];
+    const double Fjj = c.h_pinned[S_STAT + 0];
+    bool accept;
+    int m_new;
+    double tau_new;
+    double err = 0.0;
+    if (happy) {
+      tau = tau_end - tau_now;
+      accept = true;
+      m_new = m;
+      tau_new = tau;
+    } else {
+      double hsub = c.h_pinned[S_STAT + 4];
+      err = beta * hsub * std::fabs(Fjj);
+      double omega = (tau_end / tau) * err / (o.tol * beta0);
+      if (!std::isfinite(omega)) return SW_ENONFINITE;
+      accept = omega <= kDelta;
+      double order = (have_prev && prev_m == m && prev_tau != tau)
+                         ? std::max(1.0, std::log(omega / prev_omega) / std::log(tau / prev_tau))
+                         : j / 4.0;
+      double kappa = (have_prev && prev_tau == tau && prev_m != m)
+                         ? std::max(1.1, std::pow(omega / prev_omega, 1.0 / (prev_m - m)))
+                         : 2.0;
+      double remaining = accept ? tau_end - (tau_now + tau) : tau_end - tau_now;
+      double tau_same = std::min(remaining, tau);
+      double tau_opt = (omega > 0) ? tau * std::pow(kGamma / omega, 1.0 / order) : 5 * tau;
+      tau_opt = std::min(remaining, std::max(tau / 5, std::min(5 * tau, tau_opt)));
+      int m_opt = (omega > 0) ? (int)std::ceil(j + std::log(omega / kGamma) / std::log(kappa)) : o.m_min;
+      m_opt = std::max(o.m_min, std::min(o.m_max, std::max((int)std::floor(3.0 * m / 4.0),
+                                                           std::min(m_opt, (int)std::ceil(4.0 * m / 3.0)))));
+      if (j == o.m_max) {
+        m_new = m;
+        tau_new = tau_opt;
+      } else {
+        double cost_tau = tau_opt > 0 ? m * std::ceil(remaining / tau_opt) : 0.0;
+        double cost_m = tau_same > 0 ? m_opt * std::ceil(remaining / tau_same) : 0.0;
+        if (cost_tau <= cost_m) { m_new = m; tau_new = tau_opt; }
+        else { m_new = m_opt; tau_new = tau_same; }
+      }
+      if (!accept) {
+        have_prev = true;
+        prev_m = m;
+        prev_tau = tau;
+        prev_omega = omega;
+      }
+    }
+    last_err = err;
+    if (accept) {
+      if ((rc = launch_combine(c, j, n, s))) return rc;
+      tau_now += tau;
+      double tv[MAX_NB];
+      for (int l = 0; l < p; ++l) {
+        int k = p - 1 - l;
+        double f = 1.0;
+        for (int t = 2; t <= k; ++t) f *= t;
+        tv[l] = mu * std::pow(tau_now, k) / f;
+      }
+      if ((rc = launch_set_tail(c, c.d_X, n, p, tv, s))) return rc;
+      ++substeps;
+      j = 0;
+      have_prev = false;
+      if (substeps > kMaxSubsteps) return SW_EKRYLOV;
+    } else {
+      ++rejects;
+      if (rejects > kMaxRejects) return SW_EKRYLOV;
+      if (m_new < j) j = m_new;
+    }
+    m = m_new;
+    if (tau_now < tau_end) tau = (tau_new > 0) ? std::min(tau_new, tau_end - tau_now) : tau_end - tau_now;
+  }
+  if (cudaMemcpyAsync(w, c.d_X, sizeof(double) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return SW_ECUDA;
+  if (st) {
+    st->substeps = substeps;
+    st->rejects = rejects;
+    st->krylov_iters = krylov;
+    st->m_final = m;
+    st->tau_final = tau;
+    st->err_last = last_err;
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace swepi

@@ -1,0 +1,147 @@
+// Internal declarations of libswepi: the context, device tables and kernel
+// launchers shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/swepi.h"
+
+namespace swepi {
+
+constexpr int MAX_NS = 8;   // p <= 7
+constexpr int MAX_NB = 8;   // phi_0 .. phi_7
+constexpr int MAX_HIST = 4; // EPI6 uses q_{n-1..n-4}
+
+// Per-node coefficient arrays (structure of arrays, `nodes` doubles each).
+enum NodeCoef {
+  NC_C11 = 0, NC_C12, NC_C22,        // g_r h^ij / (2 sqrt g): pressure part of sqrt(g) T^ij
+  NC_K11, NC_K12, NC_K21, NC_K22,    // -2 Gamma^i_{j0} (Coriolis, Eq. 71-74)
+  NC_G1A, NC_G1B, NC_G2A, NC_G2B,    // Gamma^1_11, 2 Gamma^1_12, 2 Gamma^2_12, Gamma^2_22 (Eq. 75-80)
+  NC_B1, NC_B2,                      // -g_r h^ij d h_B / dx^j (topography)
+  NC_COUNT
+};
+
+// Per-interface-point coefficients (structure of arrays over face points), in
+// the coordinates of the face's owner side.
+enum FaceCoef {
+  FC_AD = 0,        // g_r h^dd / sqrt g   (a^d = sqrt(FC_AD * q^0), App. E)
+  FC_P1, FC_P2,     // g_r h^{i d} / (2 sqrt g)   (pressure component, App. D)
+  FC_T00, FC_T01, FC_T10, FC_T11,  // neighbour -> owner contravariant transform (App. C)
+  FC_M00, FC_M01, FC_M10, FC_M11,  // sigma * (owner -> neighbour transform), applied to the flux
+  FC_SIG,           // sigma = +-1: sign of the normal flux on the neighbour side
+  FC_COUNT
+};
+
+// One face line = the N_s points shared by two element edges.
+struct FaceLine {
+  int owner, owner_edge;   // element index, edge 0=W 1=E 2=S 3=N
+  int nbr, nbr_edge;
+  int reversed;            // neighbour point index = N_s-1-i
+  int dir;                 // owner normal direction (1 or 2)
+  int owner_is_left;       // owner edge is E or N
+  int pad;
+};
+
+// Small DFR constants passed by value to the kernels.
+struct DfrConst {
+  double D[MAX_NS][MAX_NS + 2];   // l~'_n(xi_k), Eq. (12)-(13)
+  double lm[MAX_NS], lp[MAX_NS];  // l_k(-1), l_k(+1), Eq. (8)
+  double two_over_dx;             // Eq. (6)
+  double gravity;
+};
+
+struct Ctx {
+  int device = 0;
+  int ne = 0, ns = 0;
+  double dx = 0;
+  long long nelem = 0, nodes = 0, n = 0;
+  int nlines = 0;
+  long long nfacepts = 0;
+  sw_params prm{};
+  double frame[6][3][3]{};        // per panel: centre, e1, e2
+  std::vector<double> xi, wq;     // Gauss-Legendre points and weights
+  std::vector<double> Dg;         // collocation derivative on the points [ns][ns]
+  DfrConst dc{};
+  std::vector<double> node_coef_h;  // [NC_COUNT][nodes]
+  // device tables
+  double* d_node_coef = nullptr;
+  double* d_face_coef = nullptr;
+  FaceLine* d_lines = nullptr;
+  double* d_fb = nullptr;         // face flux buffer [nelem][4][3][ns]
+  // Krylov workspace
+  int vcap = 0;                   // rows of V allocated (m_max + 1)
+  long long ldv = 0;              // leading dimension of V (>= n + MAX_NB)
+  double* d_V = nullptr;
+  double* d_X = nullptr;          // current augmented vector [ldv]
+  int ldh = 0;                    // leading dimension of H and F (m_max + 2)
+  double* d_H = nullptr;
+  double* d_F = nullptr;
+  double* d_expm_ws = nullptr;    // expm workspace
+  double* d_partials = nullptr;   // reduction partials
+  double* d_scal = nullptr;       // device scalars (see kiops.cu)
+  int* d_flags = nullptr;         // happy flag, happy size
+  double* h_pinned = nullptr;     // pinned read-back area
+  const double** d_bptr = nullptr;
+  // EPI state
+  double* d_Fn = nullptr;
+  double* d_tmp = nullptr;
+  double* d_tmp2 = nullptr;
+  double* d_R[MAX_HIST] = {};
+  double* d_b[MAX_NB] = {};
+  double* d_hq[MAX_HIST] = {};    // history ring: q_{n-i}
+  double* d_hF[MAX_HIST] = {};
+  int hist_count = 0;
+  int hist_head = 0;              // slot of the most recent entry
+  int m_warm = 0;                 // KIOPS warm start (0 = none)
+  long long launches = 0;
+};
+
+// ---- geometry / tables (geom.cpp)
+int build_tables(Ctx& c);
+void node_unit_xyz(const Ctx& c, double* xyz);
+int bottom_coefficients(Ctx& c, const double* hB);
+int fields_to_state(const Ctx& c, const double* h, const double* hB, const double* V, double* q);
+
+// ---- DFR kernels (dfr.cu)
+struct AugEpilogue {
+  // out = scale * result + nu * sum_l tail_in[l] * b[l]   (b[l] may be null)
+  double scale = 1.0;
+  double nu = 0.0;
+  int p = 0;
+  const double* b[MAX_NB] = {};
+  const double* tail_in = nullptr;  // p doubles (device)
+  double* tail_out = nullptr;       // p doubles (device): (tail_in[1..p-1], 0)
+  const int* skip = nullptr;        // if non-null and *skip != 0 the kernels return
+};
+int launch_rhs(Ctx& c, const double* q, double* F, cudaStream_t s);
+int launch_jvp(Ctx& c, const double* q, const double* v, double eps, double* out,
+               const AugEpilogue& ep, cudaStream_t s);
+
+// ---- Krylov kernels (krylov.cu)
+constexpr int RED_BLOCKS = 456;   // 3 x 152 SMs
+int launch_dot(Ctx& c, const double* x, const double* y, long long n, double* dst, const int* skip,
+               cudaStream_t s);
+int launch_norm2(Ctx& c, const double* x, long long n, double* dst, double tol, int* happy,
+                 int happy_value, const int* skip, cudaStream_t s);
+int launch_norm1(Ctx& c, const double* x, long long n, double* dst, cudaStream_t s);
+int launch_axpy_dev(Ctx& c, double* y, const double* x, const double* alpha, long long n,
+                    const int* skip, cudaStream_t s);
+int launch_scale_inv(Ctx& c, double* y, const double* x, const double* s_dev, long long n,
+                     const int* skip, cudaStream_t s);
+int launch_expm_hess(Ctx& c, int j, double tau, double tau_happy, cudaStream_t s);
+int launch_combine(Ctx& c, int j, long long n, cudaStream_t s);
+int launch_set_tail(Ctx& c, double* x, long long n, int p, const double* vals, cudaStream_t s);
+int launch_lincomb(Ctx& c, double* out, long long n, int k, const double* const* xs,
+                   const double* coef, cudaStream_t s);
+
+// ---- drivers
+int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, const double* const* b,
+              const sw_kiops_opts& o, double* w, sw_kiops_stats* st, cudaStream_t s);
+int ensure_krylov(Ctx& c, int m_max);
+
+inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? SW_OK : SW_ECUDA; }
+
+}  // namespace swepi

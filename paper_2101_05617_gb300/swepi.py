@@ -1,0 +1,268 @@
+"""Thin ctypes binding of libswepi.so (C ABI in include/swepi.h).
+
+Argument marshalling only: every step of the numerical path runs in the
+library's CUDA kernels.  Device vectors are torch float64 CUDA tensors
+(contiguous, canonical layout [var][panel][e2][e1][k2][k1]); streams are torch
+streams.  The functions keep the C names (sw_init, sw_rhs, sw_jvp,
+sw_kiops_phi, sw_epi_step, ...); the class ``SWContext`` bundles them.
+
+There is no fallback: if the library is missing or fails to load, importing
+or calling raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libswepi.so")
+
+SW_OK = 0
+STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA error",
+          -4: "Krylov solver limit", -5: "device wait timed out", -6: "non-finite value"}
+
+
+class SWError(RuntimeError):
+    def __init__(self, call, status):
+        super().__init__(f"{call} failed: {STATUS.get(status, status)} ({status})")
+        self.status = status
+
+
+class sw_params(ctypes.Structure):
+    _fields_ = [("radius", ctypes.c_double), ("gravity", ctypes.c_double), ("omega", ctypes.c_double),
+                ("lambda0", ctypes.c_double), ("phi0", ctypes.c_double), ("alpha0", ctypes.c_double),
+                ("precision", ctypes.c_int)]
+
+
+class sw_kiops_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("m_init", ctypes.c_int), ("m_min", ctypes.c_int),
+                ("m_max", ctypes.c_int), ("iop", ctypes.c_int), ("tau_init", ctypes.c_double)]
+
+
+class sw_kiops_stats(ctypes.Structure):
+    _fields_ = [("substeps", ctypes.c_int), ("rejects", ctypes.c_int), ("krylov_iters", ctypes.c_int),
+                ("m_final", ctypes.c_int), ("tau_final", ctypes.c_double), ("err_last", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libswepi.so (raises if it is missing: there is no CPU fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libswepi.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, dp, ip, ll = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_longlong
+    L.sw_init.argtypes = [ip, ip, ctypes.POINTER(sw_params), ctypes.POINTER(vp)]
+    L.sw_free.argtypes = [vp]
+    L.sw_free.restype = None
+    L.sw_num_unknowns.argtypes = [vp]
+    L.sw_num_unknowns.restype = ll
+    L.sw_grid_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), dp]
+    L.sw_node_xyz.argtypes = [vp, vp]
+    L.sw_state_from_fields.argtypes = [vp, vp, vp, vp, vp]
+    L.sw_set_bottom.argtypes = [vp, vp]
+    L.sw_rhs.argtypes = [vp, vp, vp, vp]
+    L.sw_jvp.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp]
+    L.sw_kiops_phi.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, ip, ctypes.POINTER(vp),
+                               ctypes.POINTER(sw_kiops_opts), vp, ctypes.POINTER(sw_kiops_stats), vp]
+    L.sw_epi_step.argtypes = [vp, ip, ctypes.c_double, vp, ctypes.POINTER(sw_kiops_opts),
+                              ctypes.POINTER(sw_kiops_stats), vp]
+    L.sw_epi_set_history.argtypes = [vp, ip, vp, vp, vp]
+    L.sw_epi_reset.argtypes = [vp]
+    L.sw_kernel_launches.argtypes = [vp]
+    L.sw_kernel_launches.restype = ll
+    L.sw_status_str.argtypes = [ip]
+    L.sw_status_str.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+EXPORTED = ["sw_init", "sw_free", "sw_num_unknowns", "sw_grid_info", "sw_node_xyz", "sw_state_from_fields",
+            "sw_set_bottom", "sw_rhs", "sw_jvp", "sw_kiops_phi", "sw_epi_step", "sw_epi_set_history",
+            "sw_epi_reset", "sw_kernel_launches", "sw_status_str"]
+
+
+def _check(call, rc):
+    if rc != SW_OK:
+        raise SWError(call, rc)
+
+
+def _dev_ptr(t, n=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"tensor has {t.numel()} elements, need {n}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _host(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    if a.size < n:
+        raise ValueError("host array too small")
+    return a
+
+
+def make_opts(tol=1e-10, m_init=10, m_min=10, m_max=128, iop=2, tau_init=0.0):
+    return sw_kiops_opts(tol, m_init, m_min, m_max, iop, tau_init)
+
+
+# ------------------------------------------------------------------ C names
+def sw_init(n_e, p, rotation=(0.0, 0.0, 0.0), radius=6.37122e6, gravity=9.80616, omega=7.292e-5):
+    prm = sw_params(radius, gravity, omega, rotation[0], rotation[1], rotation[2], 0)
+    h = ctypes.c_void_p()
+    _check("sw_init", lib().sw_init(int(n_e), int(p), ctypes.byref(prm), ctypes.byref(h)))
+    return h
+
+
+def sw_free(ctx):
+    lib().sw_free(ctx)
+
+
+def sw_num_unknowns(ctx):
+    return int(lib().sw_num_unknowns(ctx))
+
+
+def sw_node_xyz(ctx):
+    n = sw_num_unknowns(ctx)
+    out = np.empty(n, dtype=np.float64)
+    _check("sw_node_xyz", lib().sw_node_xyz(ctx, out.ctypes.data_as(ctypes.c_void_p)))
+    return out.reshape(3, -1)
+
+
+def sw_state_from_fields(ctx, h, hB, V):
+    n = sw_num_unknowns(ctx)
+    nodes = n // 3
+    h, hB, V = _host(h, nodes), _host(hB, nodes), _host(V, n)
+    q = np.empty(n, dtype=np.float64)
+    _check("sw_state_from_fields", lib().sw_state_from_fields(
+        ctx, h.ctypes.data_as(ctypes.c_void_p), hB.ctypes.data_as(ctypes.c_void_p),
+        V.ctypes.data_as(ctypes.c_void_p), q.ctypes.data_as(ctypes.c_void_p)))
+    return q
+
+
+def sw_set_bottom(ctx, hB):
+    nodes = sw_num_unknowns(ctx) // 3
+    hB = _host(hB, nodes)
+    _check("sw_set_bottom", lib().sw_set_bottom(ctx, hB.ctypes.data_as(ctypes.c_void_p)))
+
+
+def sw_rhs(ctx, q, F, stream=None):
+    n = sw_num_unknowns(ctx)
+    _check("sw_rhs", lib().sw_rhs(ctx, _dev_ptr(q, n), _dev_ptr(F, n), _stream(stream)))
+
+
+def sw_jvp(ctx, q, v, eps, Jv, stream=None):
+    n = sw_num_unknowns(ctx)
+    _check("sw_jvp", lib().sw_jvp(ctx, _dev_ptr(q, n), _dev_ptr(v, n), float(eps), _dev_ptr(Jv, n),
+                                  _stream(stream)))
+
+
+def sw_kiops_phi(ctx, q_lin, dt, tau_out, b, w, opts=None, stream=None):
+    n = sw_num_unknowns(ctx)
+    ptrs = (ctypes.c_void_p * len(b))(*[None if x is None else _dev_ptr(x, n).value for x in b])
+    st = sw_kiops_stats()
+    o = opts if opts is not None else make_opts()
+    _check("sw_kiops_phi", lib().sw_kiops_phi(ctx, _dev_ptr(q_lin, n), float(dt), float(tau_out), len(b), ptrs,
+                                              ctypes.byref(o), _dev_ptr(w, n), ctypes.byref(st), _stream(stream)))
+    return st.as_dict()
+
+
+def sw_epi_step(ctx, order, dt, q, opts=None, stream=None):
+    n = sw_num_unknowns(ctx)
+    st = sw_kiops_stats()
+    o = opts if opts is not None else make_opts()
+    _check("sw_epi_step", lib().sw_epi_step(ctx, int(order), float(dt), _dev_ptr(q, n), ctypes.byref(o),
+                                            ctypes.byref(st), _stream(stream)))
+    return st.as_dict()
+
+
+def sw_epi_set_history(ctx, i, q, F=None, stream=None):
+    n = sw_num_unknowns(ctx)
+    _check("sw_epi_set_history", lib().sw_epi_set_history(ctx, int(i), _dev_ptr(q, n),
+                                                          None if F is None else _dev_ptr(F, n), _stream(stream)))
+
+
+def sw_epi_reset(ctx):
+    _check("sw_epi_reset", lib().sw_epi_reset(ctx))
+
+
+def sw_kernel_launches(ctx):
+    return int(lib().sw_kernel_launches(ctx))
+
+
+def sw_status_str(status):
+    return lib().sw_status_str(int(status)).decode()
+
+
+class SWContext:
+    """Owns one library context (grid + workspace) on the current CUDA device."""
+
+    def __init__(self, n_e, p, rotation=(0.0, 0.0, 0.0), **consts):
+        self.handle = sw_init(n_e, p, rotation, **consts)
+        self.ne, self.p, self.ns = n_e, p, p + 1
+        self.n = sw_num_unknowns(self.handle)
+        self.nodes = self.n // 3
+
+    def close(self):
+        if self.handle:
+            sw_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def node_xyz(self):
+        return sw_node_xyz(self.handle)
+
+    def state_from_fields(self, h, hB, V):
+        return sw_state_from_fields(self.handle, h, hB, V)
+
+    def set_bottom(self, hB):
+        sw_set_bottom(self.handle, hB)
+
+    def rhs(self, q, out=None, stream=None):
+        import torch
+        out = torch.empty_like(q) if out is None else out
+        sw_rhs(self.handle, q, out, stream)
+        return out
+
+    def jvp(self, q, v, eps=1e-30, out=None, stream=None):
+        import torch
+        out = torch.empty_like(q) if out is None else out
+        sw_jvp(self.handle, q, v, eps, out, stream)
+        return out
+
+    def kiops_phi(self, q_lin, dt, b, tau_out=1.0, out=None, stream=None, **opts):
+        import torch
+        out = torch.empty_like(q_lin) if out is None else out
+        st = sw_kiops_phi(self.handle, q_lin, dt, tau_out, b, out, make_opts(**opts), stream)
+        return out, st
+
+    def epi_step(self, order, dt, q, stream=None, **opts):
+        return sw_epi_step(self.handle, order, dt, q, make_opts(**opts), stream)
+
+    def epi_set_history(self, i, q, F=None, stream=None):
+        sw_epi_set_history(self.handle, i, q, F, stream)
+
+    def epi_reset(self):
+        sw_epi_reset(self.handle)
+
+    def kernel_launches(self):
+        return sw_kernel_launches(self.handle)

@@ -1,0 +1,131 @@
+"""GPU parity of the DFR right-hand side and the complex-step JVP (Eq. 28)
+through the C ABI, element by element against the oracle."""
+import numpy as np
+import pytest
+
+from oracle import shallow_water as osw
+from tests.gpu_common import oracle_case, rel_err_per_var, scaled_direction, scaled_err_per_var, term_scale
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# FP64 evaluations of the same formulas in a different operation order.  The
+# error is measured against the magnitude of the summed flux-divergence terms
+# (term_scale): a balanced flow makes the tendency a small residual of them, so
+# a bound relative to the result itself would measure cancellation, not the
+# kernel.  Each output sums 2 N_s + 4 terms, each the result of ~30 rounded
+# operations (traces, the AUSM flux, the App. C transforms): ~500 u = 1e-13 of
+# the term scale bounds any evaluation order.
+TOL_RHS = 1e-13
+TOL_JVP = 1e-13
+
+CASES = [(4, 4, 0, 0.0), (3, 6, 1, 0.0), (2, 8, 2, 0.0), (5, 3, 3, 1500.0), (1, 2, 4, 0.0), (6, 7, 5, 800.0)]
+
+
+def _ctx(g):
+    from paper_2101_05617_gb300.swepi import SWContext
+    return SWContext(g.ne, g.ns - 1, g.rotation)
+
+
+@pytest.mark.parametrize("ne,ns,seed,bottom", CASES)
+def test_rhs_parity(ne, ns, seed, bottom):
+    _, g, q, hB = oracle_case(ne, ns, seed=seed, bottom_amp=bottom)
+    ctx = _ctx(g)
+    ctx.set_bottom(hB.reshape(-1))
+    qd = torch.tensor(q.reshape(-1), device="cuda")
+    F = ctx.rhs(qd)
+    torch.cuda.synchronize()
+    ref = osw.rhs_real(g, q)
+    err = scaled_err_per_var(F.cpu().numpy(), ref, term_scale(g, q))
+    assert max(err) < TOL_RHS, (err, rel_err_per_var(F.cpu().numpy(), ref))
+
+
+@pytest.mark.parametrize("ne,ns,seed,bottom", CASES)
+def test_jvp_parity(ne, ns, seed, bottom):
+    _, g, q, hB = oracle_case(ne, ns, seed=seed, bottom_amp=bottom)
+    ctx = _ctx(g)
+    ctx.set_bottom(hB.reshape(-1))
+    v = scaled_direction(q, seed + 100)
+    qd = torch.tensor(q.reshape(-1), device="cuda")
+    vd = torch.tensor(v.reshape(-1), device="cuda")
+    Jv = ctx.jvp(qd, vd, 1e-30)
+    torch.cuda.synchronize()
+    ref = osw.jvp(g, q, v, 1e-30)
+    err = scaled_err_per_var(Jv.cpu().numpy(), ref, term_scale(g, q, v))
+    assert max(err) < TOL_JVP, (err, rel_err_per_var(Jv.cpu().numpy(), ref))
+
+
+def test_geometry_and_state_conversion():
+    """Node positions and the fields->state conversion of the library agree with
+    the oracle's (independent implementations of App. B)."""
+    f, g, q, hB = oracle_case(3, 5, seed=7)
+    ctx = _ctx(g)
+    xyz = ctx.node_xyz()
+    np.testing.assert_allclose(xyz, g.node_xyz().reshape(3, -1), atol=2e-15)
+    h, hB2, V = f.evaluate(g.node_xyz())
+    qg = ctx.state_from_fields(h.reshape(-1), hB2.reshape(-1), V.reshape(3, -1))
+    err = rel_err_per_var(qg, q)
+    assert max(err) < 1e-13, err
+
+
+@pytest.mark.parametrize("workload", ["small_ne4_p3", "ne30_p5"])
+def test_mass_conservation_gpu(workload):
+    """sum w_m w_n dq^0/dt = 0 to round-off (Sec. 5.4.2) on the GPU path: the
+    interface mass fluxes cancel pairwise, so the budget is bounded by the
+    rounding of the summed divergence terms (a wrong or one-sided interface
+    flux would leave a residual ~1e-6 of that scale)."""
+    _, g, q, _ = oracle_case(6, 5, workload=workload, seed=3)
+    ctx = _ctx(g)
+    F = ctx.rhs(torch.tensor(q.reshape(-1), device="cuda")).cpu().numpy().reshape(q.shape)
+    w2 = g.w[:, None] * g.w[None, :]
+    budget = abs(np.sum(F[0] * w2))
+    assert budget < 1e-14 * np.sum(w2) * F[0].size / w2.size * term_scale(g, q)[0]
+
+
+def test_jvp_linearity_and_determinism():
+    _, g, q, _ = oracle_case(4, 6, seed=9)
+    ctx = _ctx(g)
+    qd = torch.tensor(q.reshape(-1), device="cuda")
+    v = torch.tensor(scaled_direction(q, 1).reshape(-1), device="cuda")
+    w = torch.tensor(scaled_direction(q, 2).reshape(-1), device="cuda")
+    a = ctx.jvp(qd, v)
+    b = ctx.jvp(qd, w)
+    c = ctx.jvp(qd, 2 * v + 3 * w)
+    assert torch.linalg.norm(c - 2 * a - 3 * b) < 1e-14 * torch.linalg.norm(c)
+    a2 = ctx.jvp(qd, v)
+    assert torch.equal(a, a2)
+
+
+def test_ragged_and_invalid_arguments():
+    from paper_2101_05617_gb300 import swepi
+    with pytest.raises(swepi.SWError):
+        swepi.sw_init(0, 3)
+    with pytest.raises(swepi.SWError):
+        swepi.sw_init(4, 8)
+    _, g, q, _ = oracle_case(2, 3, seed=1)
+    ctx = _ctx(g)
+    qd = torch.tensor(q.reshape(-1), device="cuda")
+    with pytest.raises(swepi.SWError):
+        swepi.sw_jvp(ctx.handle, qd, qd, 0.0, torch.empty_like(qd))
+    with pytest.raises(swepi.SWError):
+        swepi.sw_rhs(ctx.handle, qd, qd)
+
+
+@pytest.mark.parametrize("ne,ns,workload", [(60, 6, "ne60_p5"), (90, 7, "ne90_p6")])
+def test_full_size_parity(ne, ns, workload):
+    """The benchmark grids at full size (6 x 60 x 60, p = 5 and 6 x 90 x 90,
+    p = 6 with topography): RHS and JVP compared element by element."""
+    from paper_2101_05617_gb300 import synth
+    wl = synth.WORKLOADS[workload]
+    _, g, q, hB = oracle_case(ne, ns, workload=workload, seed=0,
+                              bottom_amp=wl.bottom_amp)
+    ctx = _ctx(g)
+    ctx.set_bottom(hB.reshape(-1))
+    qd = torch.tensor(q.reshape(-1), device="cuda")
+    F = ctx.rhs(qd).cpu().numpy()
+    err = scaled_err_per_var(F, osw.rhs_real(g, q), term_scale(g, q))
+    assert max(err) < TOL_RHS, err
+    v = scaled_direction(q, 3)
+    Jv = ctx.jvp(qd, torch.tensor(v.reshape(-1), device="cuda")).cpu().numpy()
+    err = scaled_err_per_var(Jv, osw.jvp(g, q, v), term_scale(g, q, v))
+    assert max(err) < TOL_JVP, err

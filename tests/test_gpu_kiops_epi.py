@@ -1,0 +1,65 @@
+"""GPU parity of the phi-function solver (Eq. 29) and of multistep EPI steps
+(Eq. 34-38) against the oracle."""
+import numpy as np
+import pytest
+
+from oracle import epi as oepi
+from oracle import kiops as okiops
+from oracle import shallow_water as osw
+from tests.gpu_common import oracle_case, rel_l2_per_var, scaled_direction
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _ctx(g):
+    from paper_2101_05617_gb300.swepi import SWContext
+    return SWContext(g.ne, g.ns - 1, g.rotation)
+
+
+@pytest.mark.parametrize("ne,ns,nb,dt,tol", [(2, 4, 2, 900.0, 1e-12), (3, 4, 4, 1800.0, 1e-10),
+                                             (4, 4, 5, 900.0, 1e-12)])
+def test_kiops_parity(ne, ns, nb, dt, tol):
+    _, g, q, _ = oracle_case(ne, ns, seed=ne)
+    F = osw.rhs_real(g, q)
+    bs = [None, dt * F] + [1e-3 * dt * scaled_direction(q, 50 + k) for k in range(nb - 2)]
+    ctx = _ctx(g)
+    qd = torch.tensor(q.reshape(-1), device="cuda")
+    bd = [None if b is None else torch.tensor(b.reshape(-1), device="cuda") for b in bs]
+    w, st = ctx.kiops_phi(qd, dt, bd, tol=tol)
+    tr = []
+    ref, rst = okiops.kiops(1.0, lambda x: dt * osw.jvp(g, q, x.reshape(q.shape)).reshape(-1),
+                            [np.zeros(q.size)] + [b.reshape(-1) for b in bs[1:]], tol=tol, trace=tr)
+    err = rel_l2_per_var(w.cpu().numpy(), ref)
+    assert max(err) < 1e-10, (err, st, rst)
+    assert st["krylov_iters"] == rst["krylov_iters"] and st["substeps"] == rst["substeps"], (st, rst)
+
+
+def test_kiops_zero_operator_closed_form():
+    """dt = 0 makes the operator zero: w = sum_k b_k / k! exactly (Eq. 26 at 0)."""
+    _, g, q, _ = oracle_case(2, 3, seed=2)
+    ctx = _ctx(g)
+    qd = torch.tensor(q.reshape(-1), device="cuda")
+    bs = [torch.tensor(scaled_direction(q, k).reshape(-1), device="cuda") for k in range(4)]
+    w, st = ctx.kiops_phi(qd, 0.0, bs, tol=1e-13)
+    ref = bs[0] + bs[1] + bs[2] / 2 + bs[3] / 6
+    assert torch.linalg.norm(w - ref) < 1e-11 * torch.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("order,steps", [(4, 10), (5, 5), (6, 6), (3, 4), (2, 3)])
+def test_epi_parity_small(order, steps):
+    """The small configuration (6 x 4 x 4 elements, p = 3, EPI4, tol 1e-12,
+    dt = 900 s, 10 steps) and the other orders: GPU trajectory vs oracle
+    trajectory, relative L2 per variable <= 1e-11."""
+    _, g, q, _ = oracle_case(4, 4, seed=0)
+    dt, tol = 900.0, 1e-12
+    ctx = _ctx(g)
+    qd = torch.tensor(q.reshape(-1), device="cuda")
+    it = oepi.EPI(lambda x: osw.rhs_real(g, x.reshape(q.shape)).reshape(-1),
+                  lambda x, v: osw.jvp(g, x.reshape(q.shape), v.reshape(q.shape)).reshape(-1), order, tol=tol)
+    y = q.reshape(-1).copy()
+    for k in range(steps):
+        st = ctx.epi_step(order, dt, qd, tol=tol)
+        y = it.step(y, dt)
+    err = rel_l2_per_var(qd.cpu().numpy(), y)
+    assert max(err) < 1e-11, err
