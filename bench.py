@@ -1,0 +1,323 @@
+#!/usr/bin/env python
+"""Benchmark of the hot path: multistep EPI steps of the DFR shallow-water
+model on the rotated cubed sphere, with complex-step JVPs inside the adaptive
+Krylov phi-function solver (arXiv 2101.05617, Sec. 3-4).
+
+Workload (default): 6 x 60 x 60 elements, p = 5 (2,332,800 unknowns), EPI5,
+dt = 1800 s, KIOPS tolerance 1e-10, seeded synthetic fields (degree <= 4
+spherical-harmonic height around 8 km, geostrophic wind, seeded rotation).
+A step = one EPI5 step (RHS, remainder JVPs, one KIOPS call with its JVPs,
+orthogonalisation and exponentials, assembly).  The first P = 3 steps of the
+run are EPI2 start-up steps and fall in the warm-up.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line on rank 0.  Multi-GPU runs are independent replicas (one
+per GPU, seed offset by rank): the path has no exchange step at one replica per
+GPU; value = steps of all ranks / slowest rank's time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "EPI steps/s and JVP DOF/s at n_e=60,p=5 vs plain FP64 GPU path, same error"
+UNIT = "EPI steps/s"
+
+
+def flops_per_jvp(ne, ns):
+    """Algorithmic FP64 flops of one complex-step JVP (first-order complex
+    arithmetic, add/mul/div/sqrt = 1, fma = 2), split into the volume and the
+    face-flux kernels; the per-node and per-interface-point counts are derived
+    operation by operation in the design doc."""
+    nodes = 6 * ne * ne * ns * ns
+    facepts = 12 * ne * ne * ns
+    return nodes * (108 + 12 * ns), facepts * (30 * ns + 182)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="ne60_p5")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if torch.cuda.is_available() and args.impl == "gpu" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def aggregate(pg, elapsed_ms, steps, device=None):
+    """(max elapsed over ranks, total steps over ranks): value = total / max."""
+    if pg is None:
+        return elapsed_ms, steps
+    import torch
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+    s = torch.tensor([float(steps)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    pg.all_reduce(s, op=pg.ReduceOp.SUM)
+    return float(t.item()), int(s.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(wl, seed, krylov_per_step, P, budget_s=15.0):
+    """The CPU oracle, as it stands, on a bounded sample of the same workload:
+    its complex-step JVP and RHS at full size, timed until ~budget_s, projected
+    to EPI steps/s with the Krylov iterations per step the GPU path took."""
+    import numpy as np
+
+    from oracle import fields as ofields
+    from oracle import shallow_water as osw
+    from paper_2101_05617_gb300 import synth
+    f = synth.make_fields(wl, seed)
+    g = osw.Grid(wl.ne, wl.ns, f.rotation)
+    h, hB, V = f.evaluate(g.node_xyz())
+    q = ofields.state_from_fields(g, h, hB, V)
+    v = synth.random_perturbation(q.size, seed + 1).reshape(q.shape)
+    t0 = time.perf_counter()
+    osw.rhs_real(g, q)
+    t_rhs = time.perf_counter() - t0
+    n_jvp, t_jvp = 0, 0.0
+    while t_jvp < budget_s or n_jvp < 2:
+        t0 = time.perf_counter()
+        osw.jvp(g, q, v)
+        t_jvp += time.perf_counter() - t0
+        n_jvp += 1
+    t_one = t_jvp / n_jvp
+    x = np.random.default_rng(0).standard_normal(q.size)
+    y = np.random.default_rng(1).standard_normal(q.size)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        hh = np.dot(x, y)
+        y = y - hh * x
+        y = y / np.linalg.norm(y)
+    t_orth = (time.perf_counter() - t0) / 3 * 2     # two window vectors per iteration
+    step_s = (krylov_per_step + P) * t_one + krylov_per_step * t_orth + t_rhs
+    return {"value": 1.0 / step_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"{n_jvp} oracle complex-step JVPs ({t_one:.2f} s each) + 1 RHS + 3 orthogonalisation "
+                       f"updates at n_e={wl.ne}, p={wl.p}; EPI{wl.order} step projected as "
+                       f"({krylov_per_step:.0f} Krylov + {P} remainder) JVPs + orthogonalisation + RHS"),
+            "jvp_dof_per_s": wl.n_unknowns / t_one}
+
+
+# Krylov iterations per EPI5 step of the GPU path on the default workload
+# (measured; used only to project the oracle's step time in --impl reference).
+KRYLOV_PER_STEP_NE60_P5 = 416.0
+
+
+def run_reference(args, world, rank):
+    from paper_2101_05617_gb300 import synth
+    if rank != 0:
+        return
+    wl = synth.WORKLOADS[args.workload]
+    P = {2: 0, 3: 1, 4: 2, 5: 3, 6: 4}[wl.order]
+    times = []
+    sample = None
+    for k in range(args.warmup + args.steps):
+        s = oracle_sample(wl, args.seed, KRYLOV_PER_STEP_NE60_P5, P, budget_s=3.0)
+        if k >= args.warmup:
+            times.append(1.0 / s["value"])
+            sample = s
+    step_s = statistics.mean(times)
+    value = 1.0 / step_s
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{wl.name}: 6x{wl.ne}x{wl.ne} elements, p={wl.p}, EPI{wl.order}, "
+                                  f"dt={wl.dt:g} s, KIOPS tol {wl.tol:g}", "parallelism": "replicas"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": sample["sample"] if sample else ""},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "jvp_dof_per_s": sample["jvp_dof_per_s"] if sample else None}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        if pg is not None:
+            pg.barrier()
+            pg.destroy_process_group()
+        return
+    import numpy as np
+    import torch
+
+    from paper_2101_05617_gb300 import swepi, synth
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = synth.WORKLOADS[args.workload]
+    P = {2: 0, 3: 1, 4: 2, 5: 3, 6: 4}[wl.order]
+    f = synth.make_fields(wl, args.seed + rank)
+    ctx = swepi.SWContext(wl.ne, wl.p, f.rotation)
+    h, hB, V = f.evaluate(ctx.node_xyz())
+    q_host = ctx.state_from_fields(h, hB, V)
+    q = torch.tensor(q_host, device=dev)
+    opts = dict(tol=wl.tol)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        ctx.epi_step(wl.order, wl.dt, q, **opts)
+    torch.cuda.synchronize()
+
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local if world > 1 else 0]
+    clocks = ClockSampler(gpu_index)
+    krylov = 0
+    if pg is not None:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ctx.profile(True)
+    launches0 = ctx.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        st = ctx.epi_step(wl.order, wl.dt, q, **opts)
+        krylov += st["krylov_iters"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if pg is not None:
+        pg.barrier()
+    elapsed_ms = e0.elapsed_time(e1)
+    clock_info = clocks.stop()
+    launches = ctx.kernel_launches() - launches0
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    max_ms, total_steps = aggregate(pg, elapsed_ms, args.steps, dev if pg is not None else None)
+
+    # end to end through the public API with host buffers: per step the state is
+    # copied in from pinned host memory and the result read back
+    q_pin = torch.from_numpy(q.cpu().numpy()).pin_memory()
+    if pg is not None:
+        pg.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        q.copy_(q_pin, non_blocking=True)
+        ctx.epi_step(wl.order, wl.dt, q, **opts)
+        q_pin.copy_(q, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_max, _ = aggregate(pg, e2e_s * 1e3, args.steps, dev if pg is not None else None)
+
+    if rank == 0:
+        ne, ns = wl.ne, wl.ns
+        fv, ff = flops_per_jvp(ne, ns)
+        vj, fj = prof["volume_jvp"], prof["face_jvp"]
+        t_vol = vj["ms"] / max(1, vj["count"]) * 1e-3
+        t_face = fj["ms"] / max(1, fj["count"]) * 1e-3
+        peak = swepi.sw_fp64_fma_peak()
+        dominant = "volume" if vj["ms"] >= fj["ms"] else "face"
+        if dominant == "volume":
+            achieved = fv / t_vol / 1e12
+        else:
+            achieved = ff / t_face / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": f"{dominant}_kernel<cs,{ns}> (complex-step JVP)",
+                    "peak_source": "FP64 FMA throughput measured live by sw_fp64_fma_peak (nominal 1.25)",
+                    "per_kernel": {"volume": {"flops": fv, "avg_ms": t_vol * 1e3, "launches": vj["count"],
+                                              "tflops": fv / t_vol / 1e12 if t_vol else None},
+                                   "face": {"flops": ff, "avg_ms": t_face * 1e3, "launches": fj["count"],
+                                            "tflops": ff / t_face / 1e12 if t_face else None},
+                                   "expm": {"avg_ms": prof["expm"]["ms"] / max(1, prof["expm"]["count"]),
+                                            "launches": prof["expm"]["count"]}},
+                    "share_of_step": {"jvp": (vj["ms"] + fj["ms"]) / elapsed_ms,
+                                      "expm": prof["expm"]["ms"] / elapsed_ms}}
+        t_jvp = t_vol + t_face
+        value = total_steps / (max_ms * 1e-3)
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": f"{wl.name}: 6x{ne}x{ne} elements, p={wl.p}, EPI{wl.order}, "
+                                      f"dt={wl.dt:g} s, KIOPS tol {wl.tol:g}, complex-step eps {wl.eps:g}",
+                          "n_unknowns": wl.n_unknowns, "parallelism": "replicas" if world > 1 else "single",
+                          "l2": "inputs larger than L2 (Krylov basis ~2.4 GB per KIOPS call)"},
+               "jvp_dof_per_s": wl.n_unknowns / t_jvp,
+               "jvp_dof_per_s_total": world * wl.n_unknowns / t_jvp,
+               "krylov_iters_per_step": krylov / args.steps,
+               "clocks": clock_info,
+               "e2e": {"value": total_steps / (e2e_max * 1e-3), "unit": UNIT,
+                       "h2d_bytes_per_step": 8 * wl.n_unknowns, "d2h_bytes_per_step": 8 * wl.n_unknowns},
+               "gpu_launches": launches,
+               "roofline": roofline}
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = oracle_sample(wl, args.seed, krylov / args.steps, P)
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -142,6 +142,25 @@ int sw_epi_reset(sw_ctx_t ctx);
 /* Number of kernels the library launched since the context was created. */
 long long sw_kernel_launches(sw_ctx_t ctx);
 
+/* Kernel timing (tracing aid; the paper has no counterpart).  While enabled,
+ * the library brackets its face-flux, volume and small-exponential kernels with
+ * CUDA events recorded on the launch stream; sw_profile_read() waits for the
+ * pending events and returns per-family launch counts and summed device
+ * milliseconds since the last sw_profile(ctx, 1).  kind: 0 = face flux (JVP),
+ * 1 = volume (JVP), 2 = face flux (RHS), 3 = volume (RHS), 4 = exponential. */
+#define SW_PROF_KINDS 5
+typedef struct {
+  long long count[SW_PROF_KINDS];
+  double ms[SW_PROF_KINDS];
+} sw_profile_stats;
+int sw_profile(sw_ctx_t ctx, int enable);
+int sw_profile_read(sw_ctx_t ctx, sw_profile_stats* out);
+
+/* Measured FP64 fused-multiply-add throughput of the current device in
+ * TFLOP/s (2 flops per FMA), from a register-resident FMA-chain kernel: the
+ * ALU roofline of the FP64 path (the paper has no counterpart). */
+int sw_fp64_fma_peak(double* tflops);
+
 /* Human-readable name of a status code (static storage). */
 const char* sw_status_str(int status);
 

@@ -2,6 +2,7 @@
 // life cycle and the multistep EPI driver (Eq. 25, 30, 34-38).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -123,7 +124,73 @@ int epi2_inplace(Ctx& c, double* q, const double* F, double h, const sw_kiops_op
 
 }  // namespace
 
+namespace swepi {
+cudaEvent_t prof_event(Ctx& c) {
+  if (c.prof_pool.empty()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+  cudaEvent_t e = c.prof_pool.back();
+  c.prof_pool.pop_back();
+  return e;
+}
+void prof_record(Ctx& c, int kind, cudaEvent_t a, cudaEvent_t b) {
+  c.prof_pending.push_back({kind, a, b});
+  if (c.prof_pending.size() > 30000) prof_drain(c);
+}
+void prof_drain(Ctx& c) {
+  std::vector<cudaEvent_t> seen;
+  for (const Ctx::ProfRec& r : c.prof_pending) {
+    if (cudaEventSynchronize(r.b) == cudaSuccess) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+        c.prof_count[r.kind]++;
+        c.prof_ms[r.kind] += ms;
+      }
+    }
+    seen.push_back(r.a);
+    seen.push_back(r.b);
+  }
+  c.prof_pending.clear();
+  // events are shared between consecutive records: return each once
+  std::sort(seen.begin(), seen.end());
+  seen.erase(std::unique(seen.begin(), seen.end()), seen.end());
+  for (cudaEvent_t e : seen) c.prof_pool.push_back(e);
+}
+}  // namespace swepi
+
 extern "C" {
+
+int sw_profile(sw_ctx_t c, int enable) {
+  if (!c) return SW_EINVAL;
+  prof_drain(*c);
+  c->prof = enable != 0;
+  for (int k = 0; k < 5; ++k) {
+    c->prof_count[k] = 0;
+    c->prof_ms[k] = 0.0;
+  }
+  return SW_OK;
+}
+
+int sw_profile_read(sw_ctx_t c, sw_profile_stats* out) {
+  if (!c || !out) return SW_EINVAL;
+  prof_drain(*c);
+  for (int k = 0; k < SW_PROF_KINDS; ++k) {
+    out->count[k] = c->prof_count[k];
+    out->ms[k] = c->prof_ms[k];
+  }
+  return SW_OK;
+}
+
+int sw_fp64_fma_peak(double* tflops) {
+  if (!tflops) return SW_EINVAL;
+  double t = fp64_fma_peak_tflops();
+  if (!(t > 0)) return SW_ECUDA;
+  *tflops = t;
+  return SW_OK;
+}
+
 
 const char* sw_status_str(int status) {
   switch (status) {
@@ -175,6 +242,8 @@ void sw_free(sw_ctx_t c) {
   if (c->d_lines) cudaFree(c->d_lines);
   if (c->d_flags) cudaFree(c->d_flags);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  prof_drain(*c);
+  for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   delete c;
 }
 

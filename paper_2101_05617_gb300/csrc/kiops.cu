@@ -45,7 +45,10 @@ int read_back(Ctx& c, cudaStream_t s) {
   if (e != cudaSuccess) return SW_ECUDA;
   e = cudaMemcpyAsync(c.h_pinned + 32, c.d_flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return SW_ECUDA;
-  return cuda_status(cudaStreamSynchronize(s));
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return SW_ECUDA;
+  if (c.prof) prof_drain(c);
+  return SW_OK;
 }
 const int* pinned_flags(const Ctx& c) { return reinterpret_cast<const int*>(c.h_pinned + 32); }
 

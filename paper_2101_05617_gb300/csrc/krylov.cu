@@ -309,7 +309,48 @@ int blocks_for(long long n, int threads) {
   return (int)b;
 }
 
+// FP64 FMA throughput probe: 8 independent FMA chains per thread, registers only
+__global__ void fma_probe_kernel(double* out, int iters, double a, double b) {
+  double x[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) x[c] = threadIdx.x + c;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = fma(x[c], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) s += x[c];
+  if (s == 12345.678) out[0] = s;   // keeps the chains live; never true in practice
+}
+
 }  // namespace
+
+double fp64_fma_peak_tflops() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  double* out = nullptr;
+  if (cudaMalloc(&out, sizeof(double)) != cudaSuccess) return -1.0;
+  const int blocks = sms * 4, threads = 256, iters = 4096;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int w = 0; w < 3; ++w) fma_probe_kernel<<<blocks, threads>>>(out, iters, 0.999, 0.001);
+  cudaEventRecord(e0);
+  const int reps = 5;
+  for (int r = 0; r < reps; ++r) fma_probe_kernel<<<blocks, threads>>>(out, iters, 0.999, 0.001);
+  cudaEventRecord(e1);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (cudaGetLastError() != cudaSuccess || ms <= 0.f) return -1.0;
+  double fmas = (double)blocks * threads * iters * 8.0 * reps;
+  return 2.0 * fmas / (ms * 1e-3) / 1e12;
+}
 
 int launch_dot(Ctx& c, const double* x, const double* y, long long n, double* dst, const int* skip, cudaStream_t s) {
   RedOut o{dst, 0.0, nullptr, 0};
@@ -384,8 +425,18 @@ int launch_expm_hess(Ctx& c, int j, double tau, double tau_happy, cudaStream_t s
   for (int k = 1; k <= m; ++k) pd.b[k] = pd.b[k - 1] * (double)(m - k + 1) / ((double)k * (double)(2 * m - k + 1));
   // the b_k above are normalised to b_0 = 1 (Higham's table scales them by 26!/13!)
   pd.theta13 = 5.371920351148152;  // Higham (2005), Table 2.3
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c.prof) {
+    e0 = prof_event(c);
+    e1 = prof_event(c);
+    cudaEventRecord(e0, s);
+  }
   expm_kernel<<<1, EXPM_THREADS, 0, s>>>(c.d_H, c.ldh, j, tau, tau_happy, c.d_flags, c.d_F, c.d_expm_ws,
                                          c.d_scal + 8, pd);
+  if (c.prof) {
+    cudaEventRecord(e1, s);
+    prof_record(c, PK_EXPM, e0, e1);
+  }
   c.launches++;
   return cuda_status(cudaGetLastError());
 }

@@ -97,7 +97,20 @@ struct Ctx {
   int hist_head = 0;              // slot of the most recent entry
   int m_warm = 0;                 // KIOPS warm start (0 = none)
   long long launches = 0;
+  // event profiling (sw_profile)
+  bool prof = false;
+  struct ProfRec { int kind; cudaEvent_t a, b; };
+  std::vector<ProfRec> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;
+  long long prof_count[5] = {};
+  double prof_ms[5] = {};
 };
+
+// event profiling helpers (capi.cu)
+cudaEvent_t prof_event(Ctx& c);
+void prof_record(Ctx& c, int kind, cudaEvent_t a, cudaEvent_t b);
+void prof_drain(Ctx& c);
+enum ProfKind { PK_FACE_JVP = 0, PK_VOL_JVP = 1, PK_FACE_RHS = 2, PK_VOL_RHS = 3, PK_EXPM = 4 };
 
 // ---- geometry / tables (geom.cpp)
 int build_tables(Ctx& c);
@@ -133,6 +146,7 @@ int launch_scale_inv(Ctx& c, double* y, const double* x, const double* s_dev, lo
                      const int* skip, cudaStream_t s);
 int launch_expm_hess(Ctx& c, int j, double tau, double tau_happy, cudaStream_t s);
 int launch_combine(Ctx& c, int j, long long n, cudaStream_t s);
+double fp64_fma_peak_tflops();
 int launch_set_tail(Ctx& c, double* x, long long n, int p, const double* vals, cudaStream_t s);
 int launch_lincomb(Ctx& c, double* out, long long n, int k, const double* const* xs,
                    const double* coef, cudaStream_t s);

@@ -39,6 +39,15 @@ class sw_kiops_opts(ctypes.Structure):
                 ("m_max", ctypes.c_int), ("iop", ctypes.c_int), ("tau_init", ctypes.c_double)]
 
 
+class sw_profile_stats(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_longlong * 5), ("ms", ctypes.c_double * 5)]
+
+    KINDS = ("face_jvp", "volume_jvp", "face_rhs", "volume_rhs", "expm")
+
+    def as_dict(self):
+        return {k: {"count": int(self.count[i]), "ms": float(self.ms[i])} for i, k in enumerate(self.KINDS)}
+
+
 class sw_kiops_stats(ctypes.Structure):
     _fields_ = [("substeps", ctypes.c_int), ("rejects", ctypes.c_int), ("krylov_iters", ctypes.c_int),
                 ("m_final", ctypes.c_int), ("tau_final", ctypes.c_double), ("err_last", ctypes.c_double)]
@@ -78,6 +87,9 @@ def lib():
     L.sw_epi_reset.argtypes = [vp]
     L.sw_kernel_launches.argtypes = [vp]
     L.sw_kernel_launches.restype = ll
+    L.sw_profile.argtypes = [vp, ip]
+    L.sw_profile_read.argtypes = [vp, ctypes.POINTER(sw_profile_stats)]
+    L.sw_fp64_fma_peak.argtypes = [dp]
     L.sw_status_str.argtypes = [ip]
     L.sw_status_str.restype = ctypes.c_char_p
     _lib = L
@@ -86,7 +98,8 @@ def lib():
 
 EXPORTED = ["sw_init", "sw_free", "sw_num_unknowns", "sw_grid_info", "sw_node_xyz", "sw_state_from_fields",
             "sw_set_bottom", "sw_rhs", "sw_jvp", "sw_kiops_phi", "sw_epi_step", "sw_epi_set_history",
-            "sw_epi_reset", "sw_kernel_launches", "sw_status_str"]
+            "sw_epi_reset", "sw_kernel_launches", "sw_profile", "sw_profile_read", "sw_fp64_fma_peak",
+            "sw_status_str"]
 
 
 def _check(call, rc):
@@ -204,6 +217,22 @@ def sw_kernel_launches(ctx):
     return int(lib().sw_kernel_launches(ctx))
 
 
+def sw_profile(ctx, enable=True):
+    _check("sw_profile", lib().sw_profile(ctx, 1 if enable else 0))
+
+
+def sw_profile_read(ctx):
+    st = sw_profile_stats()
+    _check("sw_profile_read", lib().sw_profile_read(ctx, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def sw_fp64_fma_peak():
+    t = ctypes.c_double()
+    _check("sw_fp64_fma_peak", lib().sw_fp64_fma_peak(ctypes.byref(t)))
+    return t.value
+
+
 def sw_status_str(status):
     return lib().sw_status_str(int(status)).decode()
 
@@ -266,3 +295,9 @@ class SWContext:
 
     def kernel_launches(self):
         return sw_kernel_launches(self.handle)
+
+    def profile(self, enable=True):
+        sw_profile(self.handle, enable)
+
+    def profile_read(self):
+        return sw_profile_read(self.handle)
