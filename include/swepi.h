@@ -46,6 +46,7 @@ extern "C" {
 #define SW_EKRYLOV (-4)     /* phi-function solver hit its substep/rejection cap */
 #define SW_ETIMEOUT (-5)    /* a bounded device-side wait gave up */
 #define SW_ENONFINITE (-6)  /* NaN/Inf met where a finite value is required */
+#define SW_ESCRATCH (-7)    /* grid too large for the fixed scratch of sw_jvp_static_scratch */
 
 typedef struct sw_ctx* sw_ctx_t;
 
@@ -114,6 +115,22 @@ int sw_rhs(sw_ctx_t ctx, const double* q_dev, double* F_dev, void* stream);
  * eps > 0 (1e-30 is typical).  Jv_dev may not alias q_dev or v_dev. */
 int sw_jvp(sw_ctx_t ctx, const double* q_dev, const double* v_dev, double eps,
            double* Jv_dev, void* stream);
+
+/* The same product as sw_jvp for callers that may not allocate device memory
+ * while running (an application whose memory manager owns the device memory
+ * and forbids other libraries from calling cudaMalloc, a plug-in host without
+ * allocation rights, a loop that cannot take cudaMalloc's implicit
+ * synchronisation).  The paper has no counterpart: this is a deployment
+ * variant.  It allocates nothing; its interface-flux scratch is a fixed
+ * 16 MiB device array inside the library (held by every GPU that loads the
+ * library until exit), so it serves grids with 6 n_e^2 * 12 * (p+1) <= 2^21
+ * (e.g. n_e = 60, p = 5) and returns SW_ESCRATCH for larger ones.  The first
+ * call on a device looks up the array's device address (once per device, for
+ * the current device); make that first call before any stream capture.  All
+ * calls share the array: calls that overlap on the GPU race.  Arguments and
+ * results as sw_jvp. */
+int sw_jvp_static_scratch(sw_ctx_t ctx, const double* q_dev, const double* v_dev, double eps,
+                          double* Jv_dev, void* stream);
 
 /* w = sum_{k=0}^{nb-1} tau_out^k phi_k(tau_out dt J(q_lin)) b_k (Eq. 29), J by
  * the complex-step product above.  b_dev_host: host array of nb device

@@ -201,6 +201,7 @@ const char* sw_status_str(int status) {
     case SW_EKRYLOV: return "Krylov solver substep or rejection limit reached";
     case SW_ETIMEOUT: return "bounded device wait timed out";
     case SW_ENONFINITE: return "non-finite value";
+    case SW_ESCRATCH: return "grid larger than the fixed scratch of sw_jvp_static_scratch";
     default: return "unknown status";
   }
 }

@@ -340,6 +340,36 @@ static int launch_any(Ctx& c, const double* q, const double* v, double eps, doub
   }
 }
 
+template <int NS>
+static int launch_fb_ns(Ctx& c, const double* q, const double* v, double eps, double* out, double* fb,
+                        cudaStream_t s) {
+  FaceArgs fa{q, v, eps, c.nodes, c.d_lines, c.d_face_coef, c.nfacepts, fb, nullptr};
+  const int fthreads = 128;
+  const long long fblocks = (c.nfacepts + fthreads - 1) / fthreads;
+  face_flux_kernel<cs, NS><<<(unsigned)fblocks, fthreads, 0, s>>>(fa, c.dc);
+  AugEpilogue ep;
+  VolArgs va{q, v, eps, c.nodes, c.nelem, c.d_node_coef, fb, out, ep};
+  const long long vblocks = (c.nelem + VolShape<NS>::EPB - 1) / VolShape<NS>::EPB;
+  volume_kernel<cs, NS><<<(unsigned)vblocks, VolShape<NS>::THREADS, 0, s>>>(va, c.dc);
+  c.launches += 2;
+  return cuda_status(cudaGetLastError());
+}
+
+int launch_jvp_fb(Ctx& c, const double* q, const double* v, double eps, double* out, double* fb,
+                  cudaStream_t s) {
+  switch (c.ns) {
+    case 1: return launch_fb_ns<1>(c, q, v, eps, out, fb, s);
+    case 2: return launch_fb_ns<2>(c, q, v, eps, out, fb, s);
+    case 3: return launch_fb_ns<3>(c, q, v, eps, out, fb, s);
+    case 4: return launch_fb_ns<4>(c, q, v, eps, out, fb, s);
+    case 5: return launch_fb_ns<5>(c, q, v, eps, out, fb, s);
+    case 6: return launch_fb_ns<6>(c, q, v, eps, out, fb, s);
+    case 7: return launch_fb_ns<7>(c, q, v, eps, out, fb, s);
+    case 8: return launch_fb_ns<8>(c, q, v, eps, out, fb, s);
+    default: return SW_EINVAL;
+  }
+}
+
 int launch_rhs(Ctx& c, const double* q, double* F, cudaStream_t s) {
   AugEpilogue ep;
   return launch_any<double>(c, q, nullptr, 1.0, F, ep, s);

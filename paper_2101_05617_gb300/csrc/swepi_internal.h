@@ -132,6 +132,9 @@ struct AugEpilogue {
 int launch_rhs(Ctx& c, const double* q, double* F, cudaStream_t s);
 int launch_jvp(Ctx& c, const double* q, const double* v, double eps, double* out,
                const AugEpilogue& ep, cudaStream_t s);
+// the JVP with a caller-supplied interface-flux buffer (nelem * 12 * ns doubles)
+int launch_jvp_fb(Ctx& c, const double* q, const double* v, double eps, double* out, double* fb,
+                  cudaStream_t s);
 
 // ---- Krylov kernels (krylov.cu)
 constexpr int RED_BLOCKS = 456;   // 3 x 152 SMs

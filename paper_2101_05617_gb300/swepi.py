@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libswepi.so")
 
 SW_OK = 0
 STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA error",
-          -4: "Krylov solver limit", -5: "device wait timed out", -6: "non-finite value"}
+          -4: "Krylov solver limit", -5: "device wait timed out", -6: "non-finite value",
+          -7: "grid larger than the fixed scratch of sw_jvp_static_scratch"}
 
 
 class SWError(RuntimeError):
@@ -79,6 +80,7 @@ def lib():
     L.sw_set_bottom.argtypes = [vp, vp]
     L.sw_rhs.argtypes = [vp, vp, vp, vp]
     L.sw_jvp.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp]
+    L.sw_jvp_static_scratch.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp]
     L.sw_kiops_phi.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, ip, ctypes.POINTER(vp),
                                ctypes.POINTER(sw_kiops_opts), vp, ctypes.POINTER(sw_kiops_stats), vp]
     L.sw_epi_step.argtypes = [vp, ip, ctypes.c_double, vp, ctypes.POINTER(sw_kiops_opts),
@@ -97,7 +99,7 @@ def lib():
 
 
 EXPORTED = ["sw_init", "sw_free", "sw_num_unknowns", "sw_grid_info", "sw_node_xyz", "sw_state_from_fields",
-            "sw_set_bottom", "sw_rhs", "sw_jvp", "sw_kiops_phi", "sw_epi_step", "sw_epi_set_history",
+            "sw_set_bottom", "sw_rhs", "sw_jvp", "sw_jvp_static_scratch", "sw_kiops_phi", "sw_epi_step", "sw_epi_set_history",
             "sw_epi_reset", "sw_kernel_launches", "sw_profile", "sw_profile_read", "sw_fp64_fma_peak",
             "sw_status_str"]
 
@@ -182,6 +184,14 @@ def sw_jvp(ctx, q, v, eps, Jv, stream=None):
     n = sw_num_unknowns(ctx)
     _check("sw_jvp", lib().sw_jvp(ctx, _dev_ptr(q, n), _dev_ptr(v, n), float(eps), _dev_ptr(Jv, n),
                                   _stream(stream)))
+
+
+def sw_jvp_static_scratch(ctx, q, v, eps, Jv, stream=None):
+    """sw_jvp for callers that may not allocate device memory while running;
+    the interface-flux scratch is a fixed 16 MiB array inside the library."""
+    n = sw_num_unknowns(ctx)
+    _check("sw_jvp_static_scratch", lib().sw_jvp_static_scratch(ctx, _dev_ptr(q, n), _dev_ptr(v, n), float(eps),
+                                                                _dev_ptr(Jv, n), _stream(stream)))
 
 
 def sw_kiops_phi(ctx, q_lin, dt, tau_out, b, w, opts=None, stream=None):
