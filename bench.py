@@ -231,6 +231,7 @@ def main():
     gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local if world > 1 else 0]
     clocks = ClockSampler(gpu_index)
     krylov = 0
+    krylov_list = []
     if pg is not None:
         pg.barrier()
     torch.cuda.synchronize()
@@ -243,6 +244,7 @@ def main():
     for _ in range(args.steps):
         st = ctx.epi_step(wl.order, wl.dt, q, **opts)
         krylov += st["krylov_iters"]
+        krylov_list.append(st["krylov_iters"])
     e1.record(stream)
     torch.cuda.synchronize()
     if pg is not None:
@@ -305,6 +307,7 @@ def main():
                "jvp_dof_per_s": wl.n_unknowns / t_jvp,
                "jvp_dof_per_s_total": world * wl.n_unknowns / t_jvp,
                "krylov_iters_per_step": krylov / args.steps,
+               "krylov_iters_each_step": krylov_list,
                "clocks": clock_info,
                "e2e": {"value": total_steps / (e2e_max * 1e-3), "unit": UNIT,
                        "h2d_bytes_per_step": 8 * wl.n_unknowns, "d2h_bytes_per_step": 8 * wl.n_unknowns},

@@ -132,6 +132,20 @@ int sw_jvp(sw_ctx_t ctx, const double* q_dev, const double* v_dev, double eps,
 int sw_jvp_static_scratch(sw_ctx_t ctx, const double* q_dev, const double* v_dev, double eps,
                           double* Jv_dev, void* stream);
 
+/* Split evaluation of the complex-step product (Eq. 28) for many v at one q:
+ * sw_linearize evaluates the real half of F(q + i eps v) -- every quantity that
+ * depends on q alone -- and stores the coefficients of the imaginary half
+ * (library-owned, allocated on first use); sw_jvp_linearized then returns
+ * Im F(q + i eps v)/eps for the last linearised q by propagating imaginary
+ * parts only.  Equal to sw_jvp up to rounding.  Jv_dev may not alias v_dev. */
+int sw_linearize(sw_ctx_t ctx, const double* q_dev, void* stream);
+int sw_jvp_linearized(sw_ctx_t ctx, const double* v_dev, double* Jv_dev, void* stream);
+
+/* How sw_kiops_phi and sw_epi_step evaluate their JVPs: 0 = sw_jvp per Krylov
+ * vector, 1 = sw_linearize once per linearisation point then
+ * sw_jvp_linearized (default). */
+int sw_set_jvp_mode(sw_ctx_t ctx, int mode);
+
 /* w = sum_{k=0}^{nb-1} tau_out^k phi_k(tau_out dt J(q_lin)) b_k (Eq. 29), J by
  * the complex-step product above.  b_dev_host: host array of nb device
  * pointers (1 <= nb <= 8); a NULL entry means a zero vector.  w_dev: n
@@ -164,8 +178,9 @@ long long sw_kernel_launches(sw_ctx_t ctx);
  * CUDA events recorded on the launch stream; sw_profile_read() waits for the
  * pending events and returns per-family launch counts and summed device
  * milliseconds since the last sw_profile(ctx, 1).  kind: 0 = face flux (JVP),
- * 1 = volume (JVP), 2 = face flux (RHS), 3 = volume (RHS), 4 = exponential. */
-#define SW_PROF_KINDS 5
+ * 1 = volume (JVP), 2 = face flux (RHS), 3 = volume (RHS), 4 = exponential,
+ * 5 = linearisation of the split JVP. */
+#define SW_PROF_KINDS 6
 typedef struct {
   long long count[SW_PROF_KINDS];
   double ms[SW_PROF_KINDS];

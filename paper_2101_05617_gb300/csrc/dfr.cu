@@ -26,109 +26,10 @@
 // (AUSM's |M| <= 1, max/min) test the real part, ties going to the <= 0 side.
 #include <cuda_runtime.h>
 
+#include "dfr_device.cuh"
 #include "swepi_internal.h"
 
 namespace swepi {
-
-struct cs {
-  double re, im;
-};
-__device__ __forceinline__ cs operator+(cs a, cs b) { return {a.re + b.re, a.im + b.im}; }
-__device__ __forceinline__ cs operator-(cs a, cs b) { return {a.re - b.re, a.im - b.im}; }
-__device__ __forceinline__ cs operator*(cs a, cs b) { return {a.re * b.re, fma(a.re, b.im, a.im * b.re)}; }
-__device__ __forceinline__ cs operator*(double k, cs a) { return {k * a.re, k * a.im}; }
-__device__ __forceinline__ cs operator+(cs a, double k) { return {a.re + k, a.im}; }
-__device__ __forceinline__ cs cs_rcp(cs a) {
-  double r = 1.0 / a.re;
-  return {r, -a.im * r * r};
-}
-__device__ __forceinline__ cs cs_div(cs a, cs b) {
-  double r = 1.0 / b.re;
-  double qr = a.re * r;
-  return {qr, (a.im - qr * b.im) * r};
-}
-__device__ __forceinline__ cs cs_sqrt(cs a) {
-  double s = sqrt(a.re);
-  return {s, a.im * (0.5 / s)};
-}
-__device__ __forceinline__ double re(cs a) { return a.re; }
-__device__ __forceinline__ double im(cs a) { return a.im; }
-__device__ __forceinline__ cs mk(double r, double i, cs*) { return {r, i}; }
-
-// real instantiation (the RHS): same code path on plain doubles
-__device__ __forceinline__ double cs_rcp(double a) { return 1.0 / a; }
-__device__ __forceinline__ double cs_div(double a, double b) { return a / b; }
-__device__ __forceinline__ double cs_sqrt(double a) { return sqrt(a); }
-__device__ __forceinline__ double re(double a) { return a; }
-__device__ __forceinline__ double im(double) { return 0.0; }
-__device__ __forceinline__ double mk(double r, double, double*) { return r; }
-
-// the part of a result the caller wants: the imaginary part for the JVP, the
-// value for the RHS
-__device__ __forceinline__ double part(cs a) { return a.im; }
-__device__ __forceinline__ double part(double a) { return a; }
-
-template <typename T>
-__device__ __forceinline__ T load_state(const double* __restrict__ q, const double* __restrict__ v, double eps,
-                                        long long i) {
-  return mk(__ldg(q + i), v ? eps * __ldg(v + i) : 0.0, (T*)nullptr);
-}
-
-// ---------------------------------------------------------------- AUSM
-// basic AUSM splittings (reading of App. D Eq. 138-139; [41] Eq. 6 and 8)
-template <typename T>
-__device__ __forceinline__ void ausm_side(const T q[3], int d, double ad, double p1, double p2, T& M, T A[3], T P[3]) {
-  T a = cs_sqrt(ad * q[0]);                       // a^d = sqrt(h^dd g_r H), App. E
-  T u = cs_div(q[d], q[0]);                       // u^d
-  M = cs_div(u, a);                               // Froude number
-  A[0] = a * q[0];                                // A^{mu d} = a q^mu
-  A[1] = a * q[1];
-  A[2] = a * q[2];
-  T q0sq = q[0] * q[0];
-  P[0] = 0.0 * q[0];
-  P[1] = p1 * q0sq;                               // P^{mu d} = g_r h^{mu d} (q^0)^2 / (2 sqrt g)
-  P[2] = p2 * q0sq;
-}
-
-template <typename T>
-__device__ __forceinline__ void ausm_flux(const T qL[3], const T qR[3], int d, double ad, double p1, double p2,
-                                          T flux[3]) {
-  T ML, MR, AL[3], AR[3], PL[3], PR[3];
-  ausm_side(qL, d, ad, p1, p2, ML, AL, PL);
-  ausm_side(qR, d, ad, p1, p2, MR, AR, PR);
-  // M+(M_L), beta+(M_L)
-  T mp, bp, mm, bm;
-  if (fabs(re(ML)) <= 1.0) {
-    T t = ML + 1.0;
-    mp = 0.25 * (t * t);
-    bp = (0.25 * (t * t)) * (2.0 * mk(1.0, 0.0, (T*)nullptr) - ML);
-  } else if (re(ML) > 0.0) {
-    mp = ML;
-    bp = mk(1.0, 0.0, (T*)nullptr);
-  } else {
-    mp = 0.0 * ML;
-    bp = 0.0 * ML;
-  }
-  // M-(M_R), beta-(M_R)
-  if (fabs(re(MR)) <= 1.0) {
-    T t = MR + (-1.0);
-    mm = -0.25 * (t * t);
-    bm = (0.25 * (t * t)) * (MR + 2.0);
-  } else if (re(MR) > 0.0) {
-    mm = 0.0 * MR;
-    bm = 0.0 * MR;
-  } else {
-    mm = MR;
-    bm = mk(1.0, 0.0, (T*)nullptr);
-  }
-  T Mh = mp + mm;
-  bool pos = re(Mh) > 0.0;
-#pragma unroll
-  for (int mu = 0; mu < 3; ++mu) {
-    T adv = pos ? Mh * AL[mu] : Mh * AR[mu];
-    flux[mu] = (adv + bp * PL[mu]) + bm * PR[mu];
-  }
-}
 
 // ---------------------------------------------------------------- face flux
 struct FaceArgs {
@@ -142,23 +43,6 @@ struct FaceArgs {
   double* fb;
   const int* skip;
 };
-
-template <typename T, int NS>
-__device__ __forceinline__ void trace(const double* __restrict__ q, const double* __restrict__ v, double eps,
-                                      long long nodes, int elem, int edge, int i, const DfrConst& dc, T out[3]) {
-  const long long base = (long long)elem * NS * NS;
-  const double* w = (edge == 0 || edge == 2) ? dc.lm : dc.lp;
-#pragma unroll
-  for (int var = 0; var < 3; ++var) {
-    T acc = mk(0.0, 0.0, (T*)nullptr);
-#pragma unroll
-    for (int k = 0; k < NS; ++k) {
-      long long idx = base + ((edge <= 1) ? (i * NS + k) : (k * NS + i)) + var * nodes;
-      acc = acc + w[k] * load_state<T>(q, v, eps, idx);
-    }
-    out[var] = acc;
-  }
-}
 
 template <typename T, int NS>
 __global__ void __launch_bounds__(128) face_flux_kernel(FaceArgs a, DfrConst dc) {
@@ -210,12 +94,6 @@ struct VolArgs {
   AugEpilogue ep;
 };
 
-template <int NS>
-struct VolShape {
-  static constexpr int EPB = (256 / (NS * NS)) > 0 ? (256 / (NS * NS)) : 1;
-  static constexpr int THREADS = EPB * NS * NS;
-};
-
 template <typename T, int NS>
 __global__ void __launch_bounds__(VolShape<NS>::THREADS) volume_kernel(VolArgs a, DfrConst dc) {
   constexpr int EPB = VolShape<NS>::EPB;
@@ -223,6 +101,8 @@ __global__ void __launch_bounds__(VolShape<NS>::THREADS) volume_kernel(VolArgs a
   if (a.ep.skip && *a.ep.skip) return;
   __shared__ double sF[EPB][2][3][NN];       // [dir][mu][k2*NS+k1]
   __shared__ double sB[EPB][4][3][NS];       // face fluxes [edge][mu][pt]
+  __shared__ double sD[NS][NS + 3];          // padded rows: distinct banks per k
+  for (int t = threadIdx.x; t < NS * (NS + 2); t += blockDim.x) sD[t / (NS + 2)][t % (NS + 2)] = dc.D[t / (NS + 2)][t % (NS + 2)];
   const int le = threadIdx.x / NN, node = threadIdx.x % NN;
   const long long elem = (long long)blockIdx.x * EPB + le;
   const bool active = elem < a.nelem;
@@ -264,35 +144,36 @@ __global__ void __launch_bounds__(VolShape<NS>::THREADS) volume_kernel(VolArgs a
     sF[le][1][2][node] = part(F22);
   }
   __syncthreads();
-  if (!active) return;
 
   // DFR sweeps: extended flux [F(-1), f_1..f_NS, F(+1)] per line (Eq. 11-14)
-  double res[3];
+  // this thread's rows of the derivative matrix, from shared memory into registers
+  // (a per-thread row index into the constant bank would serialise the warp)
+  double res[3] = {0.0, 0.0, 0.0};
+  double Da[NS + 2], Db[NS + 2];
 #pragma unroll
-  for (int mu = 0; mu < 3; ++mu) {
-    double d1 = dc.D[k1][0] * sB[le][0][mu][k2] + dc.D[k1][NS + 1] * sB[le][1][mu][k2];
-    double d2 = dc.D[k2][0] * sB[le][2][mu][k1] + dc.D[k2][NS + 1] * sB[le][3][mu][k1];
-#pragma unroll
-    for (int l = 0; l < NS; ++l) {
-      d1 = fma(dc.D[k1][l + 1], sF[le][0][mu][k2 * NS + l], d1);
-      d2 = fma(dc.D[k2][l + 1], sF[le][1][mu][l * NS + k1], d2);
-    }
-    res[mu] = -dc.two_over_dx * (d1 + d2) + part(S[mu]);
+  for (int n = 0; n < NS + 2; ++n) {
+    Da[n] = sD[k1][n];
+    Db[n] = sD[k2][n];
   }
-  const double scale = a.v ? a.ep.scale / a.eps : a.ep.scale;
-  const long long N = a.nodes;
+  if (active) {
 #pragma unroll
-  for (int mu = 0; mu < 3; ++mu) {
-    double o = scale * res[mu];
-    if (a.ep.p > 0) {
+    for (int mu = 0; mu < 3; ++mu) {
+      double d1 = Da[0] * sB[le][0][mu][k2] + Da[NS + 1] * sB[le][1][mu][k2];
+      double d2 = Db[0] * sB[le][2][mu][k1] + Db[NS + 1] * sB[le][3][mu][k1];
 #pragma unroll
-      for (int l = 0; l < MAX_NB; ++l)
-        if (l < a.ep.p && a.ep.b[l]) o = fma(a.ep.nu * a.ep.tail_in[l], a.ep.b[l][idx + mu * N], o);
+      for (int l = 0; l < NS; ++l) {
+        d1 = fma(Da[l + 1], sF[le][0][mu][k2 * NS + l], d1);
+        d2 = fma(Db[l + 1], sF[le][1][mu][l * NS + k1], d2);
+      }
+      res[mu] = -dc.two_over_dx * (d1 + d2) + part(S[mu]);
     }
-    a.out[idx + mu * N] = o;
   }
-  if (a.ep.tail_out && blockIdx.x == 0 && threadIdx.x < a.ep.p)
-    a.ep.tail_out[threadIdx.x] = (threadIdx.x + 1 < a.ep.p) ? a.ep.tail_in[threadIdx.x + 1] : 0.0;
+  if (active) {
+    const double sc = a.v ? 1.0 / a.eps : 1.0;
+#pragma unroll
+    for (int mu = 0; mu < 3; ++mu) res[mu] *= sc;
+  }
+  volume_epilogue<VolShape<NS>::THREADS>(a.ep, active, idx, a.nodes, res, a.out);
 }
 
 // ---------------------------------------------------------------- launchers

@@ -1,0 +1,225 @@
+// Device-side building blocks shared by the DFR kernels: the complex-step
+// number type, state loads, the AUSM interface flux (App. D/E) and the trace
+// extrapolation (Eq. 7 at the element ends).  See dfr.cu for the arithmetic
+// conventions of the complex step.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "swepi_internal.h"
+
+namespace swepi {
+
+struct cs {
+  double re, im;
+};
+__device__ __forceinline__ cs operator+(cs a, cs b) { return {a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ cs operator-(cs a, cs b) { return {a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ cs operator*(cs a, cs b) { return {a.re * b.re, fma(a.re, b.im, a.im * b.re)}; }
+__device__ __forceinline__ cs operator*(double k, cs a) { return {k * a.re, k * a.im}; }
+__device__ __forceinline__ cs operator+(cs a, double k) { return {a.re + k, a.im}; }
+__device__ __forceinline__ cs cs_rcp(cs a) {
+  double r = 1.0 / a.re;
+  return {r, -a.im * r * r};
+}
+__device__ __forceinline__ cs cs_div(cs a, cs b) {
+  double r = 1.0 / b.re;
+  double qr = a.re * r;
+  return {qr, (a.im - qr * b.im) * r};
+}
+__device__ __forceinline__ cs cs_sqrt(cs a) {
+  double s = sqrt(a.re);
+  return {s, a.im * (0.5 / s)};
+}
+__device__ __forceinline__ double re(cs a) { return a.re; }
+__device__ __forceinline__ double im(cs a) { return a.im; }
+__device__ __forceinline__ cs mk(double r, double i, cs*) { return {r, i}; }
+
+// real instantiation (the RHS): same code path on plain doubles
+__device__ __forceinline__ double cs_rcp(double a) { return 1.0 / a; }
+__device__ __forceinline__ double cs_div(double a, double b) { return a / b; }
+__device__ __forceinline__ double cs_sqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ double re(double a) { return a; }
+__device__ __forceinline__ double im(double) { return 0.0; }
+__device__ __forceinline__ double mk(double r, double, double*) { return r; }
+
+// the part of a result the caller wants: the imaginary part for the JVP, the
+// value for the RHS
+__device__ __forceinline__ double part(cs a) { return a.im; }
+__device__ __forceinline__ double part(double a) { return a; }
+
+template <typename T>
+__device__ __forceinline__ T load_state(const double* __restrict__ q, const double* __restrict__ v, double eps,
+                                        long long i) {
+  return mk(__ldg(q + i), v ? eps * __ldg(v + i) : 0.0, (T*)nullptr);
+}
+
+// ---------------------------------------------------------------- AUSM
+// basic AUSM splittings (reading of App. D Eq. 138-139; [41] Eq. 6 and 8)
+template <typename T>
+__device__ __forceinline__ void ausm_side(const T q[3], int d, double ad, double p1, double p2, T& M, T A[3], T P[3]) {
+  T a = cs_sqrt(ad * q[0]);                       // a^d = sqrt(h^dd g_r H), App. E
+  T u = cs_div(q[d], q[0]);                       // u^d
+  M = cs_div(u, a);                               // Froude number
+  A[0] = a * q[0];                                // A^{mu d} = a q^mu
+  A[1] = a * q[1];
+  A[2] = a * q[2];
+  T q0sq = q[0] * q[0];
+  P[0] = 0.0 * q[0];
+  P[1] = p1 * q0sq;                               // P^{mu d} = g_r h^{mu d} (q^0)^2 / (2 sqrt g)
+  P[2] = p2 * q0sq;
+}
+
+template <typename T>
+__device__ __forceinline__ void ausm_flux(const T qL[3], const T qR[3], int d, double ad, double p1, double p2,
+                                          T flux[3]) {
+  T ML, MR, AL[3], AR[3], PL[3], PR[3];
+  ausm_side(qL, d, ad, p1, p2, ML, AL, PL);
+  ausm_side(qR, d, ad, p1, p2, MR, AR, PR);
+  // M+(M_L), beta+(M_L)
+  T mp, bp, mm, bm;
+  if (fabs(re(ML)) <= 1.0) {
+    T t = ML + 1.0;
+    mp = 0.25 * (t * t);
+    bp = (0.25 * (t * t)) * (2.0 * mk(1.0, 0.0, (T*)nullptr) - ML);
+  } else if (re(ML) > 0.0) {
+    mp = ML;
+    bp = mk(1.0, 0.0, (T*)nullptr);
+  } else {
+    mp = 0.0 * ML;
+    bp = 0.0 * ML;
+  }
+  // M-(M_R), beta-(M_R)
+  if (fabs(re(MR)) <= 1.0) {
+    T t = MR + (-1.0);
+    mm = -0.25 * (t * t);
+    bm = (0.25 * (t * t)) * (MR + 2.0);
+  } else if (re(MR) > 0.0) {
+    mm = 0.0 * MR;
+    bm = 0.0 * MR;
+  } else {
+    mm = MR;
+    bm = mk(1.0, 0.0, (T*)nullptr);
+  }
+  T Mh = mp + mm;
+  bool pos = re(Mh) > 0.0;
+#pragma unroll
+  for (int mu = 0; mu < 3; ++mu) {
+    T adv = pos ? Mh * AL[mu] : Mh * AR[mu];
+    flux[mu] = (adv + bp * PL[mu]) + bm * PR[mu];
+  }
+}
+
+template <typename T, int NS>
+__device__ __forceinline__ void trace(const double* __restrict__ q, const double* __restrict__ v, double eps,
+                                      long long nodes, int elem, int edge, int i, const DfrConst& dc, T out[3]) {
+  const long long base = (long long)elem * NS * NS;
+  const double* w = (edge == 0 || edge == 2) ? dc.lm : dc.lp;
+#pragma unroll
+  for (int var = 0; var < 3; ++var) {
+    T acc = mk(0.0, 0.0, (T*)nullptr);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      long long idx = base + ((edge <= 1) ? (i * NS + k) : (k * NS + i)) + var * nodes;
+      acc = acc + w[k] * load_state<T>(q, v, eps, idx);
+    }
+    out[var] = acc;
+  }
+}
+
+template <int NS>
+struct VolShape {
+  static constexpr int EPB = (256 / (NS * NS)) > 0 ? (256 / (NS * NS)) : 1;
+  static constexpr int THREADS = EPB * NS * NS;
+};
+
+
+// Epilogue of the volume kernels (all threads of the block call it):
+// out = scale * res + nu * sum_l y_l b_{p-l} (the augmented operator of the
+// phi-function solver), the shift of the augmented tail, and -- when dotB is
+// set -- the window dot products of the incomplete orthogonalisation.
+template <int THREADS>
+__device__ __forceinline__ void volume_epilogue(const AugEpilogue& ep, bool active, long long idx, long long N,
+                                                const double res[3], double* __restrict__ out) {
+  double da = 0.0, db = 0.0;
+  if (active) {
+    double coef[MAX_NB];
+#pragma unroll
+    for (int l = 0; l < MAX_NB; ++l) coef[l] = (l < ep.p && ep.b[l]) ? ep.nu * ep.tail_in[l] : 0.0;
+#pragma unroll
+    for (int mu = 0; mu < 3; ++mu) {
+      double o = ep.scale * res[mu];
+#pragma unroll
+      for (int l = 0; l < MAX_NB; ++l)
+        if (l < ep.p && ep.b[l]) o = fma(coef[l], ep.b[l][idx + mu * N], o);
+      out[idx + mu * N] = o;
+      if (ep.dotB) {
+        db = fma(o, ep.dotB[idx + mu * N], db);
+        if (ep.dotA) da = fma(o, ep.dotA[idx + mu * N], da);
+      }
+    }
+  }
+  if (ep.tail_out && blockIdx.x == 0 && threadIdx.x < ep.p)
+    ep.tail_out[threadIdx.x] = (threadIdx.x + 1 < ep.p) ? ep.tail_in[threadIdx.x + 1] : 0.0;
+  if (!ep.dotB) return;   // uniform over the grid
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int l = 0; l < ep.p; ++l) {
+      const double zt = (l + 1 < ep.p) ? ep.tail_in[l + 1] : 0.0;
+      db = fma(zt, ep.dotB[ep.n + l], db);
+      if (ep.dotA) da = fma(zt, ep.dotA[ep.n + l], da);
+    }
+  }
+  __shared__ double sa[THREADS], sb[THREADS];
+  __shared__ bool last;
+  sa[threadIdx.x] = da;
+  sb[threadIdx.x] = db;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double a = 0.0, b = 0.0;
+    for (int k = threadIdx.x; k < THREADS; k += 32) { a += sa[k]; b += sb[k]; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (threadIdx.x == 0) {
+      ep.dpart[2 * blockIdx.x] = a;
+      ep.dpart[2 * blockIdx.x + 1] = b;
+      __threadfence();
+      const unsigned int t = atomicAdd(ep.dticket, 1u);
+      last = (t == gridDim.x - 1);
+    }
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double a = 0.0, b = 0.0;
+  for (int k = threadIdx.x; k < (int)gridDim.x; k += THREADS) {
+    a += __ldcg(ep.dpart + 2 * k);
+    b += __ldcg(ep.dpart + 2 * k + 1);
+  }
+  sa[threadIdx.x] = a;
+  sb[threadIdx.x] = b;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    a = 0.0;
+    b = 0.0;
+    for (int k = threadIdx.x; k < THREADS; k += 32) { a += sa[k]; b += sb[k]; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (threadIdx.x == 0) {
+      if (ep.dotA) {
+        *ep.h1_out = a;
+        *ep.h2_out = b - a * (*ep.cprev);   // V_j . (z - h1 V_{j-1})
+      } else {
+        *ep.h2_out = b;
+      }
+      *ep.dticket = 0u;
+    }
+  }
+}
+
+}  // namespace swepi

@@ -1,0 +1,316 @@
+// Complex-step JVP split into its real and imaginary halves.
+//
+// Every JVP of one Krylov solve, and the remainder products of one EPI step,
+// is taken at the same linearisation point q_n (Eq. 33-35).  In the
+// complex-step evaluation F(q_n + i eps v) the real part of every intermediate
+// (1/q^0, u^i, a^d, the Froude numbers, the AUSM splittings, ...) depends on q_n
+// only, while the imaginary part is a linear function of v whose coefficients
+// are those real parts.  The split path therefore evaluates the real half once
+// per linearisation point and stores, per solution point and per interface
+// point, the coefficients of the imaginary half:
+//   lin_node_kernel   per node: u^1, u^2 and the coefficients of the imaginary
+//                     parts of sqrt(g) T^{ij} (Eq. 136) and of the sources of
+//                     Eq. (2) as functions of Im q;
+//   lin_face_kernel   per interface point: the 3 x 6 matrix taking the
+//                     imaginary parts of the two traces to the imaginary part of
+//                     the AUSM flux, obtained by propagating unit imaginary
+//                     parts through the same complex-step AUSM code as the
+//                     plain kernels (the neighbour's App. C transform folded in).
+// Each JVP then runs only the imaginary half, in real arithmetic:
+//   face_tangent_kernel   traces of v, the 3 x 6 map, the hand-back;
+//   volume_tangent_kernel pointwise imaginary fluxes and sources, the DFR
+//                         sweeps (Eq. 12-14) and the augmented-operator epilogue.
+// The imaginary parts are proportional to eps, so the tangent is propagated for
+// v itself and the final division by eps is omitted.  Results equal the plain
+// path up to rounding; no FP64 division or square root remains per JVP.
+#include <cuda_runtime.h>
+
+#include "dfr_device.cuh"
+#include "swepi_internal.h"
+
+namespace swepi {
+
+namespace {
+
+// ---------------------------------------------------------------- linearise
+__global__ void lin_node_kernel(const double* __restrict__ q, const double* __restrict__ nc, long long nodes,
+                                double* __restrict__ ln) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nodes) return;
+  const long long N = nodes;
+  const double q0 = q[i], q1 = q[i + N], q2 = q[i + 2 * N];
+  const double r = 1.0 / q0;
+  const double u1 = q1 * r, u2 = q2 * r;
+  const double c11 = nc[NC_C11 * N + i], c12 = nc[NC_C12 * N + i], c22 = nc[NC_C22 * N + i];
+  const double g1a = nc[NC_G1A * N + i], g1b = nc[NC_G1B * N + i];
+  const double g2a = nc[NC_G2A * N + i], g2b = nc[NC_G2B * N + i];
+  // Im sqrt(g)T^{ij} = u^j Im q^i + u^i Im q^j + (g_r h^ij q^0 / sqrt g - u^i u^j) Im q^0
+  ln[LN_U1 * N + i] = u1;
+  ln[LN_U2 * N + i] = u2;
+  ln[LN_A11 * N + i] = 2.0 * c11 * q0 - u1 * u1;
+  ln[LN_A12 * N + i] = 2.0 * c12 * q0 - u1 * u2;
+  ln[LN_A22 * N + i] = 2.0 * c22 * q0 - u2 * u2;
+  // Im S^i = s_i1 Im q^1 + s_i2 Im q^2 + s_i0 Im q^0 (Coriolis, Gamma^i_jk, topography terms of Eq. 2)
+  ln[LN_S11 * N + i] = nc[NC_K11 * N + i] - 2.0 * g1a * u1 - g1b * u2;
+  ln[LN_S12 * N + i] = nc[NC_K12 * N + i] - g1b * u1;
+  ln[LN_S10 * N + i] = g1a * u1 * u1 + g1b * u1 * u2 + nc[NC_B1 * N + i];
+  ln[LN_S21 * N + i] = nc[NC_K21 * N + i] - g2a * u2;
+  ln[LN_S22 * N + i] = nc[NC_K22 * N + i] - g2a * u1 - 2.0 * g2b * u2;
+  ln[LN_S20 * N + i] = g2a * u1 * u2 + g2b * u2 * u2 + nc[NC_B2 * N + i];
+}
+
+struct LinFaceArgs {
+  const double* q;
+  long long nodes;
+  const FaceLine* lines;
+  const double* fc;
+  long long nfacepts;
+  double* lf;   // [18][nfacepts]: owner-trace block then neighbour-trace block
+};
+
+template <int NS>
+__global__ void __launch_bounds__(128) lin_face_kernel(LinFaceArgs a, DfrConst dc) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.nfacepts) return;
+  const int line = (int)(t / NS), i = (int)(t % NS);
+  const FaceLine L = a.lines[line];
+  const int in = L.reversed ? NS - 1 - i : i;
+  double qo[3], qn[3];
+  trace<double, NS>(a.q, nullptr, 0.0, a.nodes, L.owner, L.owner_edge, i, dc, qo);
+  trace<double, NS>(a.q, nullptr, 0.0, a.nodes, L.nbr, L.nbr_edge, in, dc, qn);
+  const long long P = a.nfacepts;
+  const double* fc = a.fc + t;
+  const double T00 = fc[FC_T00 * P], T01 = fc[FC_T01 * P], T10 = fc[FC_T10 * P], T11 = fc[FC_T11 * P];
+  const double qt[3] = {qn[0], T00 * qn[1] + T01 * qn[2], T10 * qn[1] + T11 * qn[2]};
+  const double ad = fc[FC_AD * P], p1 = fc[FC_P1 * P], p2 = fc[FC_P2 * P];
+  const double* qL = L.owner_is_left ? qo : qt;
+  const double* qR = L.owner_is_left ? qt : qo;
+  double J[3][6];
+#pragma unroll 1
+  for (int col = 0; col < 6; ++col) {
+    cs zL[3], zR[3], fl[3];
+    for (int k = 0; k < 3; ++k) {
+      zL[k] = {qL[k], (col == k) ? 1.0 : 0.0};
+      zR[k] = {qR[k], (col == k + 3) ? 1.0 : 0.0};
+    }
+    ausm_flux<cs>(zL, zR, L.dir, ad, p1, p2, fl);
+    for (int mu = 0; mu < 3; ++mu) J[mu][col] = fl[mu].im;
+  }
+  // columns of the owner trace and of the neighbour trace (own coordinates)
+  const int co = L.owner_is_left ? 0 : 3, cn = L.owner_is_left ? 3 : 0;
+  double* out = a.lf + t;
+  for (int mu = 0; mu < 3; ++mu) {
+    for (int k = 0; k < 3; ++k) out[(mu * 3 + k) * P] = J[mu][co + k];
+    // neighbour: Im q_t = blockdiag(1, T) Im q_n
+    out[(9 + mu * 3 + 0) * P] = J[mu][cn + 0];
+    out[(9 + mu * 3 + 1) * P] = J[mu][cn + 1] * T00 + J[mu][cn + 2] * T10;
+    out[(9 + mu * 3 + 2) * P] = J[mu][cn + 1] * T01 + J[mu][cn + 2] * T11;
+  }
+}
+
+// ---------------------------------------------------------------- tangent
+struct TanFaceArgs {
+  const double* v;
+  long long nodes;
+  const FaceLine* lines;
+  const double* fc;
+  const double* lf;
+  long long nfacepts;
+  double* fb;
+  const int* skip;
+};
+
+template <int NS>
+__global__ void __launch_bounds__(128) face_tangent_kernel(TanFaceArgs a, DfrConst dc) {
+  if (a.skip && *a.skip) return;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.nfacepts) return;
+  const int line = (int)(t / NS), i = (int)(t % NS);
+  const FaceLine L = a.lines[line];
+  const int in = L.reversed ? NS - 1 - i : i;
+  double vo[3], vn[3];
+  trace<double, NS>(a.v, nullptr, 0.0, a.nodes, L.owner, L.owner_edge, i, dc, vo);
+  trace<double, NS>(a.v, nullptr, 0.0, a.nodes, L.nbr, L.nbr_edge, in, dc, vn);
+  const long long P = a.nfacepts;
+  const double* lf = a.lf + t;
+  double f[3];
+#pragma unroll
+  for (int mu = 0; mu < 3; ++mu) {
+    double s = lf[(mu * 3) * P] * vo[0];
+    s = fma(lf[(mu * 3 + 1) * P], vo[1], s);
+    s = fma(lf[(mu * 3 + 2) * P], vo[2], s);
+    s = fma(lf[(9 + mu * 3) * P], vn[0], s);
+    s = fma(lf[(9 + mu * 3 + 1) * P], vn[1], s);
+    s = fma(lf[(9 + mu * 3 + 2) * P], vn[2], s);
+    f[mu] = s;
+  }
+  const double* fc = a.fc + t;
+  const double sig = fc[FC_SIG * P];
+  const double M00 = fc[FC_M00 * P], M01 = fc[FC_M01 * P], M10 = fc[FC_M10 * P], M11 = fc[FC_M11 * P];
+  double* fo = a.fb + ((long long)L.owner * 4 + L.owner_edge) * 3 * NS + i;
+  fo[0] = f[0];
+  fo[NS] = f[1];
+  fo[2 * NS] = f[2];
+  double* fn = a.fb + ((long long)L.nbr * 4 + L.nbr_edge) * 3 * NS + in;
+  fn[0] = sig * f[0];
+  fn[NS] = M00 * f[1] + M01 * f[2];
+  fn[2 * NS] = M10 * f[1] + M11 * f[2];
+}
+
+struct TanVolArgs {
+  const double* v;
+  long long nodes;
+  long long nelem;
+  const double* ln;
+  const double* fb;
+  double* out;
+  AugEpilogue ep;
+};
+
+template <int NS>
+__global__ void __launch_bounds__(VolShape<NS>::THREADS) volume_tangent_kernel(TanVolArgs a, DfrConst dc) {
+  constexpr int EPB = VolShape<NS>::EPB;
+  constexpr int NN = NS * NS;
+  if (a.ep.skip && *a.ep.skip) return;
+  __shared__ double sF[EPB][2][3][NN];
+  __shared__ double sB[EPB][4][3][NS];
+  __shared__ double sD[NS][NS + 3];          // padded rows: distinct banks per k
+  for (int t = threadIdx.x; t < NS * (NS + 2); t += blockDim.x) sD[t / (NS + 2)][t % (NS + 2)] = dc.D[t / (NS + 2)][t % (NS + 2)];
+  const int le = threadIdx.x / NN, node = threadIdx.x % NN;
+  const long long elem = (long long)blockIdx.x * EPB + le;
+  const bool active = elem < a.nelem;
+  const int k2 = node / NS, k1 = node % NS;
+  const long long idx = elem * NN + node;
+  for (int t = threadIdx.x; t < EPB * 12 * NS; t += blockDim.x) {
+    int e = t / (12 * NS), r = t % (12 * NS);
+    long long ge = (long long)blockIdx.x * EPB + e;
+    (&sB[e][0][0][0])[r] = (ge < a.nelem) ? a.fb[ge * 12 * NS + r] : 0.0;
+  }
+  double S1 = 0.0, S2 = 0.0;
+  const long long N = a.nodes;
+  if (active) {
+    const double v0 = __ldg(a.v + idx), v1 = __ldg(a.v + idx + N), v2 = __ldg(a.v + idx + 2 * N);
+    const double* ln = a.ln + idx;
+    const double u1 = ln[LN_U1 * N], u2 = ln[LN_U2 * N];
+    const double F11 = fma(2.0 * u1, v1, ln[LN_A11 * N] * v0);
+    const double F12 = fma(u2, v1, fma(u1, v2, ln[LN_A12 * N] * v0));
+    const double F22 = fma(2.0 * u2, v2, ln[LN_A22 * N] * v0);
+    S1 = fma(ln[LN_S11 * N], v1, fma(ln[LN_S12 * N], v2, ln[LN_S10 * N] * v0));
+    S2 = fma(ln[LN_S21 * N], v1, fma(ln[LN_S22 * N], v2, ln[LN_S20 * N] * v0));
+    sF[le][0][0][node] = v1;
+    sF[le][0][1][node] = F11;
+    sF[le][0][2][node] = F12;
+    sF[le][1][0][node] = v2;
+    sF[le][1][1][node] = F12;
+    sF[le][1][2][node] = F22;
+  }
+  __syncthreads();
+  const double src[3] = {0.0, S1, S2};
+  double res[3] = {0.0, 0.0, 0.0};
+  // this thread's rows of the derivative matrix, from shared memory into registers
+  // (a per-thread row index into the constant bank would serialise the warp)
+  double Da[NS + 2], Db[NS + 2];
+#pragma unroll
+  for (int n = 0; n < NS + 2; ++n) {
+    Da[n] = sD[k1][n];
+    Db[n] = sD[k2][n];
+  }
+  if (active) {
+#pragma unroll
+    for (int mu = 0; mu < 3; ++mu) {
+      double d1 = Da[0] * sB[le][0][mu][k2] + Da[NS + 1] * sB[le][1][mu][k2];
+      double d2 = Db[0] * sB[le][2][mu][k1] + Db[NS + 1] * sB[le][3][mu][k1];
+#pragma unroll
+      for (int l = 0; l < NS; ++l) {
+        d1 = fma(Da[l + 1], sF[le][0][mu][k2 * NS + l], d1);
+        d2 = fma(Db[l + 1], sF[le][1][mu][l * NS + k1], d2);
+      }
+      res[mu] = -dc.two_over_dx * (d1 + d2) + src[mu];
+    }
+  }
+  volume_epilogue<VolShape<NS>::THREADS>(a.ep, active, idx, N, res, a.out);
+}
+
+template <int NS>
+int linearize_ns(Ctx& c, const double* q, cudaStream_t s) {
+  const int th = 256;
+  lin_node_kernel<<<(unsigned)((c.nodes + th - 1) / th), th, 0, s>>>(q, c.d_node_coef, c.nodes, c.d_lin_node);
+  LinFaceArgs fa{q, c.nodes, c.d_lines, c.d_face_coef, c.nfacepts, c.d_lin_face};
+  lin_face_kernel<NS><<<(unsigned)((c.nfacepts + 127) / 128), 128, 0, s>>>(fa, c.dc);
+  c.launches += 2;
+  return cuda_status(cudaGetLastError());
+}
+
+template <int NS>
+int tangent_ns(Ctx& c, const double* v, double* out, const AugEpilogue& ep, cudaStream_t s) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+  if (c.prof) {
+    e0 = prof_event(c);
+    e1 = prof_event(c);
+    e2 = prof_event(c);
+    cudaEventRecord(e0, s);
+  }
+  TanFaceArgs fa{v, c.nodes, c.d_lines, c.d_face_coef, c.d_lin_face, c.nfacepts, c.d_fb, ep.skip};
+  face_tangent_kernel<NS><<<(unsigned)((c.nfacepts + 127) / 128), 128, 0, s>>>(fa, c.dc);
+  if (c.prof) cudaEventRecord(e1, s);
+  TanVolArgs va{v, c.nodes, c.nelem, c.d_lin_node, c.d_fb, out, ep};
+  const long long vblocks = (c.nelem + VolShape<NS>::EPB - 1) / VolShape<NS>::EPB;
+  volume_tangent_kernel<NS><<<(unsigned)vblocks, VolShape<NS>::THREADS, 0, s>>>(va, c.dc);
+  if (c.prof) {
+    cudaEventRecord(e2, s);
+    prof_record(c, PK_FACE_JVP, e0, e1);
+    prof_record(c, PK_VOL_JVP, e1, e2);
+  }
+  c.launches += 2;
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+
+int launch_linearize(Ctx& c, const double* q, cudaStream_t s) {
+  if (!c.d_lin_node && cudaMalloc(&c.d_lin_node, sizeof(double) * LN_COUNT * c.nodes) != cudaSuccess)
+    return SW_ENOMEM;
+  if (!c.d_lin_face && cudaMalloc(&c.d_lin_face, sizeof(double) * 18 * c.nfacepts) != cudaSuccess)
+    return SW_ENOMEM;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c.prof) {
+    e0 = prof_event(c);
+    e1 = prof_event(c);
+    cudaEventRecord(e0, s);
+  }
+  int rc;
+  switch (c.ns) {
+    case 1: rc = linearize_ns<1>(c, q, s); break;
+    case 2: rc = linearize_ns<2>(c, q, s); break;
+    case 3: rc = linearize_ns<3>(c, q, s); break;
+    case 4: rc = linearize_ns<4>(c, q, s); break;
+    case 5: rc = linearize_ns<5>(c, q, s); break;
+    case 6: rc = linearize_ns<6>(c, q, s); break;
+    case 7: rc = linearize_ns<7>(c, q, s); break;
+    case 8: rc = linearize_ns<8>(c, q, s); break;
+    default: return SW_EINVAL;
+  }
+  if (c.prof) {
+    cudaEventRecord(e1, s);
+    prof_record(c, PK_LIN, e0, e1);
+  }
+  if (rc == SW_OK) c.linearized = true;
+  return rc;
+}
+
+int launch_jvp_lin(Ctx& c, const double* v, double* out, const AugEpilogue& ep, cudaStream_t s) {
+  if (!c.linearized) return SW_EINVAL;
+  switch (c.ns) {
+    case 1: return tangent_ns<1>(c, v, out, ep, s);
+    case 2: return tangent_ns<2>(c, v, out, ep, s);
+    case 3: return tangent_ns<3>(c, v, out, ep, s);
+    case 4: return tangent_ns<4>(c, v, out, ep, s);
+    case 5: return tangent_ns<5>(c, v, out, ep, s);
+    case 6: return tangent_ns<6>(c, v, out, ep, s);
+    case 7: return tangent_ns<7>(c, v, out, ep, s);
+    case 8: return tangent_ns<8>(c, v, out, ep, s);
+    default: return SW_EINVAL;
+  }
+}
+
+}  // namespace swepi

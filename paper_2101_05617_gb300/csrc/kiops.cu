@@ -12,7 +12,9 @@
 //    new vector is orthogonalised against the last `iop` basis vectors
 //    (modified Gram-Schmidt, oldest first); ||z|| < tol is a happy breakdown,
 //    after which the projection is exact and the rest of the interval is taken;
-//  * err = beta h_{j+1,j} |F[j-1, j]| with F = exp(tau [[H_j, e_1], [0, 0]]),
+//  * err = beta h_{j+1,j} |F[j-1, j]| with F = exp(tau [[H_j, e_1], [0, 0]])
+//    (device exponential, krylov.cu; the host reads the order and 1-norm of
+//    the matrix to choose the number of squarings),
 //    omega = (tau_end / tau) err / (tol beta_0), beta_0 = ||[b_0; mu e_p]||;
 //  * accept when omega <= 1.2; new tau from the order estimate (j/4, or
 //    measured from two tries at equal m), new m from the growth estimate (2, or
@@ -74,6 +76,9 @@ int ensure_krylov(Ctx& c, int m_max) {
   if (cudaMalloc(&c.d_F, sizeof(double) * c.ldh * c.ldh) != cudaSuccess) return SW_ENOMEM;
   if (cudaMalloc(&c.d_expm_ws, sizeof(double) * 8 * 160 * 160) != cudaSuccess) return SW_ENOMEM;
   if (!c.d_partials && cudaMalloc(&c.d_partials, sizeof(double) * RED_BLOCKS) != cudaSuccess) return SW_ENOMEM;
+  if (!c.d_vpart && cudaMalloc(&c.d_vpart, sizeof(double) * 2 * (c.nelem + 1)) != cudaSuccess) return SW_ENOMEM;
+  free_ptr(c.d_cdot);
+  if (cudaMalloc(&c.d_cdot, sizeof(double) * c.ldh) != cudaSuccess) return SW_ENOMEM;
   if (!c.d_scal && cudaMalloc(&c.d_scal, sizeof(double) * 64) != cudaSuccess) return SW_ENOMEM;
   if (!c.d_flags) {
     if (cudaMalloc(&c.d_flags, sizeof(int) * 16) != cudaSuccess) return SW_ENOMEM;
@@ -85,7 +90,7 @@ int ensure_krylov(Ctx& c, int m_max) {
 }
 
 int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, const double* const* b,
-              const sw_kiops_opts& o, double* w, sw_kiops_stats* st, cudaStream_t s) {
+              const sw_kiops_opts& o, double* w, sw_kiops_stats* st, cudaStream_t s, bool use_lin) {
   if (nb < 1 || nb > MAX_NB || !(tau_out > 0) || o.m_min < 1 || o.m_max < o.m_min || o.m_max > 150 || o.iop < 1 ||
       !(o.tol > 0))
     return SW_EINVAL;
@@ -162,7 +167,28 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
       double* Vn = V + (it + 1) * ldv;
       ep.tail_in = Vi + n;
       ep.tail_out = Vn + n;
-      if ((rc = launch_jvp(c, q_lin, Vi, kEpsJvp, Vn, ep, s))) return rc;
+      if (o.iop == 2) {
+        // orthogonalisation fused into the JVP epilogue (dots) and two passes
+        double* hB = c.d_H + (long long)it * c.ldh + it;
+        double* hA = (it >= 1) ? c.d_H + (long long)(it - 1) * c.ldh + it : nullptr;
+        ep.dotA = (it >= 1) ? V + (it - 1) * ldv : nullptr;
+        ep.dotB = Vi;
+        ep.cprev = c.d_cdot + it;
+        ep.h1_out = hA;
+        ep.h2_out = hB;
+        ep.dpart = c.d_vpart;
+        ep.dticket = (unsigned int*)(c.d_flags + 9);
+        ep.n = n;
+        rc = use_lin ? launch_jvp_lin(c, Vi, Vn, ep, s) : launch_jvp(c, q_lin, Vi, kEpsJvp, Vn, ep, s);
+        if (rc) return rc;
+        double* hs = c.d_H + (long long)(it + 1) * c.ldh + it;
+        if ((rc = launch_update_norm(c, Vn, ep.dotA, Vi, hA, hB, N, hs, o.tol, it + 1, s))) return rc;
+        if ((rc = launch_scale_dot(c, Vn, Vi, hs, N, c.d_cdot + it + 1, s))) return rc;
+        continue;
+      }
+      ep.dotA = ep.dotB = nullptr;
+      rc = use_lin ? launch_jvp_lin(c, Vi, Vn, ep, s) : launch_jvp(c, q_lin, Vi, kEpsJvp, Vn, ep, s);
+      if (rc) return rc;
       for (int i = std::max(0, it - o.iop + 1); i <= it; ++i) {
         double* h = c.d_H + (long long)i * c.ldh + it;
         if ((rc = launch_dot(c, V + i * ldv, Vn, N, h, c.d_flags, s))) return rc;
@@ -172,7 +198,12 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
       if ((rc = launch_norm2(c, Vn, N, hs, o.tol, c.d_flags, it + 1, c.d_flags, s))) return rc;
       if ((rc = launch_scale_inv(c, Vn, Vn, hs, N, c.d_flags, s))) return rc;
     }
-    if ((rc = launch_expm_hess(c, m, tau, tau_end - tau_now, s))) return rc;
+    if ((rc = launch_expm_prep(c, m, tau, tau_end - tau_now, s))) return rc;
+    if ((rc = read_back(c, s))) return rc;
+    {
+      const int Ne = (int)c.h_pinned[S_STAT + 1] + 1;
+      if ((rc = launch_expm_eval(c, Ne, c.h_pinned[S_STAT + 5], nullptr, s))) return rc;
+    }
     if ((rc = read_back(c, s))) return rc;
     const int* fl = pinned_flags(c);
     const bool happy = fl[0] != 0;

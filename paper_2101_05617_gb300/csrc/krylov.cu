@@ -140,48 +140,24 @@ __global__ void combine_kernel(double* __restrict__ X, const double* __restrict_
 }
 
 // ------------------------------------------------------------ expm
-// exp(A) by scaling and squaring with the [13/13] Pade approximant (Higham,
-// "The scaling and squaring method for the matrix exponential revisited",
-// SIAM J. Matrix Anal. Appl. 26 (2005)), one thread block, FP64, matrices of
-// order N <= MAX_EXPM in global workspace (L2 resident).
+// F = exp(A), A = t [[H_j, e_1], [0, 0]] (order N = j + 1 <= MAX_EXPM): scaling
+// and squaring (Moler and Van Loan, "Nineteen dubious ways to compute the
+// exponential of a matrix, twenty-five years later", SIAM Rev. 45, 2003) with
+// the degree-16 Taylor polynomial, evaluated by the Paterson-Stockmeyer scheme
+// (SIAM J. Comput. 2, 1973) in blocks of four powers: 6 matrix products, then s
+// squarings, s = max(0, ceil(log2(||A||_1 / 0.8))).  At ||X||_1 <= 0.8 the
+// truncated tail is below 0.8^17/17! = 6e-17.  Every product is a grid-wide FP64
+// GEMM launch (8 x 8 outputs per block): the whole GPU shares the O(N^3) work.
 constexpr int MAX_EXPM = 160;
-constexpr int EXPM_THREADS = 512;
+constexpr double kTaylorTheta = 0.8;
 
-struct Pade {
-  double b[14];
-  double theta13;
-};
-
-__device__ void mm(double* C, const double* A, const double* B, int N) {
-  for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
-    int r = t / N, c = t % N;
-    double s = 0.0;
-    for (int k = 0; k < N; ++k) s = fma(A[r * N + k], B[k * N + c], s);
-    C[t] = s;
-  }
-  __syncthreads();
-}
-
-__global__ void __launch_bounds__(EXPM_THREADS) expm_kernel(const double* __restrict__ H, int ldh, int j, double tau,
-                                                            double tau_happy, const int* happy, double* F,
-                                                            double* ws, double* stat, Pade pd) {
+// one block: build A (dense, leading dimension N) and its 1-norm
+__global__ void expm_prep_kernel(const double* __restrict__ H, int ldh, int j, double tau, double tau_happy,
+                                 const int* happy, double* A, double* stat) {
   const int jj = happy[0] ? happy[1] : j;
   const double t = happy[0] ? tau_happy : tau;
   const int N = jj + 1;
-  const int NN = N * N;
-  double* A = ws;
-  double* A2 = A + NN;
-  double* A4 = A2 + NN;
-  double* A6 = A4 + NN;
-  double* U = A6 + NN;
-  double* V = U + NN;
-  double* T1 = V + NN;
-  double* T2 = T1 + NN;
-  __shared__ double colsum[MAX_EXPM];
-  __shared__ int s_sq;
-  __shared__ int piv;
-  // A = t [[H_jj, e_1], [0, 0]]
-  for (int i = threadIdx.x; i < NN; i += blockDim.x) {
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
     int r = i / N, c = i % N;
     double v = 0.0;
     if (r < jj && c < jj) v = H[(long long)r * ldh + c];
@@ -189,116 +165,135 @@ __global__ void __launch_bounds__(EXPM_THREADS) expm_kernel(const double* __rest
     A[i] = t * v;
   }
   __syncthreads();
+  __shared__ double colsum[MAX_EXPM];
   for (int c = threadIdx.x; c < N; c += blockDim.x) {
-    double s = 0.0;
-    for (int r = 0; r < N; ++r) s += fabs(A[r * N + c]);
-    colsum[c] = s;
+    double sum = 0.0;
+    for (int r = 0; r < N; ++r) sum += fabs(A[r * N + c]);
+    colsum[c] = sum;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     double nrm = 0.0;
     for (int c = 0; c < N; ++c) nrm = fmax(nrm, colsum[c]);
-    int s = 0;
-    if (nrm > pd.theta13) s = (int)ceil(log2(nrm / pd.theta13));
-    s_sq = s;
-  }
-  __syncthreads();
-  const double sc = ldexp(1.0, -s_sq);
-  for (int i = threadIdx.x; i < NN; i += blockDim.x) A[i] *= sc;
-  __syncthreads();
-  mm(A2, A, A, N);
-  mm(A4, A2, A2, N);
-  mm(A6, A4, A2, N);
-  const double* b = pd.b;
-  for (int i = threadIdx.x; i < NN; i += blockDim.x) {
-    T1[i] = b[13] * A6[i] + b[11] * A4[i] + b[9] * A2[i];
-    T2[i] = b[12] * A6[i] + b[10] * A4[i] + b[8] * A2[i];
-  }
-  __syncthreads();
-  mm(U, A6, T1, N);   // U holds A6 (b13 A6 + b11 A4 + b9 A2)
-  mm(V, A6, T2, N);   // V holds A6 (b12 A6 + b10 A4 + b8 A2)
-  for (int i = threadIdx.x; i < NN; i += blockDim.x) {
-    int r = i / N, c = i % N;
-    double id = (r == c) ? 1.0 : 0.0;
-    T1[i] = U[i] + b[7] * A6[i] + b[5] * A4[i] + b[3] * A2[i] + b[1] * id;
-    V[i] = V[i] + b[6] * A6[i] + b[4] * A4[i] + b[2] * A2[i] + b[0] * id;
-  }
-  __syncthreads();
-  mm(U, A, T1, N);
-  // Q = V - U (in T1), P = V + U (in T2); solve Q X = P
-  for (int i = threadIdx.x; i < NN; i += blockDim.x) {
-    T1[i] = V[i] - U[i];
-    T2[i] = V[i] + U[i];
-  }
-  __syncthreads();
-  for (int k = 0; k < N; ++k) {
-    if (threadIdx.x < 32) {
-      double best = -1.0;
-      int br = k;
-      for (int r = k + threadIdx.x; r < N; r += 32) {
-        double v = fabs(T1[r * N + k]);
-        if (v > best) { best = v; br = r; }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        double ob = __shfl_down_sync(0xffffffffu, best, o);
-        int orow = __shfl_down_sync(0xffffffffu, br, o);
-        if (ob > best || (ob == best && orow < br)) { best = ob; br = orow; }
-      }
-      if (threadIdx.x == 0) piv = br;
-    }
-    __syncthreads();
-    const int pr = piv;
-    if (pr != k) {
-      for (int c = threadIdx.x; c < N; c += blockDim.x) {
-        double a1 = T1[k * N + c]; T1[k * N + c] = T1[pr * N + c]; T1[pr * N + c] = a1;
-        double a2 = T2[k * N + c]; T2[k * N + c] = T2[pr * N + c]; T2[pr * N + c] = a2;
-      }
-      __syncthreads();
-    }
-    const double inv = 1.0 / T1[k * N + k];
-    const int rows = N - k - 1;
-    const int w = (N - k - 1) + N;   // columns k+1..N-1 of Q, all of P
-    for (int t2 = threadIdx.x; t2 < rows * w; t2 += blockDim.x) {
-      int r = k + 1 + t2 / w, c = t2 % w;
-      double l = T1[r * N + k] * inv;
-      if (c < N - k - 1) {
-        int cc = k + 1 + c;
-        T1[r * N + cc] = fma(-l, T1[k * N + cc], T1[r * N + cc]);
-      } else {
-        int cc = c - (N - k - 1);
-        T2[r * N + cc] = fma(-l, T2[k * N + cc], T2[r * N + cc]);
-      }
-    }
-    __syncthreads();
-    // column k below the pivot is not read again
-  }
-  for (int k = N - 1; k >= 0; --k) {
-    const double inv = 1.0 / T1[k * N + k];
-    for (int c = threadIdx.x; c < N; c += blockDim.x) T2[k * N + c] *= inv;
-    __syncthreads();
-    for (int t2 = threadIdx.x; t2 < k * N; t2 += blockDim.x) {
-      int r = t2 / N, c = t2 % N;
-      T2[r * N + c] = fma(-T1[r * N + k], T2[k * N + c], T2[r * N + c]);
-    }
-    __syncthreads();
-  }
-  double* X = T2;
-  double* Y = T1;
-  for (int q = 0; q < s_sq; ++q) {
-    mm(Y, X, X, N);
-    double* tmp = X; X = Y; Y = tmp;
-  }
-  for (int i = threadIdx.x; i < NN; i += blockDim.x) {
-    int r = i / N, c = i % N;
-    F[(long long)r * ldh + c] = X[i];
-  }
-  if (threadIdx.x == 0) {
-    stat[0] = X[(jj - 1) * N + jj];   // F[jj-1][jj] for the error estimate
     stat[1] = (double)jj;
     stat[2] = t;
-    stat[3] = (double)s_sq;
     stat[4] = happy[0] ? 0.0 : H[(long long)jj * ldh + jj - 1];   // h_{j+1,j}
+    stat[5] = nrm;
+  }
+}
+
+struct MatEpi {
+  // C += cI * I + c1 * M1 + c2 * M2 + c3 * M3 (null matrices skipped)
+  double cI, c1, c2, c3;
+  const double* M1;
+  const double* M2;
+  const double* M3;
+  double alpha;   // C = alpha * A B + ...
+};
+
+__device__ __forceinline__ double mat_epi(const MatEpi& e, int r, int c, int N) {
+  double v = (r == c) ? e.cI : 0.0;
+  const int i = r * N + c;
+  if (e.M1) v = fma(e.c1, e.M1[i], v);
+  if (e.M2) v = fma(e.c2, e.M2[i], v);
+  if (e.M3) v = fma(e.c3, e.M3[i], v);
+  return v;
+}
+
+// C = alpha A B + epilogue; A or B null means the identity
+__global__ void __launch_bounds__(64) small_gemm_kernel(double* __restrict__ C, const double* __restrict__ A,
+                                                        const double* __restrict__ B, int N, MatEpi e) {
+  const int r = blockIdx.y * 8 + threadIdx.y, c = blockIdx.x * 8 + threadIdx.x;
+  if (r >= N || c >= N) return;
+  double s = 0.0;
+  if (A && B) {
+    for (int k = 0; k < N; ++k) s = fma(A[r * N + k], B[k * N + c], s);
+  } else if (A) {
+    s = A[r * N + c];
+  } else if (B) {
+    s = B[r * N + c];
+  } else {
+    s = (r == c) ? 1.0 : 0.0;
+  }
+  C[r * N + c] = e.alpha * s + mat_epi(e, r, c, N);
+}
+
+__global__ void expm_finish_kernel(const double* __restrict__ P, int N, double* F, int ldh, double* stat) {
+  for (int i = threadIdx.x + blockIdx.x * blockDim.x; i < N * N; i += blockDim.x * gridDim.x)
+    F[(long long)(i / N) * ldh + (i % N)] = P[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) stat[0] = P[(N - 2) * N + (N - 1)];   // F[j-1][j]
+}
+
+// z -= h1 V_A + h2 V_B (the two modified Gram-Schmidt updates, in that order),
+// then ||z||_2 -> *hsub with the happy-breakdown flag below tol
+__global__ void __launch_bounds__(RED_THREADS) update_norm_kernel(double* __restrict__ z, const double* __restrict__ VA,
+                                                                  const double* __restrict__ VB, const double* h1p,
+                                                                  const double* h2p, long long n, double* partials,
+                                                                  unsigned int* ticket, double* hsub, double tol,
+                                                                  int* happy, int happy_value) {
+  if (happy[0]) return;
+  const double h1 = VA ? *h1p : 0.0, h2 = *h2p;
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double v = z[i];
+    if (VA) v = fma(-h1, VA[i], v);
+    v = fma(-h2, VB[i], v);
+    z[i] = v;
+    acc = fma(v, v, acc);
+  }
+  double b = block_sum(acc);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = b;
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double sum = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) sum += __ldcg(partials + i);
+  sum = block_sum(sum);
+  if (threadIdx.x == 0) {
+    const double r = sqrt(sum);
+    *hsub = r;
+    if (r < tol) {
+      happy[0] = 1;
+      happy[1] = happy_value;
+    }
+    *ticket = 0u;
+  }
+}
+
+// V_next = z / *hsub in place, and V_next . V_B -> *c_out (used by the next
+// iteration's orthogonalisation)
+__global__ void __launch_bounds__(RED_THREADS) scale_dot_kernel(double* __restrict__ z, const double* __restrict__ VB,
+                                                                const double* hsub, long long n, double* partials,
+                                                                unsigned int* ticket, double* c_out, const int* happy) {
+  if (happy[0]) return;
+  const double r = 1.0 / *hsub;
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = z[i] * r;
+    z[i] = v;
+    acc = fma(v, VB[i], acc);
+  }
+  double b = block_sum(acc);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = b;
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double sum = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) sum += __ldcg(partials + i);
+  sum = block_sum(sum);
+  if (threadIdx.x == 0) {
+    *c_out = sum;
+    *ticket = 0u;
   }
 }
 
@@ -391,6 +386,23 @@ int launch_scale_inv(Ctx& c, double* y, const double* x, const double* s_dev, lo
   return cuda_status(cudaGetLastError());
 }
 
+int launch_update_norm(Ctx& c, double* z, const double* VA, const double* VB, const double* h1, const double* h2,
+                       long long N, double* hsub, double tol, int happy_value, cudaStream_t s) {
+  update_norm_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(z, VA, VB, h1, h2, N, c.d_partials,
+                                                       (unsigned int*)(c.d_flags + 8), hsub, tol, c.d_flags,
+                                                       happy_value);
+  c.launches++;
+  return cuda_status(cudaGetLastError());
+}
+
+int launch_scale_dot(Ctx& c, double* z, const double* VB, const double* hsub, long long N, double* c_out,
+                     cudaStream_t s) {
+  scale_dot_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(z, VB, hsub, N, c.d_partials, (unsigned int*)(c.d_flags + 8),
+                                                     c_out, c.d_flags);
+  c.launches++;
+  return cuda_status(cudaGetLastError());
+}
+
 int launch_set_tail(Ctx& c, double* x, long long n, int p, const double* vals, cudaStream_t s) {
   Tail t{};
   for (int l = 0; l < p && l < MAX_NB; ++l) t.v[l] = vals[l];
@@ -416,28 +428,75 @@ int launch_combine(Ctx& c, int j, long long n, cudaStream_t s) {
   return cuda_status(cudaGetLastError());
 }
 
-int launch_expm_hess(Ctx& c, int j, double tau, double tau_happy, cudaStream_t s) {
+int launch_expm_prep(Ctx& c, int j, double tau, double tau_happy, cudaStream_t s) {
   if (j + 1 > MAX_EXPM) return SW_EINVAL;
-  Pade pd{};
-  // Pade [13/13] coefficients b_k = (26-k)! 13! / (26! k! (13-k)!)
-  const int m = 13;
-  pd.b[0] = 1.0;
-  for (int k = 1; k <= m; ++k) pd.b[k] = pd.b[k - 1] * (double)(m - k + 1) / ((double)k * (double)(2 * m - k + 1));
-  // the b_k above are normalised to b_0 = 1 (Higham's table scales them by 26!/13!)
-  pd.theta13 = 5.371920351148152;  // Higham (2005), Table 2.3
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c.prof) {
     e0 = prof_event(c);
     e1 = prof_event(c);
     cudaEventRecord(e0, s);
   }
-  expm_kernel<<<1, EXPM_THREADS, 0, s>>>(c.d_H, c.ldh, j, tau, tau_happy, c.d_flags, c.d_F, c.d_expm_ws,
-                                         c.d_scal + 8, pd);
+  expm_prep_kernel<<<1, 256, 0, s>>>(c.d_H, c.ldh, j, tau, tau_happy, c.d_flags, c.d_expm_ws, c.d_scal + 8);
   if (c.prof) {
     cudaEventRecord(e1, s);
     prof_record(c, PK_EXPM, e0, e1);
   }
   c.launches++;
+  return cuda_status(cudaGetLastError());
+}
+
+int launch_expm_eval(Ctx& c, int N, double norm1, int* squarings, cudaStream_t s) {
+  if (N < 2 || N > MAX_EXPM || !std::isfinite(norm1)) return SW_EINVAL;
+  int sq = 0;
+  if (norm1 > kTaylorTheta) sq = (int)std::ceil(std::log2(norm1 / kTaylorTheta));
+  if (sq > 200) return SW_ENONFINITE;
+  if (squarings) *squarings = sq;
+  const long long NN = (long long)N * N;
+  double* A = c.d_expm_ws;
+  double* X = A + NN;
+  double* X2 = X + NN;
+  double* X3 = X2 + NN;
+  double* X4 = X3 + NN;
+  double* P0 = X4 + NN;
+  double* P1 = P0 + NN;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c.prof) {
+    e0 = prof_event(c);
+    e1 = prof_event(c);
+    cudaEventRecord(e0, s);
+  }
+  double cf[17];
+  cf[0] = 1.0;
+  for (int k = 1; k <= 16; ++k) cf[k] = cf[k - 1] / k;   // 1/k!
+  const dim3 blk(8, 8), grd((N + 7) / 8, (N + 7) / 8);
+  const MatEpi none{0, 0, 0, 0, nullptr, nullptr, nullptr, 1.0};
+  MatEpi sc = none;
+  sc.alpha = std::ldexp(1.0, -sq);
+  small_gemm_kernel<<<grd, blk, 0, s>>>(X, A, nullptr, N, sc);               // X = A / 2^s
+  small_gemm_kernel<<<grd, blk, 0, s>>>(X2, X, X, N, none);
+  small_gemm_kernel<<<grd, blk, 0, s>>>(X3, X2, X, N, none);
+  small_gemm_kernel<<<grd, blk, 0, s>>>(X4, X2, X2, N, none);
+  // Paterson-Stockmeyer: T = B0 + X4 (B1 + X4 (B2 + X4 (B3 + c16 X4))), B_i = sum_k c_{4i+k} X^k
+  MatEpi b3{cf[12], cf[13], cf[14], cf[15], X, X2, X3, cf[16]};
+  small_gemm_kernel<<<grd, blk, 0, s>>>(P0, X4, nullptr, N, b3);
+  MatEpi b2{cf[8], cf[9], cf[10], cf[11], X, X2, X3, 1.0};
+  small_gemm_kernel<<<grd, blk, 0, s>>>(P1, X4, P0, N, b2);
+  MatEpi b1{cf[4], cf[5], cf[6], cf[7], X, X2, X3, 1.0};
+  small_gemm_kernel<<<grd, blk, 0, s>>>(P0, X4, P1, N, b1);
+  MatEpi b0{cf[0], cf[1], cf[2], cf[3], X, X2, X3, 1.0};
+  small_gemm_kernel<<<grd, blk, 0, s>>>(P1, X4, P0, N, b0);
+  double* cur = P1;
+  double* nxt = P0;
+  for (int q = 0; q < sq; ++q) {
+    small_gemm_kernel<<<grd, blk, 0, s>>>(nxt, cur, cur, N, none);
+    double* t = cur; cur = nxt; nxt = t;
+  }
+  expm_finish_kernel<<<(unsigned)((NN + 255) / 256), 256, 0, s>>>(cur, N, c.d_F, c.ldh, c.d_scal + 8);
+  if (c.prof) {
+    cudaEventRecord(e1, s);
+    prof_record(c, PK_EXPM, e0, e1);
+  }
+  c.launches += 10 + sq;
   return cuda_status(cudaGetLastError());
 }
 

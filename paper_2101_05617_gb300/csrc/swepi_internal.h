@@ -35,6 +35,16 @@ enum FaceCoef {
   FC_COUNT
 };
 
+// Per-node coefficients of the imaginary half of the complex-step JVP at a
+// linearisation point (dfr_split.cu).
+enum LinNode {
+  LN_U1 = 0, LN_U2,
+  LN_A11, LN_A12, LN_A22,           // Im sqrt(g)T^ij coefficient of Im q^0
+  LN_S11, LN_S12, LN_S10,           // Im S^1 = s11 Im q^1 + s12 Im q^2 + s10 Im q^0
+  LN_S21, LN_S22, LN_S20,
+  LN_COUNT
+};
+
 // One face line = the N_s points shared by two element edges.
 struct FaceLine {
   int owner, owner_edge;   // element index, edge 0=W 1=E 2=S 3=N
@@ -81,6 +91,8 @@ struct Ctx {
   double* d_F = nullptr;
   double* d_expm_ws = nullptr;    // expm workspace
   double* d_partials = nullptr;   // reduction partials
+  double* d_vpart = nullptr;      // partials of the epilogue dot products (2 per volume block)
+  double* d_cdot = nullptr;       // V_j . V_{j-1} per basis index
   double* d_scal = nullptr;       // device scalars (see kiops.cu)
   int* d_flags = nullptr;         // happy flag, happy size
   double* h_pinned = nullptr;     // pinned read-back area
@@ -97,20 +109,25 @@ struct Ctx {
   int hist_head = 0;              // slot of the most recent entry
   int m_warm = 0;                 // KIOPS warm start (0 = none)
   long long launches = 0;
+  // split JVP (dfr_split.cu): coefficients of the imaginary half at the last linearisation point
+  int jvp_mode = 1;                 // 0 = plain complex-step evaluation per JVP, 1 = split
+  bool linearized = false;
+  double* d_lin_node = nullptr;     // [LN_COUNT][nodes]
+  double* d_lin_face = nullptr;     // [18][nfacepts]
   // event profiling (sw_profile)
   bool prof = false;
   struct ProfRec { int kind; cudaEvent_t a, b; };
   std::vector<ProfRec> prof_pending;
   std::vector<cudaEvent_t> prof_pool;
-  long long prof_count[5] = {};
-  double prof_ms[5] = {};
+  long long prof_count[6] = {};
+  double prof_ms[6] = {};
 };
 
 // event profiling helpers (capi.cu)
 cudaEvent_t prof_event(Ctx& c);
 void prof_record(Ctx& c, int kind, cudaEvent_t a, cudaEvent_t b);
 void prof_drain(Ctx& c);
-enum ProfKind { PK_FACE_JVP = 0, PK_VOL_JVP = 1, PK_FACE_RHS = 2, PK_VOL_RHS = 3, PK_EXPM = 4 };
+enum ProfKind { PK_FACE_JVP = 0, PK_VOL_JVP = 1, PK_FACE_RHS = 2, PK_VOL_RHS = 3, PK_EXPM = 4, PK_LIN = 5 };
 
 // ---- geometry / tables (geom.cpp)
 int build_tables(Ctx& c);
@@ -128,10 +145,24 @@ struct AugEpilogue {
   const double* tail_in = nullptr;  // p doubles (device)
   double* tail_out = nullptr;       // p doubles (device): (tail_in[1..p-1], 0)
   const int* skip = nullptr;        // if non-null and *skip != 0 the kernels return
+  // incomplete orthogonalisation fused into the epilogue (window of two): with
+  // dotB set, h2 = V_B . z - h1 (V_B . V_A) and h1 = V_A . z are formed over the
+  // augmented length n + p (block partials, last block finalises)
+  const double* dotA = nullptr;     // V_{j-1} (null for the first basis vector)
+  const double* dotB = nullptr;     // V_j
+  const double* cprev = nullptr;    // V_j . V_{j-1}
+  double* h1_out = nullptr;
+  double* h2_out = nullptr;
+  double* dpart = nullptr;          // 2 doubles per block
+  unsigned int* dticket = nullptr;
+  long long n = 0;
 };
 int launch_rhs(Ctx& c, const double* q, double* F, cudaStream_t s);
 int launch_jvp(Ctx& c, const double* q, const double* v, double eps, double* out,
                const AugEpilogue& ep, cudaStream_t s);
+// split JVP: evaluate the real half at q, then imaginary halves for any v
+int launch_linearize(Ctx& c, const double* q, cudaStream_t s);
+int launch_jvp_lin(Ctx& c, const double* v, double* out, const AugEpilogue& ep, cudaStream_t s);
 // the JVP with a caller-supplied interface-flux buffer (nelem * 12 * ns doubles)
 int launch_jvp_fb(Ctx& c, const double* q, const double* v, double eps, double* out, double* fb,
                   cudaStream_t s);
@@ -147,16 +178,27 @@ int launch_axpy_dev(Ctx& c, double* y, const double* x, const double* alpha, lon
                     const int* skip, cudaStream_t s);
 int launch_scale_inv(Ctx& c, double* y, const double* x, const double* s_dev, long long n,
                      const int* skip, cudaStream_t s);
-int launch_expm_hess(Ctx& c, int j, double tau, double tau_happy, cudaStream_t s);
+// small exponential: prep builds A = t [[H_j, e_1], [0, 0]] and its 1-norm
+// (device scalars), eval evaluates exp(A) into F once the host knows N and the norm
+int launch_expm_prep(Ctx& c, int j, double tau, double tau_happy, cudaStream_t s);
+int launch_expm_eval(Ctx& c, int N, double norm1, int* squarings, cudaStream_t s);
 int launch_combine(Ctx& c, int j, long long n, cudaStream_t s);
+// fused incomplete orthogonalisation (window two) after an epilogue with dots:
+// z -= h1 V_A + h2 V_B and ||z|| -> *hsub (happy flag below tol), then
+// V_next = z / *hsub and V_next . V_B -> *c_out
+int launch_update_norm(Ctx& c, double* z, const double* VA, const double* VB, const double* h1, const double* h2,
+                       long long N, double* hsub, double tol, int happy_value, cudaStream_t s);
+int launch_scale_dot(Ctx& c, double* z, const double* VB, const double* hsub, long long N, double* c_out,
+                     cudaStream_t s);
 double fp64_fma_peak_tflops();
 int launch_set_tail(Ctx& c, double* x, long long n, int p, const double* vals, cudaStream_t s);
 int launch_lincomb(Ctx& c, double* out, long long n, int k, const double* const* xs,
                    const double* coef, cudaStream_t s);
 
 // ---- drivers
+// use_lin: JVPs by the split path (launch_linearize must have been called at q_lin)
 int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, const double* const* b,
-              const sw_kiops_opts& o, double* w, sw_kiops_stats* st, cudaStream_t s);
+              const sw_kiops_opts& o, double* w, sw_kiops_stats* st, cudaStream_t s, bool use_lin);
 int ensure_krylov(Ctx& c, int m_max);
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? SW_OK : SW_ECUDA; }

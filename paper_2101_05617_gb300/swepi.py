@@ -41,9 +41,9 @@ class sw_kiops_opts(ctypes.Structure):
 
 
 class sw_profile_stats(ctypes.Structure):
-    _fields_ = [("count", ctypes.c_longlong * 5), ("ms", ctypes.c_double * 5)]
+    _fields_ = [("count", ctypes.c_longlong * 6), ("ms", ctypes.c_double * 6)]
 
-    KINDS = ("face_jvp", "volume_jvp", "face_rhs", "volume_rhs", "expm")
+    KINDS = ("face_jvp", "volume_jvp", "face_rhs", "volume_rhs", "expm", "linearize")
 
     def as_dict(self):
         return {k: {"count": int(self.count[i]), "ms": float(self.ms[i])} for i, k in enumerate(self.KINDS)}
@@ -81,6 +81,9 @@ def lib():
     L.sw_rhs.argtypes = [vp, vp, vp, vp]
     L.sw_jvp.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp]
     L.sw_jvp_static_scratch.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp]
+    L.sw_linearize.argtypes = [vp, vp, vp]
+    L.sw_jvp_linearized.argtypes = [vp, vp, vp, vp]
+    L.sw_set_jvp_mode.argtypes = [vp, ip]
     L.sw_kiops_phi.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, ip, ctypes.POINTER(vp),
                                ctypes.POINTER(sw_kiops_opts), vp, ctypes.POINTER(sw_kiops_stats), vp]
     L.sw_epi_step.argtypes = [vp, ip, ctypes.c_double, vp, ctypes.POINTER(sw_kiops_opts),
@@ -99,7 +102,8 @@ def lib():
 
 
 EXPORTED = ["sw_init", "sw_free", "sw_num_unknowns", "sw_grid_info", "sw_node_xyz", "sw_state_from_fields",
-            "sw_set_bottom", "sw_rhs", "sw_jvp", "sw_jvp_static_scratch", "sw_kiops_phi", "sw_epi_step", "sw_epi_set_history",
+            "sw_set_bottom", "sw_rhs", "sw_jvp", "sw_jvp_static_scratch", "sw_linearize", "sw_jvp_linearized",
+            "sw_set_jvp_mode", "sw_kiops_phi", "sw_epi_step", "sw_epi_set_history",
             "sw_epi_reset", "sw_kernel_launches", "sw_profile", "sw_profile_read", "sw_fp64_fma_peak",
             "sw_status_str"]
 
@@ -192,6 +196,20 @@ def sw_jvp_static_scratch(ctx, q, v, eps, Jv, stream=None):
     n = sw_num_unknowns(ctx)
     _check("sw_jvp_static_scratch", lib().sw_jvp_static_scratch(ctx, _dev_ptr(q, n), _dev_ptr(v, n), float(eps),
                                                                 _dev_ptr(Jv, n), _stream(stream)))
+
+
+def sw_linearize(ctx, q, stream=None):
+    n = sw_num_unknowns(ctx)
+    _check("sw_linearize", lib().sw_linearize(ctx, _dev_ptr(q, n), _stream(stream)))
+
+
+def sw_jvp_linearized(ctx, v, Jv, stream=None):
+    n = sw_num_unknowns(ctx)
+    _check("sw_jvp_linearized", lib().sw_jvp_linearized(ctx, _dev_ptr(v, n), _dev_ptr(Jv, n), _stream(stream)))
+
+
+def sw_set_jvp_mode(ctx, mode):
+    _check("sw_set_jvp_mode", lib().sw_set_jvp_mode(ctx, int(mode)))
 
 
 def sw_kiops_phi(ctx, q_lin, dt, tau_out, b, w, opts=None, stream=None):
@@ -287,6 +305,18 @@ class SWContext:
         out = torch.empty_like(q) if out is None else out
         sw_jvp(self.handle, q, v, eps, out, stream)
         return out
+
+    def linearize(self, q, stream=None):
+        sw_linearize(self.handle, q, stream)
+
+    def jvp_linearized(self, v, out=None, stream=None):
+        import torch
+        out = torch.empty_like(v) if out is None else out
+        sw_jvp_linearized(self.handle, v, out, stream)
+        return out
+
+    def set_jvp_mode(self, mode):
+        sw_set_jvp_mode(self.handle, mode)
 
     def kiops_phi(self, q_lin, dt, b, tau_out=1.0, out=None, stream=None, **opts):
         import torch

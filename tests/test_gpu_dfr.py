@@ -129,3 +129,33 @@ def test_full_size_parity(ne, ns, workload):
     Jv = ctx.jvp(qd, torch.tensor(v.reshape(-1), device="cuda")).cpu().numpy()
     err = scaled_err_per_var(Jv, osw.jvp(g, q, v), term_scale(g, q, v))
     assert max(err) < TOL_JVP, err
+
+
+@pytest.mark.parametrize("ne,ns,seed,bottom", CASES)
+def test_split_jvp_parity(ne, ns, seed, bottom):
+    """sw_linearize + sw_jvp_linearized (real half once, imaginary half per v)
+    against the oracle's complex-step JVP, and against the plain sw_jvp."""
+    _, g, q, hB = oracle_case(ne, ns, seed=seed, bottom_amp=bottom)
+    ctx = _ctx(g)
+    ctx.set_bottom(hB.reshape(-1))
+    qd = torch.tensor(q.reshape(-1), device="cuda")
+    ctx.linearize(qd)
+    for k in range(2):
+        v = scaled_direction(q, seed + 200 + k)
+        vd = torch.tensor(v.reshape(-1), device="cuda")
+        Jv = ctx.jvp_linearized(vd).cpu().numpy()
+        ref = osw.jvp(g, q, v, 1e-30)
+        err = scaled_err_per_var(Jv, ref, term_scale(g, q, v))
+        assert max(err) < TOL_JVP, (k, err)
+        plain = ctx.jvp(qd, vd).cpu().numpy()
+        err2 = scaled_err_per_var(Jv, plain, term_scale(g, q, v))
+        assert max(err2) < TOL_JVP, (k, err2)
+
+
+def test_split_requires_linearize():
+    from paper_2101_05617_gb300 import swepi
+    _, g, q, _ = oracle_case(2, 3, seed=1)
+    ctx = _ctx(g)
+    v = torch.ones(ctx.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(swepi.SWError):
+        ctx.jvp_linearized(v)
