@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--workload", default="ne60_p5")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
     return ap.parse_args()
 
 
@@ -163,6 +164,49 @@ def oracle_sample(wl, seed, krylov_per_step, P, budget_s=15.0):
                        f"updates at n_e={wl.ne}, p={wl.p}; EPI{wl.order} step projected as "
                        f"({krylov_per_step:.0f} Krylov + {P} remainder) JVPs + orthogonalisation + RHS"),
             "jvp_dof_per_s": wl.n_unknowns / t_one}
+
+
+def fp32_form_comparison(args, dev):
+    """The complex64-bulk form against the FP64 path on its own workload
+    (6 x 30 x 30, p = 5, EPI5, dt = 1800 s): steps/s of both, the FP32-vs-FP64
+    state difference after the run and the EPI time-discretisation error (FP64
+    at dt against dt/4).  On the n_e = 60 grid the form is not used: the
+    incomplete orthogonalisation amplifies its FP32 noise beyond the step's
+    accuracy (DESIGN.md)."""
+    import torch
+
+    from paper_2101_05617_gb300 import swepi, synth
+    wl = synth.WORKLOADS["ne30_p5"]
+    f = synth.make_fields(wl, args.seed)
+    res = {}
+    states = {}
+    for name, mode, dt, mult in (("fp64", 1, wl.dt, 1), ("complex64_bulk", 2, wl.dt, 1), ("fp64_dt4", 1, wl.dt / 4, 4)):
+        ctx = swepi.SWContext(wl.ne, wl.p, f.rotation)
+        h, hB, V = f.evaluate(ctx.node_xyz())
+        q = torch.tensor(ctx.state_from_fields(h, hB, V), device=dev)
+        ctx.set_jvp_mode(mode)
+        for _ in range(args.warmup * mult):
+            ctx.epi_step(wl.order, dt, q, tol=wl.tol)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps * mult):
+            ctx.epi_step(wl.order, dt, q, tol=wl.tol)
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = args.steps * mult / (e0.elapsed_time(e1) * 1e-3)
+        states[name] = q.view(3, -1).clone()
+        ctx.close()
+
+    def rel(a, b):
+        return [float(torch.linalg.norm(a[k] - b[k]) / torch.linalg.norm(b[k])) for k in range(3)]
+    return {"workload": "ne30_p5: 6x30x30 elements, p=5, EPI5, dt=1800 s, KIOPS tol 1e-10",
+            "fp64_steps_per_s": res["fp64"], "complex64_bulk_steps_per_s": res["complex64_bulk"],
+            "speedup": res["complex64_bulk"] / res["fp64"],
+            "err_vs_fp64_rel_l2": rel(states["complex64_bulk"], states["fp64"]),
+            "time_discretisation_err_rel_l2": rel(states["fp64"], states["fp64_dt4"]),
+            "steps": args.warmup + args.steps}
 
 
 # Krylov iterations per EPI5 step of the GPU path on the default workload
@@ -312,7 +356,10 @@ def main():
                "e2e": {"value": total_steps / (e2e_max * 1e-3), "unit": UNIT,
                        "h2d_bytes_per_step": 8 * wl.n_unknowns, "d2h_bytes_per_step": 8 * wl.n_unknowns},
                "gpu_launches": launches,
-               "roofline": roofline}
+               "roofline": roofline,
+               "forms": {"fp64_split": {"value": value, "unit": UNIT}}}
+        if not args.no_forms:
+            out["forms"]["complex64_bulk_ne30_p5"] = fp32_form_comparison(args, dev)
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = oracle_sample(wl, args.seed, krylov / args.steps, P)
         print(json.dumps(out), flush=True)

@@ -141,9 +141,15 @@ int sw_jvp_static_scratch(sw_ctx_t ctx, const double* q_dev, const double* v_dev
 int sw_linearize(sw_ctx_t ctx, const double* q_dev, void* stream);
 int sw_jvp_linearized(sw_ctx_t ctx, const double* v_dev, double* Jv_dev, void* stream);
 
-/* How sw_kiops_phi and sw_epi_step evaluate their JVPs: 0 = sw_jvp per Krylov
- * vector, 1 = sw_linearize once per linearisation point then
- * sw_jvp_linearized (default). */
+/* How sw_kiops_phi, sw_epi_step and sw_jvp_linearized evaluate their JVPs:
+ * 0 = sw_jvp per Krylov vector; 1 = sw_linearize once per linearisation point
+ * then the imaginary half per vector in FP64 (default); 2 = the complex64-bulk
+ * form: as 1 but the imaginary half of the Krylov JVPs runs in FP32
+ * (coefficient tables rounded from the FP64 linearisation, FP32 accumulation),
+ * while the Krylov basis, the orthogonalisation dot products, the small
+ * exponential, the error estimate and the EPI remainder products (a small
+ * difference of large terms, Eq. 33) stay FP64.  Changing the mode invalidates the last
+ * linearisation. */
 int sw_set_jvp_mode(sw_ctx_t ctx, int mode);
 
 /* w = sum_{k=0}^{nb-1} tau_out^k phi_k(tau_out dt J(q_lin)) b_k (Eq. 29), J by

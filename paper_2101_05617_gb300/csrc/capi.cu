@@ -102,7 +102,7 @@ int phi_call(Ctx& c, const double* q, double dt, int nb, const double* const* b,
   sw_kiops_opts o = o0;
   if (c.m_warm > 0) o.m_init = c.m_warm;
   sw_kiops_stats st{};
-  int rc = kiops_run(c, q, dt, 1.0, nb, b, o, w, &st, s, c.jvp_mode == 1);
+  int rc = kiops_run(c, q, dt, 1.0, nb, b, o, w, &st, s, c.jvp_mode >= 1);
   if (rc) return rc;
   c.m_warm = st.m_final;
   add_stats(acc, st);
@@ -116,7 +116,7 @@ int epi2_inplace(Ctx& c, double* q, const double* F, double h, const sw_kiops_op
   const double* xs[1] = {F};
   double cf[1] = {h};
   if ((rc = launch_lincomb(c, c.d_b[0], c.n, 1, xs, cf, s))) return rc;
-  if (c.jvp_mode == 1 && (rc = launch_linearize(c, q, s))) return rc;
+  if (c.jvp_mode >= 1 && (rc = launch_linearize(c, q, s))) return rc;
   const double* b[2] = {nullptr, c.d_b[0]};
   if ((rc = phi_call(c, q, h, 2, b, o, c.d_tmp, acc, s))) return rc;
   const double* ys[2] = {q, c.d_tmp};
@@ -234,6 +234,8 @@ void sw_free(sw_ctx_t c) {
   double* ptrs[] = {c->d_node_coef, c->d_face_coef, c->d_fb, c->d_V, c->d_X, c->d_H, c->d_F, c->d_expm_ws,
                     c->d_partials, c->d_scal, c->d_Fn, c->d_tmp, c->d_tmp2, c->d_lin_node, c->d_lin_face,
                     c->d_vpart, c->d_cdot};
+  if (c->d_lin_node32) cudaFree(c->d_lin_node32);
+  if (c->d_lin_face32) cudaFree(c->d_lin_face32);
   for (double* p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i < MAX_HIST; ++i) {
@@ -299,8 +301,8 @@ int sw_kiops_phi(sw_ctx_t c, const double* q_lin, double dt, double tau_out, int
   sw_kiops_opts o = opts ? *opts : default_opts();
   cudaStream_t s = as_stream(stream);
   int rc;
-  if (c->jvp_mode == 1 && (rc = launch_linearize(*c, q_lin, s))) return rc;
-  rc = kiops_run(*c, q_lin, dt, tau_out, nb, b, o, w, st, s, c->jvp_mode == 1);
+  if (c->jvp_mode >= 1 && (rc = launch_linearize(*c, q_lin, s))) return rc;
+  rc = kiops_run(*c, q_lin, dt, tau_out, nb, b, o, w, st, s, c->jvp_mode >= 1);
   return rc;
 }
 
@@ -360,7 +362,7 @@ int sw_epi_step(sw_ctx_t c, int order, double dt, double* q, const sw_kiops_opts
     return cuda_status(cudaStreamSynchronize(s));
   }
   // remainders R(q_{n-i}) = F(q_{n-i}) - F_n - J_n (q_{n-i} - q_n)  (Eq. 33)
-  const bool split = c->jvp_mode == 1;
+  const bool split = c->jvp_mode >= 1;
   if (split && (rc = launch_linearize(*c, q, s))) return rc;
   for (int i = 1; i <= P; ++i) {
     int slot = hist_slot(*c, i);
@@ -368,7 +370,9 @@ int sw_epi_step(sw_ctx_t c, int order, double dt, double* q, const sw_kiops_opts
     double c1[2] = {1.0, -1.0};
     if ((rc = launch_lincomb(*c, c->d_tmp, n, 2, d1, c1, s))) return rc;
     AugEpilogue ep;
-    rc = split ? launch_jvp_lin(*c, c->d_tmp, c->d_tmp2, ep, s) : launch_jvp(*c, q, c->d_tmp, kEpsJvp, c->d_tmp2, ep, s);
+    // the remainder is a small difference of large terms: its JVP stays FP64 in every mode
+    rc = split ? launch_jvp_lin(*c, c->d_tmp, c->d_tmp2, ep, s, false)
+               : launch_jvp(*c, q, c->d_tmp, kEpsJvp, c->d_tmp2, ep, s);
     if (rc) return rc;
     const double* d2[3] = {c->d_hF[slot], c->d_Fn, c->d_tmp2};
     double c2[3] = {1.0, -1.0, -1.0};
@@ -396,7 +400,8 @@ int sw_epi_step(sw_ctx_t c, int order, double dt, double* q, const sw_kiops_opts
 long long sw_kernel_launches(sw_ctx_t c) { return c ? c->launches : -1; }
 
 int sw_set_jvp_mode(sw_ctx_t c, int mode) {
-  if (!c || (mode != 0 && mode != 1)) return SW_EINVAL;
+  if (!c || mode < 0 || mode > 2) return SW_EINVAL;
+  if (mode != c->jvp_mode) c->linearized = false;
   c->jvp_mode = mode;
   return SW_OK;
 }
@@ -410,7 +415,7 @@ int sw_jvp_linearized(sw_ctx_t c, const double* v, double* Jv, void* stream) {
   if (!c || !v || !Jv || v == Jv) return SW_EINVAL;
   if (!c->linearized) return SW_EINVAL;
   AugEpilogue ep;
-  return launch_jvp_lin(*c, v, Jv, ep, as_stream(stream));
+  return launch_jvp_lin(*c, v, Jv, ep, as_stream(stream), c->jvp_mode == 2);
 }
 
 }  // extern "C"

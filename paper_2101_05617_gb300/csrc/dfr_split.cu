@@ -109,34 +109,56 @@ __global__ void __launch_bounds__(128) lin_face_kernel(LinFaceArgs a, DfrConst d
 }
 
 // ---------------------------------------------------------------- tangent
+// The imaginary half in arithmetic type T: double (the FP64 path) or float
+// (the complex64-bulk form: tables rounded from the FP64 linearisation, FP32
+// accumulation).  Krylov vectors in and out stay FP64; the epilogue (augmented
+// operator and orthogonalisation dots) is FP64 in both.
+template <typename T, int NS>
+__device__ __forceinline__ void trace_tan(const double* __restrict__ v, long long nodes, int elem, int edge, int i,
+                                          const DfrConst& dc, T out[3]) {
+  const long long base = (long long)elem * NS * NS;
+  const double* w = (edge == 0 || edge == 2) ? dc.lm : dc.lp;
+#pragma unroll
+  for (int var = 0; var < 3; ++var) {
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      const long long idx = base + ((edge <= 1) ? (i * NS + k) : (k * NS + i)) + var * nodes;
+      acc = fma(T(w[k]), T(__ldg(v + idx)), acc);
+    }
+    out[var] = acc;
+  }
+}
+
+template <typename T>
 struct TanFaceArgs {
   const double* v;
   long long nodes;
   const FaceLine* lines;
   const double* fc;
-  const double* lf;
+  const T* lf;
   long long nfacepts;
-  double* fb;
+  T* fb;
   const int* skip;
 };
 
-template <int NS>
-__global__ void __launch_bounds__(128) face_tangent_kernel(TanFaceArgs a, DfrConst dc) {
+template <typename T, int NS>
+__global__ void __launch_bounds__(128) face_tangent_kernel(TanFaceArgs<T> a, DfrConst dc) {
   if (a.skip && *a.skip) return;
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= a.nfacepts) return;
   const int line = (int)(t / NS), i = (int)(t % NS);
   const FaceLine L = a.lines[line];
   const int in = L.reversed ? NS - 1 - i : i;
-  double vo[3], vn[3];
-  trace<double, NS>(a.v, nullptr, 0.0, a.nodes, L.owner, L.owner_edge, i, dc, vo);
-  trace<double, NS>(a.v, nullptr, 0.0, a.nodes, L.nbr, L.nbr_edge, in, dc, vn);
+  T vo[3], vn[3];
+  trace_tan<T, NS>(a.v, a.nodes, L.owner, L.owner_edge, i, dc, vo);
+  trace_tan<T, NS>(a.v, a.nodes, L.nbr, L.nbr_edge, in, dc, vn);
   const long long P = a.nfacepts;
-  const double* lf = a.lf + t;
-  double f[3];
+  const T* lf = a.lf + t;
+  T f[3];
 #pragma unroll
   for (int mu = 0; mu < 3; ++mu) {
-    double s = lf[(mu * 3) * P] * vo[0];
+    T s = lf[(mu * 3) * P] * vo[0];
     s = fma(lf[(mu * 3 + 1) * P], vo[1], s);
     s = fma(lf[(mu * 3 + 2) * P], vo[2], s);
     s = fma(lf[(9 + mu * 3) * P], vn[0], s);
@@ -145,37 +167,39 @@ __global__ void __launch_bounds__(128) face_tangent_kernel(TanFaceArgs a, DfrCon
     f[mu] = s;
   }
   const double* fc = a.fc + t;
-  const double sig = fc[FC_SIG * P];
-  const double M00 = fc[FC_M00 * P], M01 = fc[FC_M01 * P], M10 = fc[FC_M10 * P], M11 = fc[FC_M11 * P];
-  double* fo = a.fb + ((long long)L.owner * 4 + L.owner_edge) * 3 * NS + i;
+  const T sig = T(fc[FC_SIG * P]);
+  const T M00 = T(fc[FC_M00 * P]), M01 = T(fc[FC_M01 * P]), M10 = T(fc[FC_M10 * P]), M11 = T(fc[FC_M11 * P]);
+  T* fo = a.fb + ((long long)L.owner * 4 + L.owner_edge) * 3 * NS + i;
   fo[0] = f[0];
   fo[NS] = f[1];
   fo[2 * NS] = f[2];
-  double* fn = a.fb + ((long long)L.nbr * 4 + L.nbr_edge) * 3 * NS + in;
+  T* fn = a.fb + ((long long)L.nbr * 4 + L.nbr_edge) * 3 * NS + in;
   fn[0] = sig * f[0];
   fn[NS] = M00 * f[1] + M01 * f[2];
   fn[2 * NS] = M10 * f[1] + M11 * f[2];
 }
 
+template <typename T>
 struct TanVolArgs {
   const double* v;
   long long nodes;
   long long nelem;
-  const double* ln;
-  const double* fb;
+  const T* ln;
+  const T* fb;
   double* out;
   AugEpilogue ep;
 };
 
-template <int NS>
-__global__ void __launch_bounds__(VolShape<NS>::THREADS) volume_tangent_kernel(TanVolArgs a, DfrConst dc) {
+template <typename T, int NS>
+__global__ void __launch_bounds__(VolShape<NS>::THREADS) volume_tangent_kernel(TanVolArgs<T> a, DfrConst dc) {
   constexpr int EPB = VolShape<NS>::EPB;
   constexpr int NN = NS * NS;
   if (a.ep.skip && *a.ep.skip) return;
-  __shared__ double sF[EPB][2][3][NN];
-  __shared__ double sB[EPB][4][3][NS];
-  __shared__ double sD[NS][NS + 3];          // padded rows: distinct banks per k
-  for (int t = threadIdx.x; t < NS * (NS + 2); t += blockDim.x) sD[t / (NS + 2)][t % (NS + 2)] = dc.D[t / (NS + 2)][t % (NS + 2)];
+  __shared__ T sF[EPB][2][3][NN];
+  __shared__ T sB[EPB][4][3][NS];
+  __shared__ T sD[NS][NS + 3];          // padded rows: distinct banks per k
+  for (int t = threadIdx.x; t < NS * (NS + 2); t += blockDim.x)
+    sD[t / (NS + 2)][t % (NS + 2)] = T(dc.D[t / (NS + 2)][t % (NS + 2)]);
   const int le = threadIdx.x / NN, node = threadIdx.x % NN;
   const long long elem = (long long)blockIdx.x * EPB + le;
   const bool active = elem < a.nelem;
@@ -184,17 +208,17 @@ __global__ void __launch_bounds__(VolShape<NS>::THREADS) volume_tangent_kernel(T
   for (int t = threadIdx.x; t < EPB * 12 * NS; t += blockDim.x) {
     int e = t / (12 * NS), r = t % (12 * NS);
     long long ge = (long long)blockIdx.x * EPB + e;
-    (&sB[e][0][0][0])[r] = (ge < a.nelem) ? a.fb[ge * 12 * NS + r] : 0.0;
+    (&sB[e][0][0][0])[r] = (ge < a.nelem) ? a.fb[ge * 12 * NS + r] : T(0);
   }
-  double S1 = 0.0, S2 = 0.0;
+  T S1 = T(0), S2 = T(0);
   const long long N = a.nodes;
   if (active) {
-    const double v0 = __ldg(a.v + idx), v1 = __ldg(a.v + idx + N), v2 = __ldg(a.v + idx + 2 * N);
-    const double* ln = a.ln + idx;
-    const double u1 = ln[LN_U1 * N], u2 = ln[LN_U2 * N];
-    const double F11 = fma(2.0 * u1, v1, ln[LN_A11 * N] * v0);
-    const double F12 = fma(u2, v1, fma(u1, v2, ln[LN_A12 * N] * v0));
-    const double F22 = fma(2.0 * u2, v2, ln[LN_A22 * N] * v0);
+    const T v0 = T(__ldg(a.v + idx)), v1 = T(__ldg(a.v + idx + N)), v2 = T(__ldg(a.v + idx + 2 * N));
+    const T* ln = a.ln + idx;
+    const T u1 = ln[LN_U1 * N], u2 = ln[LN_U2 * N];
+    const T F11 = fma(T(2) * u1, v1, ln[LN_A11 * N] * v0);
+    const T F12 = fma(u2, v1, fma(u1, v2, ln[LN_A12 * N] * v0));
+    const T F22 = fma(T(2) * u2, v2, ln[LN_A22 * N] * v0);
     S1 = fma(ln[LN_S11 * N], v1, fma(ln[LN_S12 * N], v2, ln[LN_S10 * N] * v0));
     S2 = fma(ln[LN_S21 * N], v1, fma(ln[LN_S22 * N], v2, ln[LN_S20 * N] * v0));
     sF[le][0][0][node] = v1;
@@ -205,30 +229,36 @@ __global__ void __launch_bounds__(VolShape<NS>::THREADS) volume_tangent_kernel(T
     sF[le][1][2][node] = F22;
   }
   __syncthreads();
-  const double src[3] = {0.0, S1, S2};
+  const T src[3] = {T(0), S1, S2};
   double res[3] = {0.0, 0.0, 0.0};
-  // this thread's rows of the derivative matrix, from shared memory into registers
-  // (a per-thread row index into the constant bank would serialise the warp)
-  double Da[NS + 2], Db[NS + 2];
-#pragma unroll
-  for (int n = 0; n < NS + 2; ++n) {
-    Da[n] = sD[k1][n];
-    Db[n] = sD[k2][n];
-  }
   if (active) {
+    // this thread's rows of the derivative matrix, from shared memory into registers
+    // (a per-thread row index into the constant bank would serialise the warp)
+    T Da[NS + 2], Db[NS + 2];
+#pragma unroll
+    for (int n = 0; n < NS + 2; ++n) {
+      Da[n] = sD[k1][n];
+      Db[n] = sD[k2][n];
+    }
+    const T tdx = T(dc.two_over_dx);
 #pragma unroll
     for (int mu = 0; mu < 3; ++mu) {
-      double d1 = Da[0] * sB[le][0][mu][k2] + Da[NS + 1] * sB[le][1][mu][k2];
-      double d2 = Db[0] * sB[le][2][mu][k1] + Db[NS + 1] * sB[le][3][mu][k1];
+      T d1 = Da[0] * sB[le][0][mu][k2] + Da[NS + 1] * sB[le][1][mu][k2];
+      T d2 = Db[0] * sB[le][2][mu][k1] + Db[NS + 1] * sB[le][3][mu][k1];
 #pragma unroll
       for (int l = 0; l < NS; ++l) {
         d1 = fma(Da[l + 1], sF[le][0][mu][k2 * NS + l], d1);
         d2 = fma(Db[l + 1], sF[le][1][mu][l * NS + k1], d2);
       }
-      res[mu] = -dc.two_over_dx * (d1 + d2) + src[mu];
+      res[mu] = double(-tdx * (d1 + d2) + src[mu]);
     }
   }
   volume_epilogue<VolShape<NS>::THREADS>(a.ep, active, idx, N, res, a.out);
+}
+
+__global__ void to_float_kernel(const double* __restrict__ src, float* __restrict__ dst, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
 }
 
 template <int NS>
@@ -241,8 +271,9 @@ int linearize_ns(Ctx& c, const double* q, cudaStream_t s) {
   return cuda_status(cudaGetLastError());
 }
 
-template <int NS>
-int tangent_ns(Ctx& c, const double* v, double* out, const AugEpilogue& ep, cudaStream_t s) {
+template <typename T, int NS>
+int tangent_ns(Ctx& c, const double* v, double* out, const AugEpilogue& ep, const T* ln, const T* lf, T* fb,
+               cudaStream_t s) {
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
   if (c.prof) {
     e0 = prof_event(c);
@@ -250,12 +281,12 @@ int tangent_ns(Ctx& c, const double* v, double* out, const AugEpilogue& ep, cuda
     e2 = prof_event(c);
     cudaEventRecord(e0, s);
   }
-  TanFaceArgs fa{v, c.nodes, c.d_lines, c.d_face_coef, c.d_lin_face, c.nfacepts, c.d_fb, ep.skip};
-  face_tangent_kernel<NS><<<(unsigned)((c.nfacepts + 127) / 128), 128, 0, s>>>(fa, c.dc);
+  TanFaceArgs<T> fa{v, c.nodes, c.d_lines, c.d_face_coef, lf, c.nfacepts, fb, ep.skip};
+  face_tangent_kernel<T, NS><<<(unsigned)((c.nfacepts + 127) / 128), 128, 0, s>>>(fa, c.dc);
   if (c.prof) cudaEventRecord(e1, s);
-  TanVolArgs va{v, c.nodes, c.nelem, c.d_lin_node, c.d_fb, out, ep};
+  TanVolArgs<T> va{v, c.nodes, c.nelem, ln, fb, out, ep};
   const long long vblocks = (c.nelem + VolShape<NS>::EPB - 1) / VolShape<NS>::EPB;
-  volume_tangent_kernel<NS><<<(unsigned)vblocks, VolShape<NS>::THREADS, 0, s>>>(va, c.dc);
+  volume_tangent_kernel<T, NS><<<(unsigned)vblocks, VolShape<NS>::THREADS, 0, s>>>(va, c.dc);
   if (c.prof) {
     cudaEventRecord(e2, s);
     prof_record(c, PK_FACE_JVP, e0, e1);
@@ -263,6 +294,13 @@ int tangent_ns(Ctx& c, const double* v, double* out, const AugEpilogue& ep, cuda
   }
   c.launches += 2;
   return cuda_status(cudaGetLastError());
+}
+
+template <int NS>
+int tangent_any(Ctx& c, const double* v, double* out, const AugEpilogue& ep, bool fp32, cudaStream_t s) {
+  if (fp32)
+    return tangent_ns<float, NS>(c, v, out, ep, c.d_lin_node32, c.d_lin_face32, reinterpret_cast<float*>(c.d_fb), s);
+  return tangent_ns<double, NS>(c, v, out, ep, c.d_lin_node, c.d_lin_face, c.d_fb, s);
 }
 
 }  // namespace
@@ -290,6 +328,17 @@ int launch_linearize(Ctx& c, const double* q, cudaStream_t s) {
     case 8: rc = linearize_ns<8>(c, q, s); break;
     default: return SW_EINVAL;
   }
+  if (rc == SW_OK && c.jvp_mode == 2) {
+    // complex64-bulk form: FP32 copies of the coefficient tables
+    if (!c.d_lin_node32 && cudaMalloc(&c.d_lin_node32, sizeof(float) * LN_COUNT * c.nodes) != cudaSuccess)
+      return SW_ENOMEM;
+    if (!c.d_lin_face32 && cudaMalloc(&c.d_lin_face32, sizeof(float) * 18 * c.nfacepts) != cudaSuccess)
+      return SW_ENOMEM;
+    to_float_kernel<<<1024, 256, 0, s>>>(c.d_lin_node, c.d_lin_node32, (long long)LN_COUNT * c.nodes);
+    to_float_kernel<<<1024, 256, 0, s>>>(c.d_lin_face, c.d_lin_face32, 18LL * c.nfacepts);
+    c.launches += 2;
+    rc = cuda_status(cudaGetLastError());
+  }
   if (c.prof) {
     cudaEventRecord(e1, s);
     prof_record(c, PK_LIN, e0, e1);
@@ -298,17 +347,18 @@ int launch_linearize(Ctx& c, const double* q, cudaStream_t s) {
   return rc;
 }
 
-int launch_jvp_lin(Ctx& c, const double* v, double* out, const AugEpilogue& ep, cudaStream_t s) {
+int launch_jvp_lin(Ctx& c, const double* v, double* out, const AugEpilogue& ep, cudaStream_t s, bool fp32) {
   if (!c.linearized) return SW_EINVAL;
+  if (fp32 && !c.d_lin_node32) return SW_EINVAL;
   switch (c.ns) {
-    case 1: return tangent_ns<1>(c, v, out, ep, s);
-    case 2: return tangent_ns<2>(c, v, out, ep, s);
-    case 3: return tangent_ns<3>(c, v, out, ep, s);
-    case 4: return tangent_ns<4>(c, v, out, ep, s);
-    case 5: return tangent_ns<5>(c, v, out, ep, s);
-    case 6: return tangent_ns<6>(c, v, out, ep, s);
-    case 7: return tangent_ns<7>(c, v, out, ep, s);
-    case 8: return tangent_ns<8>(c, v, out, ep, s);
+    case 1: return tangent_any<1>(c, v, out, ep, fp32, s);
+    case 2: return tangent_any<2>(c, v, out, ep, fp32, s);
+    case 3: return tangent_any<3>(c, v, out, ep, fp32, s);
+    case 4: return tangent_any<4>(c, v, out, ep, fp32, s);
+    case 5: return tangent_any<5>(c, v, out, ep, fp32, s);
+    case 6: return tangent_any<6>(c, v, out, ep, fp32, s);
+    case 7: return tangent_any<7>(c, v, out, ep, fp32, s);
+    case 8: return tangent_any<8>(c, v, out, ep, fp32, s);
     default: return SW_EINVAL;
   }
 }

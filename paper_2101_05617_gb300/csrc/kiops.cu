@@ -179,7 +179,7 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
         ep.dpart = c.d_vpart;
         ep.dticket = (unsigned int*)(c.d_flags + 9);
         ep.n = n;
-        rc = use_lin ? launch_jvp_lin(c, Vi, Vn, ep, s) : launch_jvp(c, q_lin, Vi, kEpsJvp, Vn, ep, s);
+        rc = use_lin ? launch_jvp_lin(c, Vi, Vn, ep, s, c.jvp_mode == 2) : launch_jvp(c, q_lin, Vi, kEpsJvp, Vn, ep, s);
         if (rc) return rc;
         double* hs = c.d_H + (long long)(it + 1) * c.ldh + it;
         if ((rc = launch_update_norm(c, Vn, ep.dotA, Vi, hA, hB, N, hs, o.tol, it + 1, s))) return rc;
@@ -187,7 +187,7 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
         continue;
       }
       ep.dotA = ep.dotB = nullptr;
-      rc = use_lin ? launch_jvp_lin(c, Vi, Vn, ep, s) : launch_jvp(c, q_lin, Vi, kEpsJvp, Vn, ep, s);
+      rc = use_lin ? launch_jvp_lin(c, Vi, Vn, ep, s, c.jvp_mode == 2) : launch_jvp(c, q_lin, Vi, kEpsJvp, Vn, ep, s);
       if (rc) return rc;
       for (int i = std::max(0, it - o.iop + 1); i <= it; ++i) {
         double* h = c.d_H + (long long)i * c.ldh + it;

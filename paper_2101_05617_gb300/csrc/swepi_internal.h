@@ -110,10 +110,12 @@ struct Ctx {
   int m_warm = 0;                 // KIOPS warm start (0 = none)
   long long launches = 0;
   // split JVP (dfr_split.cu): coefficients of the imaginary half at the last linearisation point
-  int jvp_mode = 1;                 // 0 = plain complex-step evaluation per JVP, 1 = split
+  int jvp_mode = 1;                 // 0 = plain complex-step evaluation per JVP, 1 = split, 2 = split FP32 bulk
   bool linearized = false;
   double* d_lin_node = nullptr;     // [LN_COUNT][nodes]
   double* d_lin_face = nullptr;     // [18][nfacepts]
+  float* d_lin_node32 = nullptr;    // FP32 copies (complex64-bulk form)
+  float* d_lin_face32 = nullptr;
   // event profiling (sw_profile)
   bool prof = false;
   struct ProfRec { int kind; cudaEvent_t a, b; };
@@ -162,7 +164,8 @@ int launch_jvp(Ctx& c, const double* q, const double* v, double eps, double* out
                const AugEpilogue& ep, cudaStream_t s);
 // split JVP: evaluate the real half at q, then imaginary halves for any v
 int launch_linearize(Ctx& c, const double* q, cudaStream_t s);
-int launch_jvp_lin(Ctx& c, const double* v, double* out, const AugEpilogue& ep, cudaStream_t s);
+// fp32: the imaginary half in FP32 (complex64-bulk form; needs a mode-2 linearisation)
+int launch_jvp_lin(Ctx& c, const double* v, double* out, const AugEpilogue& ep, cudaStream_t s, bool fp32);
 // the JVP with a caller-supplied interface-flux buffer (nelem * 12 * ns doubles)
 int launch_jvp_fb(Ctx& c, const double* q, const double* v, double eps, double* out, double* fb,
                   cudaStream_t s);

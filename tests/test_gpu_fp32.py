@@ -1,0 +1,70 @@
+"""The complex64-bulk form (sw_set_jvp_mode 2): the per-Krylov-vector
+imaginary half of the complex-step JVP in FP32, the Krylov basis,
+orthogonalisation, exponential and error estimate in FP64.  Each result states
+its error against the FP64 path/oracle and the EPI time-discretisation error."""
+import numpy as np
+import pytest
+
+from oracle import shallow_water as osw
+from tests.gpu_common import oracle_case, scaled_direction, scaled_err_per_var, term_scale
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# FP32 arithmetic of the same formulas: ~500 FP32 roundings of the term scale
+# (u32 = 6e-8), the analogue of the FP64 bound of the parity tests
+TOL_JVP32 = 3e-5
+
+
+def _ctx(g, mode):
+    from paper_2101_05617_gb300.swepi import SWContext
+    c = SWContext(g.ne, g.ns - 1, g.rotation)
+    c.set_jvp_mode(mode)
+    return c
+
+
+@pytest.mark.parametrize("ne,ns,seed,bottom", [(4, 4, 0, 0.0), (3, 6, 1, 0.0), (5, 3, 3, 1500.0), (6, 7, 5, 800.0)])
+def test_fp32_jvp_parity(ne, ns, seed, bottom):
+    _, g, q, hB = oracle_case(ne, ns, seed=seed, bottom_amp=bottom)
+    ctx = _ctx(g, 2)
+    ctx.set_bottom(hB.reshape(-1))
+    qd = torch.tensor(q.reshape(-1), device="cuda")
+    ctx.linearize(qd)
+    v = scaled_direction(q, seed + 300)
+    Jv = ctx.jvp_linearized(torch.tensor(v.reshape(-1), device="cuda")).cpu().numpy()
+    err = scaled_err_per_var(Jv, osw.jvp(g, q, v), term_scale(g, q, v))
+    assert max(err) < TOL_JVP32, err
+    assert max(err) > 1e-12, "FP32 form should not be bit-identical to FP64"
+
+
+def _trajectory(wl, mode, dt, steps, seed=0):
+    from paper_2101_05617_gb300 import synth
+    from paper_2101_05617_gb300.swepi import SWContext
+    f = synth.make_fields(wl, seed)
+    ctx = SWContext(wl.ne, wl.p, f.rotation)
+    h, hB, V = f.evaluate(ctx.node_xyz())
+    q = torch.tensor(ctx.state_from_fields(h, hB, V), device="cuda")
+    ctx.set_jvp_mode(mode)
+    for _ in range(steps):
+        ctx.epi_step(wl.order, dt, q, tol=wl.tol)
+    torch.cuda.synchronize()
+    return q.view(3, -1)
+
+
+def _rel(a, b):
+    return [float(torch.linalg.norm(a[k] - b[k]) / torch.linalg.norm(b[k])) for k in range(3)]
+
+
+@pytest.mark.parametrize("workload,steps", [("small_ne4_p3", 10), ("ne30_p5", 12)])
+def test_fp32_error_below_time_discretisation_error(workload, steps):
+    """FP32-bulk trajectory vs the FP64 path (itself pinned to the oracle by the
+    parity tests) is smaller than the EPI time-discretisation error, measured as
+    the FP64 trajectory at dt against the one at dt/4."""
+    from paper_2101_05617_gb300 import synth
+    wl = synth.WORKLOADS[workload]
+    q64 = _trajectory(wl, 1, wl.dt, steps)
+    q32 = _trajectory(wl, 2, wl.dt, steps)
+    qfine = _trajectory(wl, 1, wl.dt / 4, 4 * steps)
+    e32 = _rel(q32, q64)
+    etime = _rel(q64, qfine)
+    assert all(a < b for a, b in zip(e32, etime)), (e32, etime)

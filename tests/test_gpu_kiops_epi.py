@@ -37,11 +37,13 @@ def test_kiops_parity(ne, ns, nb, dt, tol, mode):
     assert st["krylov_iters"] == rst["krylov_iters"] and st["substeps"] == rst["substeps"], (st, rst)
 
 
-@pytest.mark.parametrize("iop", [3, 4])
+@pytest.mark.parametrize("iop", [3, 5])
 def test_kiops_parity_other_windows(iop):
-    """Orthogonalisation windows other than two take the unfused kernels.  (A
-    window of one is left out: the basis loses orthogonality and the result is
-    rounding-dominated -- the oracle itself is O(1e9) off a dense exponential.)"""
+    """Orthogonalisation windows other than two take the unfused kernels.  Windows
+    1 and 4 are left out: on this operator the incomplete basis loses
+    orthogonality and the result is rounding-dominated (the oracle itself is
+    1e9 resp. 0.16 off the dense exponential, and a 1e-15 perturbation of the
+    operator changes it by O(1) resp. 0.1)."""
     _, g, q, _ = oracle_case(3, 4, seed=5)
     dt, tol = 1800.0, 1e-11
     F = osw.rhs_real(g, q)
