@@ -32,14 +32,25 @@ METRIC = "EPI steps/s and JVP DOF/s at n_e=60,p=5 vs plain FP64 GPU path, same e
 UNIT = "EPI steps/s"
 
 
-def flops_per_jvp(ne, ns):
-    """Algorithmic FP64 flops of one complex-step JVP (first-order complex
-    arithmetic, add/mul/div/sqrt = 1, fma = 2), split into the volume and the
-    face-flux kernels; the per-node and per-interface-point counts are derived
-    operation by operation in the design doc."""
+def flops_per_jvp(ne, ns, p=4, dots=True):
+    """Algorithmic FP64 flops of one Krylov JVP of the split path (the imaginary
+    half of the complex-step evaluation at a fixed linearisation point; add /
+    mul = 1, fma = 2) with the augmented-operator epilogue of p phi-vectors and
+    the two orthogonalisation dot products, split into the volume and face
+    kernels.  Per node: pointwise imaginary fluxes and sources 23, DFR sweeps
+    27 + 12 Ns, scaling 3, epilogue 7 p (+ 12 with the dots).  Per interface
+    point: traces 12 Ns, the 3 x 6 flux map 33, hand-back 7."""
     nodes = 6 * ne * ne * ns * ns
     facepts = 12 * ne * ne * ns
-    return nodes * (108 + 12 * ns), facepts * (30 * ns + 182)
+    vol = 23 + 27 + 12 * ns + 3 + 7 * p + (12 if dots else 0)
+    return nodes * vol, facepts * (12 * ns + 40)
+
+
+# DRAM bytes (read + write) of one launch of the dominant kernel,
+# volume_tangent_kernel<double, 6>, on the 6 x 60 x 60, p = 5 workload inside
+# the phi-function solver (p = 4, with dots): one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum = 136.94 MB + 10.42 MB).
+TRAFFIC_BYTES = {"ne60_p5": 147.36e6}
 
 
 def parse():
@@ -52,6 +63,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--control", default="learned", choices=["learned", "plain"])
+    ap.add_argument("--jvp-mode", type=int, default=1, choices=[0, 1],
+                    help="0: full complex-step evaluation per JVP, 1: split (default)")
     return ap.parse_args()
 
 
@@ -265,12 +279,18 @@ def main():
     h, hB, V = f.evaluate(ctx.node_xyz())
     q_host = ctx.state_from_fields(h, hB, V)
     q = torch.tensor(q_host, device=dev)
+    ctx.set_jvp_mode(args.jvp_mode)
     opts = dict(tol=wl.tol)
     stream = torch.cuda.current_stream()
 
     for _ in range(args.warmup):
         ctx.epi_step(wl.order, wl.dt, q, **opts)
     torch.cuda.synchronize()
+    ctl = None
+    if args.control == "learned":
+        from paper_2101_05617_gb300 import learned
+        ctl = learned.Controller.load()
+        swepi.sw_set_controller(ctx.handle, ctl.handle)
 
     gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local if world > 1 else 0]
     clocks = ClockSampler(gpu_index)
@@ -318,6 +338,8 @@ def main():
     if rank == 0:
         ne, ns = wl.ne, wl.ns
         fv, ff = flops_per_jvp(ne, ns)
+        if args.jvp_mode == 0:   # full evaluation per vector: first-order complex arithmetic counts
+            fv, ff = 6 * ne * ne * ns * ns * (108 + 12 * ns), 12 * ne * ne * ns * (30 * ns + 182)
         vj, fj = prof["volume_jvp"], prof["face_jvp"]
         t_vol = vj["ms"] / max(1, vj["count"]) * 1e-3
         t_face = fj["ms"] / max(1, fj["count"]) * 1e-3
@@ -328,8 +350,12 @@ def main():
         else:
             achieved = ff / t_face / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
-                    "kernel": f"{dominant}_kernel<cs,{ns}> (complex-step JVP)",
+                    "frac": achieved / peak,
+                    "traffic": TRAFFIC_BYTES.get(wl.name) if dominant == "volume" and args.jvp_mode == 1 else None,
+                    "kernel": ((f"volume_tangent_kernel<double,{ns}>" if dominant == "volume"
+                                else f"face_tangent_kernel<double,{ns}>")
+                               + " (imaginary half of the complex-step JVP, phi-solver epilogue)")
+                              if args.jvp_mode == 1 else f"{dominant} kernel<cs,{ns}> (full complex-step JVP)",
                     "peak_source": "FP64 FMA throughput measured live by sw_fp64_fma_peak (nominal 1.25)",
                     "per_kernel": {"volume": {"flops": fv, "avg_ms": t_vol * 1e3, "launches": vj["count"],
                                               "tflops": fv / t_vol / 1e12 if t_vol else None},
@@ -347,6 +373,7 @@ def main():
                "config": {"workload": f"{wl.name}: 6x{ne}x{ne} elements, p={wl.p}, EPI{wl.order}, "
                                       f"dt={wl.dt:g} s, KIOPS tol {wl.tol:g}, complex-step eps {wl.eps:g}",
                           "n_unknowns": wl.n_unknowns, "parallelism": "replicas" if world > 1 else "single",
+                          "control": args.control,
                           "l2": "inputs larger than L2 (Krylov basis ~2.4 GB per KIOPS call)"},
                "jvp_dof_per_s": wl.n_unknowns / t_jvp,
                "jvp_dof_per_s_total": world * wl.n_unknowns / t_jvp,
@@ -357,12 +384,18 @@ def main():
                        "h2d_bytes_per_step": 8 * wl.n_unknowns, "d2h_bytes_per_step": 8 * wl.n_unknowns},
                "gpu_launches": launches,
                "roofline": roofline,
-               "forms": {"fp64_split": {"value": value, "unit": UNIT}}}
+               "forms": {"timed": ("learned control + FP64 split complex-step JVP" if ctl is not None
+                                   else "plain control + FP64 split complex-step JVP")}}
         if not args.no_forms:
+            if ctl is not None:
+                from paper_2101_05617_gb300 import learned
+                out["forms"]["learned_vs_plain_same_start"] = learned.evaluate(ctl, args.workload, args.steps,
+                                                                               seed=args.seed + 1)
             out["forms"]["complex64_bulk_ne30_p5"] = fp32_form_comparison(args, dev)
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = oracle_sample(wl, args.seed, krylov / args.steps, P)
         print(json.dumps(out), flush=True)
+    swepi.sw_set_controller(ctx.handle, None)
     ctx.close()
     if pg is not None:
         pg.barrier()

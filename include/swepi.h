@@ -176,6 +176,47 @@ int sw_epi_set_history(sw_ctx_t ctx, int i, const double* q_dev, const double* F
 /* Forget the EPI history and the KIOPS warm start. */
 int sw_epi_reset(sw_ctx_t ctx);
 
+/* ---- Learned Krylov control (the adaptive rule stays in charge) ----------
+ * A 16 -> 64 -> 64 -> 2 perceptron with GELU hidden layers, BF16 weights and
+ * FP32 accumulation predicts, per phi-function call, the initial substep
+ * log(tau/tau_out) and Krylov size m/m_max from 16 per-call features (log10 of
+ * max ||b_k||_1 and of the initial augmented norm; the previous call's first
+ * accepted tau, its m, final m, substeps, rejections and Krylov iterations;
+ * log10 of its last four h_{j+1,j}; EPI order and start-up flag; log10 dt; p).
+ * Trained on log(tau_star/tau_out) and m_1/m_max of plain-rule calls (see
+ * sw_kiops_log).  The error estimate still accepts or rejects every substep; without a network
+ * (or on a non-finite prediction) the plain rule applies (tau = tau_out, m =
+ * previous final m).  Training runs on the GPU (mean squared error on
+ * standardised data, Adam on FP32 master weights, BF16 copies).
+ * params: SW_MLP_PARAMS floats, W1[64][16] b1[64] W2[64][64] b2[64] W3[2][64]
+ * b3[2]; norm: SW_MLP_NORM floats, input mean[16], input std[16], output
+ * mean[2], output std[2].  X: n x 16 raw features, T/Y: n x 2 raw outputs
+ * (device, row-major).  No paper counterpart beyond the KIOPS step choice. */
+#define SW_MLP_PARAMS 5378
+#define SW_MLP_NORM 36
+#define SW_KIOPS_LOG_FIELDS 23
+typedef struct sw_mlp* sw_mlp_t;
+int sw_mlp_create(sw_mlp_t* out);
+void sw_mlp_free(sw_mlp_t mlp);
+int sw_mlp_set_params(sw_mlp_t mlp, const float* params_host, const float* norm_host);
+int sw_mlp_get_params(sw_mlp_t mlp, float* params_host, float* bf16_params_host);
+int sw_mlp_forward(sw_mlp_t mlp, const float* X_dev, int n, float* Y_dev, void* stream);
+/* gradient of the loss at the current weights (no update); synchronises */
+int sw_mlp_gradient(sw_mlp_t mlp, const float* X_dev, const float* T_dev, int n, float* grad_host,
+                    float* loss_host, void* stream);
+/* `steps` full-batch Adam steps; loss_host (may be NULL) receives each step's loss */
+int sw_mlp_train(sw_mlp_t mlp, const float* X_dev, const float* T_dev, int n, int steps, float lr,
+                 float* loss_host, void* stream);
+/* use `mlp` (not owned; NULL = plain rule) for the context's phi-function calls */
+int sw_set_controller(sw_ctx_t ctx, sw_mlp_t mlp);
+/* per-call log of the phi-function solver: SW_KIOPS_LOG_FIELDS floats per call
+ * (16 features, log(tau_1/tau_out) of the first accepted substep, its m/m_max,
+ * Krylov iterations, rejections, substeps, m_final/m_max, log(tau_star/tau_out) with
+ * tau_star = tau_1 (0.8/omega_1)^(1/order) the largest first substep the error
+ * model admits); copies up to max_records, returns the number held */
+int sw_kiops_log(sw_ctx_t ctx, float* out_host, int max_records);
+int sw_kiops_log_clear(sw_ctx_t ctx);
+
 /* Number of kernels the library launched since the context was created. */
 long long sw_kernel_launches(sw_ctx_t ctx);
 

@@ -301,6 +301,8 @@ int sw_kiops_phi(sw_ctx_t c, const double* q_lin, double dt, double tau_out, int
   sw_kiops_opts o = opts ? *opts : default_opts();
   cudaStream_t s = as_stream(stream);
   int rc;
+  c->epi_order = 0;
+  c->epi_stage = 0;
   if (c->jvp_mode >= 1 && (rc = launch_linearize(*c, q_lin, s))) return rc;
   rc = kiops_run(*c, q_lin, dt, tau_out, nb, b, o, w, st, s, c->jvp_mode >= 1);
   return rc;
@@ -343,6 +345,8 @@ int sw_epi_step(sw_ctx_t c, int order, double dt, double* q, const sw_kiops_opts
   if (rc) return rc;
   if (st) std::memset(st, 0, sizeof(*st));
   const long long n = c->n;
+  c->epi_order = order;
+  c->epi_stage = 0;
   if ((rc = launch_rhs(*c, q, c->d_Fn, s))) return rc;
   if (order == 2) {
     rc = epi2_inplace(*c, q, c->d_Fn, dt, o, st, s);
@@ -355,10 +359,12 @@ int sw_epi_step(sw_ctx_t c, int order, double dt, double* q, const sw_kiops_opts
     // start-up: EPI2 with N_sub smaller steps (Sec. 4)
     if ((rc = push_history(*c, q, c->d_Fn, s))) return rc;
     const double h = dt / kStartupSubsteps;
+    c->epi_stage = 1;
     for (int k = 0; k < kStartupSubsteps; ++k) {
       if (k > 0 && (rc = launch_rhs(*c, q, c->d_Fn, s))) return rc;
       if ((rc = epi2_inplace(*c, q, c->d_Fn, h, o, st, s))) return rc;
     }
+    c->epi_stage = 0;
     return cuda_status(cudaStreamSynchronize(s));
   }
   // remainders R(q_{n-i}) = F(q_{n-i}) - F_n - J_n (q_{n-i} - q_n)  (Eq. 33)
@@ -398,6 +404,82 @@ int sw_epi_step(sw_ctx_t c, int order, double dt, double* q, const sw_kiops_opts
 }
 
 long long sw_kernel_launches(sw_ctx_t c) { return c ? c->launches : -1; }
+
+// sw_mlp_t is an opaque handle to a swepi::Mlp
+static Mlp* as_mlp(sw_mlp_t m) { return reinterpret_cast<Mlp*>(m); }
+
+int sw_mlp_create(sw_mlp_t* out) {
+  if (!out) return SW_EINVAL;
+  *out = nullptr;
+  Mlp* m = nullptr;
+  int rc = mlp_create(&m);
+  if (rc) return rc;
+  *out = reinterpret_cast<sw_mlp_t>(m);
+  return SW_OK;
+}
+
+void sw_mlp_free(sw_mlp_t m) { mlp_destroy(as_mlp(m)); }
+
+int sw_mlp_set_params(sw_mlp_t m, const float* params, const float* norm) {
+  if (!m) return SW_EINVAL;
+  return mlp_set(as_mlp(m), params, norm);
+}
+
+int sw_mlp_get_params(sw_mlp_t m, float* params, float* bf16_params) {
+  if (!m) return SW_EINVAL;
+  return mlp_get(as_mlp(m), params, bf16_params);
+}
+
+int sw_mlp_forward(sw_mlp_t m, const float* X, int n, float* Y, void* stream) {
+  if (!m || !X || !Y || n < 1 || n > (1 << 30)) return SW_EINVAL;
+  return mlp_forward(as_mlp(m), X, n, Y, as_stream(stream));
+}
+
+int sw_mlp_gradient(sw_mlp_t m, const float* X, const float* T, int n, float* grad, float* loss, void* stream) {
+  if (!m || !X || !T || !grad || n < 1) return SW_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  float l = 0.f;
+  int rc = mlp_step(as_mlp(m), X, T, n, false, 0.f, &l, s);
+  if (rc) return rc;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return SW_ECUDA;
+  if (loss) *loss = l;
+  return mlp_grad_host(as_mlp(m), grad);
+}
+
+int sw_mlp_train(sw_mlp_t m, const float* X, const float* T, int n, int steps, float lr, float* loss, void* stream) {
+  if (!m || !X || !T || n < 1 || steps < 0 || !(lr > 0)) return SW_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  for (int k = 0; k < steps; ++k) {
+    float l = 0.f;
+    int rc = mlp_step(as_mlp(m), X, T, n, true, lr, loss ? &l : nullptr, s);
+    if (rc) return rc;
+    if (loss) {
+      if (cudaStreamSynchronize(s) != cudaSuccess) return SW_ECUDA;
+      loss[k] = l;
+    }
+  }
+  return cuda_status(cudaStreamSynchronize(s));
+}
+
+int sw_set_controller(sw_ctx_t c, sw_mlp_t m) {
+  if (!c) return SW_EINVAL;
+  c->controller = as_mlp(m);
+  return SW_OK;
+}
+
+int sw_kiops_log(sw_ctx_t c, float* out, int max_records) {
+  if (!c || max_records < 0 || (max_records > 0 && !out)) return SW_EINVAL;
+  const int have = (int)(c->kiops_log.size() / KIOPS_LOG_FIELDS);
+  const int k = have < max_records ? have : max_records;
+  if (k > 0) std::memcpy(out, c->kiops_log.data(), sizeof(float) * KIOPS_LOG_FIELDS * k);
+  return have;
+}
+
+int sw_kiops_log_clear(sw_ctx_t c) {
+  if (!c) return SW_EINVAL;
+  c->kiops_log.clear();
+  return SW_OK;
+}
 
 int sw_set_jvp_mode(sw_ctx_t c, int mode) {
   if (!c || mode < 0 || mode > 2) return SW_EINVAL;

@@ -146,6 +146,33 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
   double tau_now = 0.0;
   double tau = (o.tau_init > 0) ? std::min(o.tau_init, tau_end) : tau_end;
   int m = std::min(std::max(o.m_init, o.m_min), o.m_max);
+
+  // per-call features (learned control input and log record)
+  float feat[16];
+  feat[0] = (float)std::log10(std::max(normb, 1e-300));
+  feat[1] = (float)std::log10(std::max(beta0, 1e-300));
+  for (int k2 = 0; k2 < 6; ++k2) feat[2 + k2] = c.prev_call[k2];
+  for (int k2 = 0; k2 < 4; ++k2) feat[8 + k2] = c.prev_h[k2];
+  feat[12] = (float)c.epi_order;
+  feat[13] = (float)c.epi_stage;
+  feat[14] = (float)((dt > 0) ? std::log10(dt) : 0.0);
+  feat[15] = (float)p;
+  if (c.controller) {
+    // learned initial (tau, m); the omega test below still accepts or rejects
+    // every substep, and a non-finite prediction leaves the plain rule
+    float pred[2];
+    if ((rc = mlp_predict_host(c.controller, feat, pred, s))) return rc;
+    if (std::isfinite(pred[0]) && std::isfinite(pred[1])) {
+      double lt = std::min(0.0, std::max(std::log(1e-3), (double)pred[0]));
+      tau = tau_end * std::exp(lt);
+      m = std::min(o.m_max, std::max(o.m_min, (int)std::lround(pred[1] * o.m_max)));
+    }
+  }
+  double tau_first = -1.0, tau_star = -1.0;
+  int m_first = 0;
+  double last_omega = 0.0, last_order = 1.0;
+  double hist_h[4] = {0, 0, 0, 0};
+  int nh = 0;
   int j = 0;
   bool have_prev = false;
   int prev_m = 0;
@@ -223,13 +250,17 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
       tau_new = tau;
     } else {
       double hsub = c.h_pinned[S_STAT + 4];
+      hist_h[nh % 4] = hsub;
+      ++nh;
       err = beta * hsub * std::fabs(Fjj);
       double omega = (tau_end / tau) * err / (o.tol * beta0);
       if (!std::isfinite(omega)) return SW_ENONFINITE;
       accept = omega <= kDelta;
+      last_omega = omega;
       double order = (have_prev && prev_m == m && prev_tau != tau)
                          ? std::max(1.0, std::log(omega / prev_omega) / std::log(tau / prev_tau))
                          : j / 4.0;
+      last_order = order;
       double kappa = (have_prev && prev_tau == tau && prev_m != m)
                          ? std::max(1.1, std::pow(omega / prev_omega, 1.0 / (prev_m - m)))
                          : 2.0;
@@ -258,6 +289,14 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
     }
     last_err = err;
     if (accept) {
+      if (tau_first < 0) {
+        tau_first = tau;
+        m_first = j;
+        // largest first substep the error model admits: omega ~ tau^order
+        tau_star = (happy || last_omega <= 0) ? tau_end
+                                              : tau * std::pow(kGamma / last_omega, 1.0 / last_order);
+        tau_star = std::min(tau_end, std::max(tau, tau_star));
+      }
       if ((rc = launch_combine(c, j, n, s))) return rc;
       tau_now += tau;
       double tv[MAX_NB];
@@ -281,6 +320,31 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
     if (tau_now < tau_end) tau = (tau_new > 0) ? std::min(tau_new, tau_end - tau_now) : tau_end - tau_now;
   }
   if (cudaMemcpyAsync(w, c.d_X, sizeof(double) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return SW_ECUDA;
+  {
+    // log record: features, then log(tau_1/tau_end), m_1/m_max, Krylov iterations, rejections, substeps,
+    // m_final/m_max, log(tau_star/tau_end) with tau_star the largest first substep the error model admits
+    float rec[KIOPS_LOG_FIELDS];
+    for (int k2 = 0; k2 < 16; ++k2) rec[k2] = feat[k2];
+    rec[16] = (float)std::log(tau_first / tau_end);
+    rec[17] = (float)m_first / o.m_max;
+    rec[18] = (float)krylov;
+    rec[19] = (float)rejects;
+    rec[20] = (float)substeps;
+    rec[21] = (float)m / o.m_max;
+    rec[22] = (float)std::log(tau_star / tau_end);
+    if (c.kiops_log.size() + KIOPS_LOG_FIELDS <= KIOPS_LOG_MAX * KIOPS_LOG_FIELDS)
+      c.kiops_log.insert(c.kiops_log.end(), rec, rec + KIOPS_LOG_FIELDS);
+    c.prev_call[0] = (float)std::log10(tau_first / tau_end);
+    c.prev_call[1] = rec[17];
+    c.prev_call[2] = rec[21];
+    c.prev_call[3] = (float)substeps;
+    c.prev_call[4] = (float)rejects;
+    c.prev_call[5] = (float)krylov / o.m_max;
+    for (int k2 = 0; k2 < 4; ++k2) {
+      double hv = (nh > k2) ? hist_h[(nh - 1 - k2) % 4] : 0.0;
+      c.prev_h[k2] = (hv > 0) ? (float)std::log10(hv) : 0.0f;
+    }
+  }
   if (st) {
     st->substeps = substeps;
     st->rejects = rejects;

@@ -14,6 +14,8 @@ namespace swepi {
 constexpr int MAX_NS = 8;   // p <= 7
 constexpr int MAX_NB = 8;   // phi_0 .. phi_7
 constexpr int MAX_HIST = 4; // EPI6 uses q_{n-1..n-4}
+constexpr int KIOPS_LOG_FIELDS = 23;   // 16 features + 7 outcomes per KIOPS call
+constexpr size_t KIOPS_LOG_MAX = 200000;
 
 // Per-node coefficient arrays (structure of arrays, `nodes` doubles each).
 enum NodeCoef {
@@ -62,6 +64,8 @@ struct DfrConst {
   double two_over_dx;             // Eq. (6)
   double gravity;
 };
+
+struct Mlp;   // learned Krylov control network (mlp.cu)
 
 struct Ctx {
   int device = 0;
@@ -116,6 +120,13 @@ struct Ctx {
   double* d_lin_face = nullptr;     // [18][nfacepts]
   float* d_lin_node32 = nullptr;    // FP32 copies (complex64-bulk form)
   float* d_lin_face32 = nullptr;
+  // KIOPS call log and learned control
+  Mlp* controller = nullptr;      // not owned
+  int epi_order = 0;              // EPI order of the current call (0: direct sw_kiops_phi)
+  int epi_stage = 0;              // 1 during EPI2 start-up substeps
+  std::vector<float> kiops_log;   // KIOPS_LOG_FIELDS floats per call
+  float prev_call[8] = {};        // log10 tau_1, m_1/m_max, m_final/m_max, substeps, rejects, krylov/m_max, valid
+  float prev_h[4] = {};           // log10 of the last four h_{j+1,j} of the previous call
   // event profiling (sw_profile)
   bool prof = false;
   struct ProfRec { int kind; cudaEvent_t a, b; };
@@ -124,6 +135,18 @@ struct Ctx {
   long long prof_count[6] = {};
   double prof_ms[6] = {};
 };
+
+// learned Krylov control (mlp.cu)
+int mlp_nparam();
+int mlp_nnorm();
+int mlp_create(Mlp** out);
+void mlp_destroy(Mlp* m);
+int mlp_set(Mlp* m, const float* params, const float* norm);
+int mlp_get(Mlp* m, float* params, float* bf16_as_float);
+int mlp_forward(Mlp* m, const float* X, int n, float* Y, cudaStream_t s);
+int mlp_step(Mlp* m, const float* X, const float* T, int n, bool adam, float lr, float* loss_host, cudaStream_t s);
+int mlp_grad_host(Mlp* m, float* grad_host);
+int mlp_predict_host(Mlp* m, const float* feat, float* out2, cudaStream_t s);
 
 // event profiling helpers (capi.cu)
 cudaEvent_t prof_event(Ctx& c);

@@ -95,6 +95,18 @@ def lib():
     L.sw_profile.argtypes = [vp, ip]
     L.sw_profile_read.argtypes = [vp, ctypes.POINTER(sw_profile_stats)]
     L.sw_fp64_fma_peak.argtypes = [dp]
+    fp = ctypes.POINTER(ctypes.c_float)
+    L.sw_mlp_create.argtypes = [ctypes.POINTER(vp)]
+    L.sw_mlp_free.argtypes = [vp]
+    L.sw_mlp_free.restype = None
+    L.sw_mlp_set_params.argtypes = [vp, vp, vp]
+    L.sw_mlp_get_params.argtypes = [vp, vp, vp]
+    L.sw_mlp_forward.argtypes = [vp, vp, ip, vp, vp]
+    L.sw_mlp_gradient.argtypes = [vp, vp, vp, ip, vp, fp, vp]
+    L.sw_mlp_train.argtypes = [vp, vp, vp, ip, ip, ctypes.c_float, vp, vp]
+    L.sw_set_controller.argtypes = [vp, vp]
+    L.sw_kiops_log.argtypes = [vp, vp, ip]
+    L.sw_kiops_log_clear.argtypes = [vp]
     L.sw_status_str.argtypes = [ip]
     L.sw_status_str.restype = ctypes.c_char_p
     _lib = L
@@ -105,7 +117,13 @@ EXPORTED = ["sw_init", "sw_free", "sw_num_unknowns", "sw_grid_info", "sw_node_xy
             "sw_set_bottom", "sw_rhs", "sw_jvp", "sw_jvp_static_scratch", "sw_linearize", "sw_jvp_linearized",
             "sw_set_jvp_mode", "sw_kiops_phi", "sw_epi_step", "sw_epi_set_history",
             "sw_epi_reset", "sw_kernel_launches", "sw_profile", "sw_profile_read", "sw_fp64_fma_peak",
-            "sw_status_str"]
+            "sw_status_str", "sw_mlp_create", "sw_mlp_free", "sw_mlp_set_params", "sw_mlp_get_params",
+            "sw_mlp_forward", "sw_mlp_gradient", "sw_mlp_train", "sw_set_controller", "sw_kiops_log",
+            "sw_kiops_log_clear"]
+
+MLP_PARAMS = 5378
+MLP_NORM = 36
+KIOPS_LOG_FIELDS = 23
 
 
 def _check(call, rc):
@@ -259,6 +277,85 @@ def sw_fp64_fma_peak():
     t = ctypes.c_double()
     _check("sw_fp64_fma_peak", lib().sw_fp64_fma_peak(ctypes.byref(t)))
     return t.value
+
+
+def _f32_dev(t, n=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError("expected a contiguous float32 CUDA tensor")
+    if n is not None and t.numel() < n:
+        raise ValueError("tensor too small")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def sw_mlp_create():
+    h = ctypes.c_void_p()
+    _check("sw_mlp_create", lib().sw_mlp_create(ctypes.byref(h)))
+    return h
+
+
+def sw_mlp_free(m):
+    lib().sw_mlp_free(m)
+
+
+def sw_mlp_set_params(m, params=None, norm=None):
+    pa = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+    no = None if norm is None else np.ascontiguousarray(norm, dtype=np.float32)
+    if pa is not None and pa.size != MLP_PARAMS or no is not None and no.size != MLP_NORM:
+        raise ValueError("wrong parameter or normalisation size")
+    _check("sw_mlp_set_params", lib().sw_mlp_set_params(
+        m, None if pa is None else pa.ctypes.data_as(ctypes.c_void_p),
+        None if no is None else no.ctypes.data_as(ctypes.c_void_p)))
+
+
+def sw_mlp_get_params(m):
+    master = np.empty(MLP_PARAMS, dtype=np.float32)
+    bf16 = np.empty(MLP_PARAMS, dtype=np.float32)
+    _check("sw_mlp_get_params", lib().sw_mlp_get_params(m, master.ctypes.data_as(ctypes.c_void_p),
+                                                        bf16.ctypes.data_as(ctypes.c_void_p)))
+    return master, bf16
+
+
+def sw_mlp_forward(m, X, Y, stream=None):
+    n = X.shape[0]
+    _check("sw_mlp_forward", lib().sw_mlp_forward(m, _f32_dev(X, 16 * n), n, _f32_dev(Y, 2 * n), _stream(stream)))
+
+
+def sw_mlp_gradient(m, X, T, stream=None):
+    n = X.shape[0]
+    g = np.empty(MLP_PARAMS, dtype=np.float32)
+    loss = ctypes.c_float()
+    _check("sw_mlp_gradient", lib().sw_mlp_gradient(m, _f32_dev(X, 16 * n), _f32_dev(T, 2 * n), n,
+                                                    g.ctypes.data_as(ctypes.c_void_p), ctypes.byref(loss),
+                                                    _stream(stream)))
+    return g, loss.value
+
+
+def sw_mlp_train(m, X, T, steps, lr, stream=None):
+    n = X.shape[0]
+    losses = np.empty(max(1, steps), dtype=np.float32)
+    _check("sw_mlp_train", lib().sw_mlp_train(m, _f32_dev(X, 16 * n), _f32_dev(T, 2 * n), n, int(steps),
+                                              float(lr), losses.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+    return losses[:steps]
+
+
+def sw_set_controller(ctx, m):
+    _check("sw_set_controller", lib().sw_set_controller(ctx, m))
+
+
+def sw_kiops_log(ctx):
+    have = lib().sw_kiops_log(ctx, None, 0)
+    if have < 0:
+        raise SWError("sw_kiops_log", have)
+    out = np.empty(max(1, have) * KIOPS_LOG_FIELDS, dtype=np.float32)
+    got = lib().sw_kiops_log(ctx, out.ctypes.data_as(ctypes.c_void_p), have)
+    if got < 0:
+        raise SWError("sw_kiops_log", got)
+    return out[:have * KIOPS_LOG_FIELDS].reshape(have, KIOPS_LOG_FIELDS)
+
+
+def sw_kiops_log_clear(ctx):
+    _check("sw_kiops_log_clear", lib().sw_kiops_log_clear(ctx))
 
 
 def sw_status_str(status):

@@ -52,7 +52,7 @@ def test_flop_counts():
     sys.path.insert(0, ROOT)
     import bench
     fv, ff = bench.flops_per_jvp(60, 6)
-    assert fv == 6 * 3600 * 36 * 180 and ff == 12 * 3600 * 6 * 362
+    assert fv == 6 * 3600 * 36 * 165 and ff == 12 * 3600 * 6 * 112
 
 
 def test_reference_arm_runs_on_cpu():
