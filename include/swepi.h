@@ -132,6 +132,19 @@ int sw_jvp(sw_ctx_t ctx, const double* q_dev, const double* v_dev, double eps,
 int sw_jvp_static_scratch(sw_ctx_t ctx, const double* q_dev, const double* v_dev, double eps,
                           double* Jv_dev, void* stream);
 
+/* Diagnostics of Sec. 5 (synchronises): out[0..3] = the Gauss-Legendre
+ * integrals (Eq. 42, without the common element Jacobian) of mass H, total
+ * energy (H g_ij u^i u^j + g_r((H + h_B)^2 - h_B^2))/2 and potential enstrophy
+ * (zeta + f)^2/(2H) -- the invariants whose normalised drift Eq. (44) monitors
+ * -- and max |zeta|, with zeta the relative vorticity of Eq. (43) (element-local
+ * collocation derivative of u_j = g_jk u^k) and f of Eq. (46).  zeta_dev (n/3
+ * doubles, may be NULL) receives zeta at the nodes. */
+int sw_diagnostics(sw_ctx_t ctx, const double* q_dev, double* out_host, double* zeta_dev, void* stream);
+
+/* Error norms of Eq. (39)-(41) of H = q^0/sqrt(g) against the H of q_ref:
+ * out[0] = L1, out[1] = L2, out[2] = Linf (synchronises). */
+int sw_error_norms(sw_ctx_t ctx, const double* q_dev, const double* q_ref_dev, double* out_host, void* stream);
+
 /* Split evaluation of the complex-step product (Eq. 28) for many v at one q:
  * sw_linearize evaluates the real half of F(q + i eps v) -- every quantity that
  * depends on q alone -- and stores the coefficients of the imaginary half

@@ -233,7 +233,8 @@ void sw_free(sw_ctx_t c) {
   if (!c) return;
   double* ptrs[] = {c->d_node_coef, c->d_face_coef, c->d_fb, c->d_V, c->d_X, c->d_H, c->d_F, c->d_expm_ws,
                     c->d_partials, c->d_scal, c->d_Fn, c->d_tmp, c->d_tmp2, c->d_lin_node, c->d_lin_face,
-                    c->d_vpart, c->d_cdot};
+                    c->d_vpart, c->d_cdot, c->d_diag_tab, c->d_diag_part, c->d_diag_out};
+  if (c->d_diag_flags) cudaFree(c->d_diag_flags);
   if (c->d_lin_node32) cudaFree(c->d_lin_node32);
   if (c->d_lin_face32) cudaFree(c->d_lin_face32);
   for (double* p : ptrs)
@@ -271,13 +272,36 @@ int sw_node_xyz(sw_ctx_t c, double* xyz) {
 
 int sw_set_bottom(sw_ctx_t c, const double* hB) {
   if (!c || !hB) return SW_EINVAL;
-  return bottom_coefficients(*c, hB);
+  int rc = bottom_coefficients(*c, hB);
+  return rc ? rc : refresh_diag_bottom(*c, hB);
+}
+
+int sw_diagnostics(sw_ctx_t c, const double* q, double* out, double* zeta, void* stream) {
+  if (!c || !q || !out) return SW_EINVAL;
+  double r[6];
+  int rc = launch_diagnostics(*c, q, nullptr, zeta, r, as_stream(stream));
+  if (rc) return rc;
+  for (int k = 0; k < 4; ++k) out[k] = r[k];
+  return SW_OK;
+}
+
+int sw_error_norms(sw_ctx_t c, const double* q, const double* q_ref, double* out, void* stream) {
+  if (!c || !q || !q_ref || !out) return SW_EINVAL;
+  double r[6];
+  int rc = launch_diagnostics(*c, q, q_ref, nullptr, r, as_stream(stream));
+  if (rc) return rc;
+  if (!(r[2] != 0) || !(r[3] > 0) || !(r[5] > 0)) return SW_ENONFINITE;
+  out[0] = r[0] / r[2];
+  out[1] = std::sqrt(r[1] / r[3]);
+  out[2] = r[4] / r[5];
+  return SW_OK;
 }
 
 int sw_state_from_fields(sw_ctx_t c, const double* h, const double* hB, const double* V, double* q) {
   if (!c || !h || !hB || !V || !q) return SW_EINVAL;
   int rc = bottom_coefficients(*c, hB);
   if (rc) return rc;
+  if ((rc = refresh_diag_bottom(*c, hB))) return rc;
   return fields_to_state(*c, h, hB, V, q);
 }
 

@@ -215,6 +215,8 @@ int build_tables(Ctx& c) {
     for (int k = 0; k < ns; ++k) { c.dc.lm[k] = lm[k]; c.dc.lp[k] = lp[k]; }
   }
   c.Dg = (ns == 1) ? std::vector<double>(1, 0.0) : bary_diff(c.xi);
+  for (int k = 0; k < ns; ++k)
+    for (int l = 0; l < ns; ++l) c.dc.Dg[k][l] = c.Dg[k * ns + l];
   c.dc.two_over_dx = 2.0 / c.dx;
   c.dc.gravity = c.prm.gravity;
 
@@ -360,6 +362,7 @@ void node_unit_xyz(const Ctx& c, double* xyz) {
 
 int bottom_coefficients(Ctx& c, const double* hB) {
   const int ne = c.ne, ns = c.ns;
+  c.hB_h.assign(hB, hB + c.nodes);
   const double a = c.prm.radius, gr = c.prm.gravity;
   for (long long el = 0; el < c.nelem; ++el) {
     int e1 = (int)(el % ne), e2 = (int)((el / ne) % ne);
@@ -383,6 +386,33 @@ int bottom_coefficients(Ctx& c, const double* hB) {
   cudaError_t e = cudaMemcpy(c.d_node_coef + (size_t)NC_B1 * c.nodes, c.node_coef_h.data() + (size_t)NC_B1 * c.nodes,
                              sizeof(double) * 2 * c.nodes, cudaMemcpyHostToDevice);
   return cuda_status(e);
+}
+
+// per-node tables of the diagnostics: sqrt g, w_m w_n, g_11, g_12, g_22, the
+// Coriolis parameter f = 2 Omega s / delta (Eq. 46) and h_B
+void diag_tables_host(const Ctx& c, double* tab) {
+  const int ne = c.ne, ns = c.ns;
+  const double a = c.prm.radius, om = c.prm.omega;
+  const long long N = c.nodes;
+  for (int p = 0; p < 6; ++p) {
+    const double cz = c.frame[p][0][2], e1z = c.frame[p][1][2], e2z = c.frame[p][2][2];
+    for (int e2 = 0; e2 < ne; ++e2)
+      for (int e1 = 0; e1 < ne; ++e1)
+        for (int k2 = 0; k2 < ns; ++k2)
+          for (int k1 = 0; k1 < ns; ++k1) {
+            long long i = elem_index(c, p, e2, e1) * ns * ns + k2 * ns + k1;
+            double X = std::tan(line_coord(c, e1, k1)), Y = std::tan(line_coord(c, e2, k2));
+            double d2 = 1 + X * X + Y * Y;
+            Metric m = metric_at(X, Y, a);
+            tab[0 * N + i] = m.sqrtg;
+            tab[1 * N + i] = c.wq[k1] * c.wq[k2];
+            tab[2 * N + i] = a * a / (d2 * d2) * (1 + X * X) * (1 + X * X) * (1 + Y * Y);   // Eq. (64)
+            tab[3 * N + i] = -a * a / (d2 * d2) * X * Y * (1 + X * X) * (1 + Y * Y);        // Eq. (65)
+            tab[4 * N + i] = a * a / (d2 * d2) * (1 + X * X) * (1 + Y * Y) * (1 + Y * Y);   // Eq. (66)
+            tab[5 * N + i] = 2.0 * om * (cz + X * e1z + Y * e2z) / std::sqrt(d2);
+            tab[6 * N + i] = c.hB_h.empty() ? 0.0 : c.hB_h[i];
+          }
+  }
 }
 
 int fields_to_state(const Ctx& c, const double* h, const double* hB, const double* V, double* q) {

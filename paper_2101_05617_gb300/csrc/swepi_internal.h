@@ -60,6 +60,7 @@ struct FaceLine {
 // Small DFR constants passed by value to the kernels.
 struct DfrConst {
   double D[MAX_NS][MAX_NS + 2];   // l~'_n(xi_k), Eq. (12)-(13)
+  double Dg[MAX_NS][MAX_NS];      // l'_l(xi_k) on the solution points (collocation derivative)
   double lm[MAX_NS], lp[MAX_NS];  // l_k(-1), l_k(+1), Eq. (8)
   double two_over_dx;             // Eq. (6)
   double gravity;
@@ -127,6 +128,12 @@ struct Ctx {
   std::vector<float> kiops_log;   // KIOPS_LOG_FIELDS floats per call
   float prev_call[8] = {};        // log10 tau_1, m_1/m_max, m_final/m_max, substeps, rejects, krylov/m_max, valid
   float prev_h[4] = {};           // log10 of the last four h_{j+1,j} of the previous call
+  // diagnostics (diag.cu)
+  double* d_diag_tab = nullptr;    // sqrt g, w_m w_n, g_ij, f, h_B per node
+  double* d_diag_part = nullptr;
+  double* d_diag_out = nullptr;
+  void* d_diag_flags = nullptr;
+  std::vector<double> hB_h;        // nodal bottom (host copy)
   // event profiling (sw_profile)
   bool prof = false;
   struct ProfRec { int kind; cudaEvent_t a, b; };
@@ -159,6 +166,12 @@ int build_tables(Ctx& c);
 void node_unit_xyz(const Ctx& c, double* xyz);
 int bottom_coefficients(Ctx& c, const double* hB);
 int fields_to_state(const Ctx& c, const double* h, const double* hB, const double* V, double* q);
+void diag_tables_host(const Ctx& c, double* tab);
+
+// ---- diagnostics (diag.cu)
+int ensure_diag(Ctx& c);
+int refresh_diag_bottom(Ctx& c, const double* hB);
+int launch_diagnostics(Ctx& c, const double* q, const double* qref, double* zeta, double* out_host, cudaStream_t s);
 
 // ---- DFR kernels (dfr.cu)
 struct AugEpilogue {

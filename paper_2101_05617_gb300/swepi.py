@@ -105,6 +105,8 @@ def lib():
     L.sw_mlp_gradient.argtypes = [vp, vp, vp, ip, vp, fp, vp]
     L.sw_mlp_train.argtypes = [vp, vp, vp, ip, ip, ctypes.c_float, vp, vp]
     L.sw_set_controller.argtypes = [vp, vp]
+    L.sw_diagnostics.argtypes = [vp, vp, vp, vp, vp]
+    L.sw_error_norms.argtypes = [vp, vp, vp, vp, vp]
     L.sw_kiops_log.argtypes = [vp, vp, ip]
     L.sw_kiops_log_clear.argtypes = [vp]
     L.sw_status_str.argtypes = [ip]
@@ -119,7 +121,7 @@ EXPORTED = ["sw_init", "sw_free", "sw_num_unknowns", "sw_grid_info", "sw_node_xy
             "sw_epi_reset", "sw_kernel_launches", "sw_profile", "sw_profile_read", "sw_fp64_fma_peak",
             "sw_status_str", "sw_mlp_create", "sw_mlp_free", "sw_mlp_set_params", "sw_mlp_get_params",
             "sw_mlp_forward", "sw_mlp_gradient", "sw_mlp_train", "sw_set_controller", "sw_kiops_log",
-            "sw_kiops_log_clear"]
+            "sw_kiops_log_clear", "sw_diagnostics", "sw_error_norms"]
 
 MLP_PARAMS = 5378
 MLP_NORM = 36
@@ -356,6 +358,24 @@ def sw_kiops_log(ctx):
 
 def sw_kiops_log_clear(ctx):
     _check("sw_kiops_log_clear", lib().sw_kiops_log_clear(ctx))
+
+
+def sw_diagnostics(ctx, q, zeta=None, stream=None):
+    """(mass, energy, potential enstrophy, max |zeta|) of Sec. 5."""
+    n = sw_num_unknowns(ctx)
+    out = np.empty(4, dtype=np.float64)
+    z = None if zeta is None else _dev_ptr(zeta, n // 3)
+    _check("sw_diagnostics", lib().sw_diagnostics(ctx, _dev_ptr(q, n), out.ctypes.data_as(ctypes.c_void_p), z,
+                                                  _stream(stream)))
+    return out
+
+
+def sw_error_norms(ctx, q, q_ref, stream=None):
+    n = sw_num_unknowns(ctx)
+    out = np.empty(3, dtype=np.float64)
+    _check("sw_error_norms", lib().sw_error_norms(ctx, _dev_ptr(q, n), _dev_ptr(q_ref, n),
+                                                  out.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+    return out
 
 
 def sw_status_str(status):
