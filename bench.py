@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--control", default="learned", choices=["learned", "plain"])
     ap.add_argument("--jvp-mode", type=int, default=1, choices=[0, 1],
                     help="0: full complex-step evaluation per JVP, 1: split (default)")
@@ -226,6 +227,72 @@ def fp32_form_comparison(args, dev):
 # Krylov iterations per EPI5 step of the GPU path on the default workload
 # (measured; used only to project the oracle's step time in --impl reference).
 KRYLOV_PER_STEP_NE60_P5 = 416.0
+
+
+def ensemble_form(args, dev, fp64_peak):
+    """The batched ensemble: 96 members on uneven grids (n_e in {8, 16, 24, 32},
+    p in {3, 4, 5}, EPI4/5, dt = 900 s, degree <= 12 perturbations of 50 m)
+    for 24 steps through sw_ens_epi_run after autotuning; against one member
+    per (n_e, p) class run alone through sw_epi_step (rate and state difference)."""
+    import torch
+    from paper_2101_05617_gb300 import ensemble, swepi, synth
+    members = synth.ensemble_members(96, seed=args.seed)
+    steps = 24
+    t0 = time.perf_counter()
+    ctxs, qs = ensemble.build(members)
+    build_s = time.perf_counter() - t0
+    ens = swepi.SWEnsemble(ctxs)
+    block = ens.tune(qs, iters=4)
+    tiles = {}
+    for i, m in enumerate(members):
+        tiles[f"ne{m.ne}_p{m.p}"] = ens.tiles(i)
+    orders = [m.order for m in members]
+    dts = [m.dt for m in members]
+    ys = [q.clone() for q in qs]
+    ens.epi_run(1, orders, dts, ys, tol=1e-10)                 # warm-up: first-touch allocations
+    ensemble.reset(ctxs)
+    ys = [q.clone() for q in qs]
+    ens.profile(True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    st = ens.epi_run(steps, orders, dts, ys, tol=1e-10)
+    e1.record()
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) * 1e-3
+    info = ens.stats()
+    ens.close()
+    krylov = [a["krylov_iters"] for a in st]
+    # one member per class alone, same start, same steps
+    pick = {}
+    for i, m in enumerate(members):
+        pick.setdefault((m.ne, m.p), i)
+    idx = sorted(pick.values())
+    refs, _, single_s = ensemble.run_single([members[i] for i in idx], [ctxs[i] for i in idx], [qs[i] for i in idx],
+                                            steps, tol=1e-10)
+    diff = 0.0
+    for i, r in zip(idx, refs):
+        a, b = ys[i].view(3, -1), r.view(3, -1)
+        diff = max(diff, max(float(torch.linalg.norm(a[k] - b[k]) / torch.linalg.norm(b[k])) for k in range(3)))
+    fl = 0.0
+    for m, k in zip(members, krylov):
+        fv, ff = flops_per_jvp(m.ne, m.ns, p=m.order - 1)
+        fl += k * (fv + ff)
+    achieved = fl / (info["iter_ms"] * 1e-3) / 1e12 if info["iter_ms"] > 0 else None
+    return {"members": len(members), "steps": steps, "seconds": sec,
+            "members_per_s": len(members) / sec, "member_steps_per_s": len(members) * steps / sec,
+            "jvp_dof_per_s": sum(k * 3 * m.nodes for m, k in zip(members, krylov)) / sec,
+            "unknowns_total": sum(3 * m.nodes for m in members),
+            "krylov_iters": {"total": sum(krylov), "max_member": max(krylov)},
+            "batched_iterations": info["ticks"], "read_backs": info["reads"], "expm_batches": info["expm_batches"],
+            "gpu_launches": info["launches"], "block": info["block"], "ctas": info["ctas"],
+            "tiles_by_class": tiles,
+            "iteration_kernel": {"ms": info["iter_ms"], "share_of_run": info["iter_ms"] * 1e-3 / sec,
+                                 "fp64_tflops": achieved, "peak_tflops": fp64_peak,
+                                 "frac": (achieved / fp64_peak) if achieved and fp64_peak else None},
+            "single_member_path": {"members": len(idx), "seconds": single_s,
+                                   "member_steps_per_s": len(idx) * steps / single_s},
+            "max_rel_l2_vs_single": diff, "build_s": build_s}
 
 
 def run_reference(args, world, rank):
@@ -392,6 +459,8 @@ def main():
                 out["forms"]["learned_vs_plain_same_start"] = learned.evaluate(ctl, args.workload, args.steps,
                                                                                seed=args.seed + 1)
             out["forms"]["complex64_bulk_ne30_p5"] = fp32_form_comparison(args, dev)
+            if world == 1 and not args.no_ensemble:
+                out["forms"]["ensemble_96"] = ensemble_form(args, dev, peak)
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = oracle_sample(wl, args.seed, krylov / args.steps, P)
         print(json.dumps(out), flush=True)

@@ -230,6 +230,61 @@ int sw_set_controller(sw_ctx_t ctx, sw_mlp_t mlp);
 int sw_kiops_log(sw_ctx_t ctx, float* out_host, int max_records);
 int sw_kiops_log_clear(sw_ctx_t ctx);
 
+/* ---- Batched ensemble -------------------------------------------------------
+ * Many independent members (each an sw_ctx_t of its own grid: n_e, p in 3..5,
+ * rotation, bottom) advanced together by sw_epi_step's method.  Per member the
+ * sequence of operations, the adaptive rule and the statistics are those of
+ * sw_epi_step (FP64 split JVP, iop 2, plain rule); results agree with
+ * per-member sw_epi_step runs up to the order of floating-point sums.  Each
+ * Krylov iteration of all members that are building a basis is one launch of
+ * a persistent kernel captured once in a CUDA graph; the small exponentials of
+ * all members that finished a basis are batched, and one read-back serves all
+ * members waiting for a decision (Sec. 4's KIOPS per member).  The members'
+ * contexts stay owned by the caller and must outlive the ensemble; the
+ * ensemble uses their workspace and EPI history (sw_epi_reset still applies).
+ * Every call synchronises `stream` before returning.
+ *
+ * Tiles (per member) and threads per CTA (per ensemble) shape the batched
+ * kernel: interface points per face task, element tiles per volume task (a
+ * tile = threads per CTA / (p+1)^2 elements, one thread per solution point)
+ * and vector entries per orthogonalisation task.  sw_ens_tune searches them
+ * per (n_e, p) class and threads per CTA in {128, 256, 512} by timing `iters`
+ * batched iterations at the members' states q_dev (it overwrites the members'
+ * Krylov workspace, not q).  sw_ens_set_policy: while the members that iterate
+ * hold at least theta (0..1, default 0.5) of the unfinished members' nodes, the
+ * driver keeps iterating and defers the members that wait for a decision.
+ * q_dev_host / stats: host arrays of `members` entries (device state vectors;
+ * per-member statistics accumulated over the run, may be NULL). */
+typedef struct sw_ens* sw_ens_t;
+typedef struct {
+  int face_pts;   /* interface points per face task */
+  int vol_tiles;  /* element tiles per volume task */
+  int vec_len;    /* vector entries per update / scale task */
+} sw_ens_tiles;
+typedef struct {
+  long long ticks;         /* batched Krylov iterations (graph replays) in the last run */
+  long long reads;         /* host read-backs in the last run */
+  long long expm_batches;  /* batched exponentials in the last run */
+  long long launches;      /* kernel launches of the last run (graph replays count one) */
+  double iter_ms;          /* device time of the batched iterations (while sw_ens_profile is on) */
+  int block;               /* threads per CTA of the batched iteration kernel */
+  int ctas;                /* its persistent grid */
+} sw_ens_stats;
+int sw_ens_create(int members, const sw_ctx_t* ctxs_host, sw_ens_t* out);
+int sw_ens_free(sw_ens_t ens);
+int sw_ens_set_block(sw_ens_t ens, int block);
+int sw_ens_set_tiles(sw_ens_t ens, int member, const sw_ens_tiles* tiles);
+int sw_ens_get_tiles(sw_ens_t ens, int member, sw_ens_tiles* tiles);
+int sw_ens_set_policy(sw_ens_t ens, double theta);
+int sw_ens_tune(sw_ens_t ens, double* const* q_dev_host, int iters, int* block, void* stream);
+/* `steps` EPI steps of every member: orders (2..6) and dts per member. */
+int sw_ens_epi_run(sw_ens_t ens, int steps, const int* orders_host, const double* dts_host,
+                   double* const* q_dev_host, const sw_kiops_opts* opts, sw_kiops_stats* stats_host,
+                   void* stream);
+int sw_ens_stats_read(sw_ens_t ens, sw_ens_stats* out);
+/* bracket every batched iteration with CUDA events on the run's stream */
+int sw_ens_profile(sw_ens_t ens, int enable);
+
 /* Number of kernels the library launched since the context was created. */
 long long sw_kernel_launches(sw_ctx_t ctx);
 

@@ -12,18 +12,15 @@
 
 using namespace swepi;
 
-struct sw_ctx : public Ctx {};
-
 namespace {
-
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+}  // namespace
+
+namespace swepi {
 
 // EPI coefficient matrices: rows phi_1..phi_M, columns q_{n-1}..q_{n-P}
 // (Eq. 30 for order 3, Eq. 36-38 for orders 4-6).
-struct Coefs {
-  int M, P;
-  double a[4][4];
-};
+namespace {
 const Coefs kEpi3 = {2, 1, {{0.0}, {2.0 / 3.0}}};
 const Coefs kEpi4 = {3, 2, {{0.0, 0.0}, {-3.0 / 10.0, 3.0 / 40.0}, {32.0 / 5.0, -11.0 / 10.0}}};
 const Coefs kEpi5 = {4, 3,
@@ -34,6 +31,8 @@ const Coefs kEpi6 = {4, 4,
                       {-49.0 / 60.0, 351.0 / 560.0, -359.0 / 1260.0, 367.0 / 6720.0},
                       {92.0 / 7.0, -99.0 / 14.0, 176.0 / 63.0, -1.0 / 2.0},
                       {485.0 / 21.0, -151.0 / 14.0, 23.0 / 9.0, -31.0 / 168.0}}};
+}  // namespace
+
 const Coefs* coefs_for(int order) {
   switch (order) {
     case 3: return &kEpi3;
@@ -43,9 +42,6 @@ const Coefs* coefs_for(int order) {
     default: return nullptr;
   }
 }
-constexpr int kStartupSubsteps = 8;
-constexpr double kEpsJvp = 1e-30;
-
 sw_kiops_opts default_opts() {
   sw_kiops_opts o;
   o.tol = 1e-10;
@@ -57,7 +53,7 @@ sw_kiops_opts default_opts() {
   return o;
 }
 
-int alloc_vec(double*& p, long long n) {
+static int alloc_vec(double*& p, long long n) {
   if (p) return SW_OK;
   return cudaMalloc(&p, sizeof(double) * n) == cudaSuccess ? SW_OK : SW_ENOMEM;
 }
@@ -95,6 +91,11 @@ void add_stats(sw_kiops_stats* acc, const sw_kiops_stats& s) {
   acc->tau_final = s.tau_final;
   acc->err_last = s.err_last;
 }
+
+}  // namespace swepi
+
+namespace {
+constexpr double kEpsJvp = 1e-30;
 
 // KIOPS call of the EPI driver; in split mode the caller has linearised at q
 int phi_call(Ctx& c, const double* q, double dt, int nb, const double* const* b, const sw_kiops_opts& o0, double* w,
@@ -382,9 +383,9 @@ int sw_epi_step(sw_ctx_t c, int order, double dt, double* q, const sw_kiops_opts
   if (c->hist_count < P) {
     // start-up: EPI2 with N_sub smaller steps (Sec. 4)
     if ((rc = push_history(*c, q, c->d_Fn, s))) return rc;
-    const double h = dt / kStartupSubsteps;
+    const double h = dt / EPI_STARTUP_SUBSTEPS;
     c->epi_stage = 1;
-    for (int k = 0; k < kStartupSubsteps; ++k) {
+    for (int k = 0; k < EPI_STARTUP_SUBSTEPS; ++k) {
       if (k > 0 && (rc = launch_rhs(*c, q, c->d_Fn, s))) return rc;
       if ((rc = epi2_inplace(*c, q, c->d_Fn, h, o, st, s))) return rc;
     }

@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(VolShape<NS>::THREADS) volume_kernel(VolArgs a
 #pragma unroll
     for (int mu = 0; mu < 3; ++mu) res[mu] *= sc;
   }
-  volume_epilogue<VolShape<NS>::THREADS>(a.ep, active, idx, a.nodes, res, a.out);
+  volume_epilogue<VolShape<NS>::THREADS>(a.ep, active, idx, a.nodes, res, a.out, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------- launchers

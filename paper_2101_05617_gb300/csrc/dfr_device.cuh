@@ -134,13 +134,15 @@ struct VolShape {
 };
 
 
-// Epilogue of the volume kernels (all threads of the block call it):
+// Epilogue of the volume kernels (all threads of the block call it; blk/nblk:
+// this block's index and the number of blocks working on the same vector):
 // out = scale * res + nu * sum_l y_l b_{p-l} (the augmented operator of the
 // phi-function solver), the shift of the augmented tail, and -- when dotB is
 // set -- the window dot products of the incomplete orthogonalisation.
 template <int THREADS>
 __device__ __forceinline__ void volume_epilogue(const AugEpilogue& ep, bool active, long long idx, long long N,
-                                                const double res[3], double* __restrict__ out) {
+                                                const double res[3], double* __restrict__ out, unsigned int blk,
+                                                unsigned int nblk) {
   double da = 0.0, db = 0.0;
   if (active) {
     double coef[MAX_NB];
@@ -159,10 +161,10 @@ __device__ __forceinline__ void volume_epilogue(const AugEpilogue& ep, bool acti
       }
     }
   }
-  if (ep.tail_out && blockIdx.x == 0 && threadIdx.x < ep.p)
+  if (ep.tail_out && blk == 0 && threadIdx.x < ep.p)
     ep.tail_out[threadIdx.x] = (threadIdx.x + 1 < ep.p) ? ep.tail_in[threadIdx.x + 1] : 0.0;
   if (!ep.dotB) return;   // uniform over the grid
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (blk == 0 && threadIdx.x == 0) {
     for (int l = 0; l < ep.p; ++l) {
       const double zt = (l + 1 < ep.p) ? ep.tail_in[l + 1] : 0.0;
       db = fma(zt, ep.dotB[ep.n + l], db);
@@ -183,18 +185,18 @@ __device__ __forceinline__ void volume_epilogue(const AugEpilogue& ep, bool acti
       b += __shfl_down_sync(0xffffffffu, b, o);
     }
     if (threadIdx.x == 0) {
-      ep.dpart[2 * blockIdx.x] = a;
-      ep.dpart[2 * blockIdx.x + 1] = b;
+      ep.dpart[2 * blk] = a;
+      ep.dpart[2 * blk + 1] = b;
       __threadfence();
       const unsigned int t = atomicAdd(ep.dticket, 1u);
-      last = (t == gridDim.x - 1);
+      last = (t == nblk - 1);
     }
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
   double a = 0.0, b = 0.0;
-  for (int k = threadIdx.x; k < (int)gridDim.x; k += THREADS) {
+  for (int k = threadIdx.x; k < (int)nblk; k += THREADS) {
     a += __ldcg(ep.dpart + 2 * k);
     b += __ldcg(ep.dpart + 2 * k + 1);
   }

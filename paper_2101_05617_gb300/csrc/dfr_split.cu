@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include "dfr_device.cuh"
+#include "dfr_tangent.cuh"
 #include "swepi_internal.h"
 
 namespace swepi {
@@ -108,152 +109,18 @@ __global__ void __launch_bounds__(128) lin_face_kernel(LinFaceArgs a, DfrConst d
   }
 }
 
-// ---------------------------------------------------------------- tangent
-// The imaginary half in arithmetic type T: double (the FP64 path) or float
-// (the complex64-bulk form: tables rounded from the FP64 linearisation, FP32
-// accumulation).  Krylov vectors in and out stay FP64; the epilogue (augmented
-// operator and orthogonalisation dots) is FP64 in both.
-template <typename T, int NS>
-__device__ __forceinline__ void trace_tan(const double* __restrict__ v, long long nodes, int elem, int edge, int i,
-                                          const DfrConst& dc, T out[3]) {
-  const long long base = (long long)elem * NS * NS;
-  const double* w = (edge == 0 || edge == 2) ? dc.lm : dc.lp;
-#pragma unroll
-  for (int var = 0; var < 3; ++var) {
-    T acc = T(0);
-#pragma unroll
-    for (int k = 0; k < NS; ++k) {
-      const long long idx = base + ((edge <= 1) ? (i * NS + k) : (k * NS + i)) + var * nodes;
-      acc = fma(T(w[k]), T(__ldg(v + idx)), acc);
-    }
-    out[var] = acc;
-  }
-}
-
-template <typename T>
-struct TanFaceArgs {
-  const double* v;
-  long long nodes;
-  const FaceLine* lines;
-  const double* fc;
-  const T* lf;
-  long long nfacepts;
-  T* fb;
-  const int* skip;
-};
-
+// single-grid kernels around the shared bodies (dfr_tangent.cuh)
 template <typename T, int NS>
 __global__ void __launch_bounds__(128) face_tangent_kernel(TanFaceArgs<T> a, DfrConst dc) {
   if (a.skip && *a.skip) return;
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= a.nfacepts) return;
-  const int line = (int)(t / NS), i = (int)(t % NS);
-  const FaceLine L = a.lines[line];
-  const int in = L.reversed ? NS - 1 - i : i;
-  T vo[3], vn[3];
-  trace_tan<T, NS>(a.v, a.nodes, L.owner, L.owner_edge, i, dc, vo);
-  trace_tan<T, NS>(a.v, a.nodes, L.nbr, L.nbr_edge, in, dc, vn);
-  const long long P = a.nfacepts;
-  const T* lf = a.lf + t;
-  T f[3];
-#pragma unroll
-  for (int mu = 0; mu < 3; ++mu) {
-    T s = lf[(mu * 3) * P] * vo[0];
-    s = fma(lf[(mu * 3 + 1) * P], vo[1], s);
-    s = fma(lf[(mu * 3 + 2) * P], vo[2], s);
-    s = fma(lf[(9 + mu * 3) * P], vn[0], s);
-    s = fma(lf[(9 + mu * 3 + 1) * P], vn[1], s);
-    s = fma(lf[(9 + mu * 3 + 2) * P], vn[2], s);
-    f[mu] = s;
-  }
-  const double* fc = a.fc + t;
-  const T sig = T(fc[FC_SIG * P]);
-  const T M00 = T(fc[FC_M00 * P]), M01 = T(fc[FC_M01 * P]), M10 = T(fc[FC_M10 * P]), M11 = T(fc[FC_M11 * P]);
-  T* fo = a.fb + ((long long)L.owner * 4 + L.owner_edge) * 3 * NS + i;
-  fo[0] = f[0];
-  fo[NS] = f[1];
-  fo[2 * NS] = f[2];
-  T* fn = a.fb + ((long long)L.nbr * 4 + L.nbr_edge) * 3 * NS + in;
-  fn[0] = sig * f[0];
-  fn[NS] = M00 * f[1] + M01 * f[2];
-  fn[2 * NS] = M10 * f[1] + M11 * f[2];
+  face_tangent_body<T, NS>(a, dc, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
-
-template <typename T>
-struct TanVolArgs {
-  const double* v;
-  long long nodes;
-  long long nelem;
-  const T* ln;
-  const T* fb;
-  double* out;
-  AugEpilogue ep;
-};
 
 template <typename T, int NS>
 __global__ void __launch_bounds__(VolShape<NS>::THREADS) volume_tangent_kernel(TanVolArgs<T> a, DfrConst dc) {
-  constexpr int EPB = VolShape<NS>::EPB;
-  constexpr int NN = NS * NS;
   if (a.ep.skip && *a.ep.skip) return;
-  __shared__ T sF[EPB][2][3][NN];
-  __shared__ T sB[EPB][4][3][NS];
-  __shared__ T sD[NS][NS + 3];          // padded rows: distinct banks per k
-  for (int t = threadIdx.x; t < NS * (NS + 2); t += blockDim.x)
-    sD[t / (NS + 2)][t % (NS + 2)] = T(dc.D[t / (NS + 2)][t % (NS + 2)]);
-  const int le = threadIdx.x / NN, node = threadIdx.x % NN;
-  const long long elem = (long long)blockIdx.x * EPB + le;
-  const bool active = elem < a.nelem;
-  const int k2 = node / NS, k1 = node % NS;
-  const long long idx = elem * NN + node;
-  for (int t = threadIdx.x; t < EPB * 12 * NS; t += blockDim.x) {
-    int e = t / (12 * NS), r = t % (12 * NS);
-    long long ge = (long long)blockIdx.x * EPB + e;
-    (&sB[e][0][0][0])[r] = (ge < a.nelem) ? a.fb[ge * 12 * NS + r] : T(0);
-  }
-  T S1 = T(0), S2 = T(0);
-  const long long N = a.nodes;
-  if (active) {
-    const T v0 = T(__ldg(a.v + idx)), v1 = T(__ldg(a.v + idx + N)), v2 = T(__ldg(a.v + idx + 2 * N));
-    const T* ln = a.ln + idx;
-    const T u1 = ln[LN_U1 * N], u2 = ln[LN_U2 * N];
-    const T F11 = fma(T(2) * u1, v1, ln[LN_A11 * N] * v0);
-    const T F12 = fma(u2, v1, fma(u1, v2, ln[LN_A12 * N] * v0));
-    const T F22 = fma(T(2) * u2, v2, ln[LN_A22 * N] * v0);
-    S1 = fma(ln[LN_S11 * N], v1, fma(ln[LN_S12 * N], v2, ln[LN_S10 * N] * v0));
-    S2 = fma(ln[LN_S21 * N], v1, fma(ln[LN_S22 * N], v2, ln[LN_S20 * N] * v0));
-    sF[le][0][0][node] = v1;
-    sF[le][0][1][node] = F11;
-    sF[le][0][2][node] = F12;
-    sF[le][1][0][node] = v2;
-    sF[le][1][1][node] = F12;
-    sF[le][1][2][node] = F22;
-  }
-  __syncthreads();
-  const T src[3] = {T(0), S1, S2};
-  double res[3] = {0.0, 0.0, 0.0};
-  if (active) {
-    // this thread's rows of the derivative matrix, from shared memory into registers
-    // (a per-thread row index into the constant bank would serialise the warp)
-    T Da[NS + 2], Db[NS + 2];
-#pragma unroll
-    for (int n = 0; n < NS + 2; ++n) {
-      Da[n] = sD[k1][n];
-      Db[n] = sD[k2][n];
-    }
-    const T tdx = T(dc.two_over_dx);
-#pragma unroll
-    for (int mu = 0; mu < 3; ++mu) {
-      T d1 = Da[0] * sB[le][0][mu][k2] + Da[NS + 1] * sB[le][1][mu][k2];
-      T d2 = Db[0] * sB[le][2][mu][k1] + Db[NS + 1] * sB[le][3][mu][k1];
-#pragma unroll
-      for (int l = 0; l < NS; ++l) {
-        d1 = fma(Da[l + 1], sF[le][0][mu][k2 * NS + l], d1);
-        d2 = fma(Db[l + 1], sF[le][1][mu][l * NS + k1], d2);
-      }
-      res[mu] = double(-tdx * (d1 + d2) + src[mu]);
-    }
-  }
-  volume_epilogue<VolShape<NS>::THREADS>(a.ep, active, idx, N, res, a.out);
+  __shared__ VolSmem<T, NS, VolShape<NS>::EPB> sm;
+  volume_tangent_body<T, NS, VolShape<NS>::EPB>(a, dc, blockIdx.x, gridDim.x, sm);
 }
 
 __global__ void to_float_kernel(const double* __restrict__ src, float* __restrict__ dst, long long n) {

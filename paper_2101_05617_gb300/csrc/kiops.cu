@@ -28,19 +28,13 @@
 #include <cmath>
 #include <cstring>
 
+#include "kiops_ctl.h"
 #include "swepi_internal.h"
 
 namespace swepi {
 
 namespace {
-constexpr double kDelta = 1.2;
-constexpr double kGamma = 0.8;
-constexpr int kMaxSubsteps = 100000;
-constexpr int kMaxRejects = 100000;
 constexpr double kEpsJvp = 1e-30;
-
-// device scalar slots (d_scal)
-constexpr int S_BETA = 0, S_BETA0 = 1, S_STAT = 8, S_NORMB = 16;
 
 int read_back(Ctx& c, cudaStream_t s) {
   cudaError_t e = cudaMemcpyAsync(c.h_pinned, c.d_scal, sizeof(double) * 32, cudaMemcpyDeviceToHost, s);
@@ -143,20 +137,12 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
   ep.skip = c.d_flags;
 
   const double tau_end = tau_out;
-  double tau_now = 0.0;
   double tau = (o.tau_init > 0) ? std::min(o.tau_init, tau_end) : tau_end;
   int m = std::min(std::max(o.m_init, o.m_min), o.m_max);
 
   // per-call features (learned control input and log record)
   float feat[16];
-  feat[0] = (float)std::log10(std::max(normb, 1e-300));
-  feat[1] = (float)std::log10(std::max(beta0, 1e-300));
-  for (int k2 = 0; k2 < 6; ++k2) feat[2 + k2] = c.prev_call[k2];
-  for (int k2 = 0; k2 < 4; ++k2) feat[8 + k2] = c.prev_h[k2];
-  feat[12] = (float)c.epi_order;
-  feat[13] = (float)c.epi_stage;
-  feat[14] = (float)((dt > 0) ? std::log10(dt) : 0.0);
-  feat[15] = (float)p;
+  kiops_features(c, normb, beta0, dt, p, feat);
   if (c.controller) {
     // learned initial (tau, m); the omega test below still accepts or rejects
     // every substep, and a non-finite prediction leaves the plain rule
@@ -168,28 +154,20 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
       m = std::min(o.m_max, std::max(o.m_min, (int)std::lround(pred[1] * o.m_max)));
     }
   }
-  double tau_first = -1.0, tau_star = -1.0;
-  int m_first = 0;
-  double last_omega = 0.0, last_order = 1.0;
-  double hist_h[4] = {0, 0, 0, 0};
-  int nh = 0;
-  int j = 0;
-  bool have_prev = false;
-  int prev_m = 0;
-  double prev_tau = 0.0, prev_omega = 0.0;
-  int krylov = 0, substeps = 0, rejects = 0;
-  double last_err = 0.0;
+  KiopsController K;
+  K.start(tau_end, o.tol, beta0, o, tau, m);
   double* V = c.d_V;
   const long long ldv = c.ldv;
 
-  while (tau_now < tau_end) {
+  while (!K.done()) {
+    const int j = K.j, m_cur = K.m;
     if (j == 0) {
       if ((rc = launch_norm2(c, c.d_X, N, c.d_scal + S_BETA, 0.0, nullptr, 0, nullptr, s))) return rc;
       if ((rc = launch_scale_inv(c, V, c.d_X, c.d_scal + S_BETA, N, nullptr, s))) return rc;
       if (cudaMemsetAsync(c.d_flags, 0, sizeof(int) * 2, s) != cudaSuccess) return SW_ECUDA;
       if (cudaMemsetAsync(c.d_H, 0, sizeof(double) * c.ldh * c.ldh, s) != cudaSuccess) return SW_ECUDA;
     }
-    for (int it = j; it < m; ++it) {
+    for (int it = j; it < m_cur; ++it) {
       double* Vi = V + it * ldv;
       double* Vn = V + (it + 1) * ldv;
       ep.tail_in = Vi + n;
@@ -225,7 +203,7 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
       if ((rc = launch_norm2(c, Vn, N, hs, o.tol, c.d_flags, it + 1, c.d_flags, s))) return rc;
       if ((rc = launch_scale_inv(c, Vn, Vn, hs, N, c.d_flags, s))) return rc;
     }
-    if ((rc = launch_expm_prep(c, m, tau, tau_end - tau_now, s))) return rc;
+    if ((rc = launch_expm_prep(c, m_cur, K.tau, tau_end - K.tau_now, s))) return rc;
     if ((rc = read_back(c, s))) return rc;
     {
       const int Ne = (int)c.h_pinned[S_STAT + 1] + 1;
@@ -234,125 +212,21 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
     if ((rc = read_back(c, s))) return rc;
     const int* fl = pinned_flags(c);
     const bool happy = fl[0] != 0;
-    const int jnew = happy ? fl[1] : m;
-    krylov += jnew - j;
-    j = jnew;
-    const double beta = c.h_pinned[S_BETA];
-    const double Fjj = c.h_pinned[S_STAT + 0];
-    bool accept;
-    int m_new;
-    double tau_new;
-    double err = 0.0;
-    if (happy) {
-      tau = tau_end - tau_now;
-      accept = true;
-      m_new = m;
-      tau_new = tau;
-    } else {
-      double hsub = c.h_pinned[S_STAT + 4];
-      hist_h[nh % 4] = hsub;
-      ++nh;
-      err = beta * hsub * std::fabs(Fjj);
-      double omega = (tau_end / tau) * err / (o.tol * beta0);
-      if (!std::isfinite(omega)) return SW_ENONFINITE;
-      accept = omega <= kDelta;
-      last_omega = omega;
-      double order = (have_prev && prev_m == m && prev_tau != tau)
-                         ? std::max(1.0, std::log(omega / prev_omega) / std::log(tau / prev_tau))
-                         : j / 4.0;
-      last_order = order;
-      double kappa = (have_prev && prev_tau == tau && prev_m != m)
-                         ? std::max(1.1, std::pow(omega / prev_omega, 1.0 / (prev_m - m)))
-                         : 2.0;
-      double remaining = accept ? tau_end - (tau_now + tau) : tau_end - tau_now;
-      double tau_same = std::min(remaining, tau);
-      double tau_opt = (omega > 0) ? tau * std::pow(kGamma / omega, 1.0 / order) : 5 * tau;
-      tau_opt = std::min(remaining, std::max(tau / 5, std::min(5 * tau, tau_opt)));
-      int m_opt = (omega > 0) ? (int)std::ceil(j + std::log(omega / kGamma) / std::log(kappa)) : o.m_min;
-      m_opt = std::max(o.m_min, std::min(o.m_max, std::max((int)std::floor(3.0 * m / 4.0),
-                                                           std::min(m_opt, (int)std::ceil(4.0 * m / 3.0)))));
-      if (j == o.m_max) {
-        m_new = m;
-        tau_new = tau_opt;
-      } else {
-        double cost_tau = tau_opt > 0 ? m * std::ceil(remaining / tau_opt) : 0.0;
-        double cost_m = tau_same > 0 ? m_opt * std::ceil(remaining / tau_same) : 0.0;
-        if (cost_tau <= cost_m) { m_new = m; tau_new = tau_opt; }
-        else { m_new = m_opt; tau_new = tau_same; }
-      }
-      if (!accept) {
-        have_prev = true;
-        prev_m = m;
-        prev_tau = tau;
-        prev_omega = omega;
-      }
+    if ((rc = K.decide(happy, happy ? fl[1] : m_cur, c.h_pinned[S_BETA], c.h_pinned[S_STAT + 4],
+                       c.h_pinned[S_STAT + 0])))
+      return rc;
+    if (K.accept) {
+      if ((rc = launch_combine(c, K.j_used, n, s))) return rc;
     }
-    last_err = err;
-    if (accept) {
-      if (tau_first < 0) {
-        tau_first = tau;
-        m_first = j;
-        // largest first substep the error model admits: omega ~ tau^order
-        tau_star = (happy || last_omega <= 0) ? tau_end
-                                              : tau * std::pow(kGamma / last_omega, 1.0 / last_order);
-        tau_star = std::min(tau_end, std::max(tau, tau_star));
-      }
-      if ((rc = launch_combine(c, j, n, s))) return rc;
-      tau_now += tau;
+    if ((rc = K.finish(kMaxSubsteps, kMaxRejects))) return rc;
+    if (K.accept) {
       double tv[MAX_NB];
-      for (int l = 0; l < p; ++l) {
-        int k = p - 1 - l;
-        double f = 1.0;
-        for (int t = 2; t <= k; ++t) f *= t;
-        tv[l] = mu * std::pow(tau_now, k) / f;
-      }
+      K.tail(p, mu, tv);
       if ((rc = launch_set_tail(c, c.d_X, n, p, tv, s))) return rc;
-      ++substeps;
-      j = 0;
-      have_prev = false;
-      if (substeps > kMaxSubsteps) return SW_EKRYLOV;
-    } else {
-      ++rejects;
-      if (rejects > kMaxRejects) return SW_EKRYLOV;
-      if (m_new < j) j = m_new;
     }
-    m = m_new;
-    if (tau_now < tau_end) tau = (tau_new > 0) ? std::min(tau_new, tau_end - tau_now) : tau_end - tau_now;
   }
   if (cudaMemcpyAsync(w, c.d_X, sizeof(double) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return SW_ECUDA;
-  {
-    // log record: features, then log(tau_1/tau_end), m_1/m_max, Krylov iterations, rejections, substeps,
-    // m_final/m_max, log(tau_star/tau_end) with tau_star the largest first substep the error model admits
-    float rec[KIOPS_LOG_FIELDS];
-    for (int k2 = 0; k2 < 16; ++k2) rec[k2] = feat[k2];
-    rec[16] = (float)std::log(tau_first / tau_end);
-    rec[17] = (float)m_first / o.m_max;
-    rec[18] = (float)krylov;
-    rec[19] = (float)rejects;
-    rec[20] = (float)substeps;
-    rec[21] = (float)m / o.m_max;
-    rec[22] = (float)std::log(tau_star / tau_end);
-    if (c.kiops_log.size() + KIOPS_LOG_FIELDS <= KIOPS_LOG_MAX * KIOPS_LOG_FIELDS)
-      c.kiops_log.insert(c.kiops_log.end(), rec, rec + KIOPS_LOG_FIELDS);
-    c.prev_call[0] = (float)std::log10(tau_first / tau_end);
-    c.prev_call[1] = rec[17];
-    c.prev_call[2] = rec[21];
-    c.prev_call[3] = (float)substeps;
-    c.prev_call[4] = (float)rejects;
-    c.prev_call[5] = (float)krylov / o.m_max;
-    for (int k2 = 0; k2 < 4; ++k2) {
-      double hv = (nh > k2) ? hist_h[(nh - 1 - k2) % 4] : 0.0;
-      c.prev_h[k2] = (hv > 0) ? (float)std::log10(hv) : 0.0f;
-    }
-  }
-  if (st) {
-    st->substeps = substeps;
-    st->rejects = rejects;
-    st->krylov_iters = krylov;
-    st->m_final = m;
-    st->tau_final = tau;
-    st->err_last = last_err;
-  }
+  kiops_finish_call(c, K, feat, o, st);
   return cuda_status(cudaGetLastError());
 }
 

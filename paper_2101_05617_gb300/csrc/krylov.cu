@@ -6,6 +6,7 @@
 
 #include <cmath>
 
+#include "krylov_device.cuh"
 #include "swepi_internal.h"
 
 namespace swepi {
@@ -13,28 +14,6 @@ namespace swepi {
 namespace {
 
 constexpr int RED_THREADS = 256;
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// block sum in a fixed order; result valid in thread 0
-__device__ double block_sum(double v) {
-  __shared__ double ws[32];
-  v = warp_sum(v);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) ws[w] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (w == 0) {
-    r = (lane < (int)(blockDim.x >> 5)) ? ws[lane] : 0.0;
-    r = warp_sum(r);
-  }
-  return r;
-}
 
 enum { OP_DOT = 0, OP_NORM2 = 1, OP_NORM1 = 2 };
 
@@ -140,88 +119,24 @@ __global__ void combine_kernel(double* __restrict__ X, const double* __restrict_
 }
 
 // ------------------------------------------------------------ expm
-// F = exp(A), A = t [[H_j, e_1], [0, 0]] (order N = j + 1 <= MAX_EXPM): scaling
-// and squaring (Moler and Van Loan, "Nineteen dubious ways to compute the
-// exponential of a matrix, twenty-five years later", SIAM Rev. 45, 2003) with
-// the degree-16 Taylor polynomial, evaluated by the Paterson-Stockmeyer scheme
-// (SIAM J. Comput. 2, 1973) in blocks of four powers: 6 matrix products, then s
-// squarings, s = max(0, ceil(log2(||A||_1 / 0.8))).  At ||X||_1 <= 0.8 the
-// truncated tail is below 0.8^17/17! = 6e-17.  Every product is a grid-wide FP64
-// GEMM launch (8 x 8 outputs per block): the whole GPU shares the O(N^3) work.
-constexpr int MAX_EXPM = 160;
-constexpr double kTaylorTheta = 0.8;
-
-// one block: build A (dense, leading dimension N) and its 1-norm
+// (scheme and workspace slots: krylov_device.cuh)
 __global__ void expm_prep_kernel(const double* __restrict__ H, int ldh, int j, double tau, double tau_happy,
                                  const int* happy, double* A, double* stat) {
-  const int jj = happy[0] ? happy[1] : j;
-  const double t = happy[0] ? tau_happy : tau;
-  const int N = jj + 1;
-  for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
-    int r = i / N, c = i % N;
-    double v = 0.0;
-    if (r < jj && c < jj) v = H[(long long)r * ldh + c];
-    else if (r == 0 && c == jj) v = 1.0;
-    A[i] = t * v;
-  }
-  __syncthreads();
-  __shared__ double colsum[MAX_EXPM];
-  for (int c = threadIdx.x; c < N; c += blockDim.x) {
-    double sum = 0.0;
-    for (int r = 0; r < N; ++r) sum += fabs(A[r * N + c]);
-    colsum[c] = sum;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double nrm = 0.0;
-    for (int c = 0; c < N; ++c) nrm = fmax(nrm, colsum[c]);
-    stat[1] = (double)jj;
-    stat[2] = t;
-    stat[4] = happy[0] ? 0.0 : H[(long long)jj * ldh + jj - 1];   // h_{j+1,j}
-    stat[5] = nrm;
-  }
+  expm_prep_body(H, ldh, j, tau, tau_happy, happy, A, stat);
 }
 
-struct MatEpi {
-  // C += cI * I + c1 * M1 + c2 * M2 + c3 * M3 (null matrices skipped)
-  double cI, c1, c2, c3;
-  const double* M1;
-  const double* M2;
-  const double* M3;
-  double alpha;   // C = alpha * A B + ...
-};
-
-__device__ __forceinline__ double mat_epi(const MatEpi& e, int r, int c, int N) {
-  double v = (r == c) ? e.cI : 0.0;
-  const int i = r * N + c;
-  if (e.M1) v = fma(e.c1, e.M1[i], v);
-  if (e.M2) v = fma(e.c2, e.M2[i], v);
-  if (e.M3) v = fma(e.c3, e.M3[i], v);
-  return v;
-}
-
-// C = alpha A B + epilogue; A or B null means the identity
-__global__ void __launch_bounds__(64) small_gemm_kernel(double* __restrict__ C, const double* __restrict__ A,
-                                                        const double* __restrict__ B, int N, MatEpi e) {
+// one product over the whole grid (8 x 8 outputs per block)
+__global__ void __launch_bounds__(64) small_gemm_kernel(double* __restrict__ ws, int N, int sc, int sa, int sb,
+                                                        MatEpi e) {
   const int r = blockIdx.y * 8 + threadIdx.y, c = blockIdx.x * 8 + threadIdx.x;
   if (r >= N || c >= N) return;
-  double s = 0.0;
-  if (A && B) {
-    for (int k = 0; k < N; ++k) s = fma(A[r * N + k], B[k * N + c], s);
-  } else if (A) {
-    s = A[r * N + c];
-  } else if (B) {
-    s = B[r * N + c];
-  } else {
-    s = (r == c) ? 1.0 : 0.0;
-  }
-  C[r * N + c] = e.alpha * s + mat_epi(e, r, c, N);
+  expm_gemm_entry(ws, N, sc, sa, sb, e, r, c);
 }
 
 __global__ void expm_finish_kernel(const double* __restrict__ P, int N, double* F, int ldh, double* stat) {
-  for (int i = threadIdx.x + blockIdx.x * blockDim.x; i < N * N; i += blockDim.x * gridDim.x)
-    F[(long long)(i / N) * ldh + (i % N)] = P[i];
-  if (blockIdx.x == 0 && threadIdx.x == 0) stat[0] = P[(N - 2) * N + (N - 1)];   // F[j-1][j]
+  for (long long i = threadIdx.x + (long long)blockIdx.x * blockDim.x; i < (long long)N * N;
+       i += (long long)blockDim.x * gridDim.x)
+    expm_finish_entry(P, N, F, ldh, stat, i);
 }
 
 // z -= h1 V_A + h2 V_B (the two modified Gram-Schmidt updates, in that order),
@@ -447,56 +362,32 @@ int launch_expm_prep(Ctx& c, int j, double tau, double tau_happy, cudaStream_t s
 
 int launch_expm_eval(Ctx& c, int N, double norm1, int* squarings, cudaStream_t s) {
   if (N < 2 || N > MAX_EXPM || !std::isfinite(norm1)) return SW_EINVAL;
-  int sq = 0;
-  if (norm1 > kTaylorTheta) sq = (int)std::ceil(std::log2(norm1 / kTaylorTheta));
-  if (sq > 200) return SW_ENONFINITE;
+  const int sq = expm_squarings(norm1);
+  if (sq < 0) return SW_ENONFINITE;
   if (squarings) *squarings = sq;
   const long long NN = (long long)N * N;
-  double* A = c.d_expm_ws;
-  double* X = A + NN;
-  double* X2 = X + NN;
-  double* X3 = X2 + NN;
-  double* X4 = X3 + NN;
-  double* P0 = X4 + NN;
-  double* P1 = P0 + NN;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c.prof) {
     e0 = prof_event(c);
     e1 = prof_event(c);
     cudaEventRecord(e0, s);
   }
-  double cf[17];
-  cf[0] = 1.0;
-  for (int k = 1; k <= 16; ++k) cf[k] = cf[k - 1] / k;   // 1/k!
+  ExpmProduct pr[8];
+  expm_products(sq, pr);
   const dim3 blk(8, 8), grd((N + 7) / 8, (N + 7) / 8);
-  const MatEpi none{0, 0, 0, 0, nullptr, nullptr, nullptr, 1.0};
-  MatEpi sc = none;
-  sc.alpha = std::ldexp(1.0, -sq);
-  small_gemm_kernel<<<grd, blk, 0, s>>>(X, A, nullptr, N, sc);               // X = A / 2^s
-  small_gemm_kernel<<<grd, blk, 0, s>>>(X2, X, X, N, none);
-  small_gemm_kernel<<<grd, blk, 0, s>>>(X3, X2, X, N, none);
-  small_gemm_kernel<<<grd, blk, 0, s>>>(X4, X2, X2, N, none);
-  // Paterson-Stockmeyer: T = B0 + X4 (B1 + X4 (B2 + X4 (B3 + c16 X4))), B_i = sum_k c_{4i+k} X^k
-  MatEpi b3{cf[12], cf[13], cf[14], cf[15], X, X2, X3, cf[16]};
-  small_gemm_kernel<<<grd, blk, 0, s>>>(P0, X4, nullptr, N, b3);
-  MatEpi b2{cf[8], cf[9], cf[10], cf[11], X, X2, X3, 1.0};
-  small_gemm_kernel<<<grd, blk, 0, s>>>(P1, X4, P0, N, b2);
-  MatEpi b1{cf[4], cf[5], cf[6], cf[7], X, X2, X3, 1.0};
-  small_gemm_kernel<<<grd, blk, 0, s>>>(P0, X4, P1, N, b1);
-  MatEpi b0{cf[0], cf[1], cf[2], cf[3], X, X2, X3, 1.0};
-  small_gemm_kernel<<<grd, blk, 0, s>>>(P1, X4, P0, N, b0);
-  double* cur = P1;
-  double* nxt = P0;
+  for (int k = 0; k < 8; ++k) small_gemm_kernel<<<grd, blk, 0, s>>>(c.d_expm_ws, N, pr[k].c, pr[k].a, pr[k].b, pr[k].e);
+  const MatEpi none{0, 0, 0, 0, -1, -1, -1, 1.0};
   for (int q = 0; q < sq; ++q) {
-    small_gemm_kernel<<<grd, blk, 0, s>>>(nxt, cur, cur, N, none);
-    double* t = cur; cur = nxt; nxt = t;
+    const int src = expm_square_src(q);
+    small_gemm_kernel<<<grd, blk, 0, s>>>(c.d_expm_ws, N, expm_square_dst(q), src, src, none);
   }
-  expm_finish_kernel<<<(unsigned)((NN + 255) / 256), 256, 0, s>>>(cur, N, c.d_F, c.ldh, c.d_scal + 8);
+  expm_finish_kernel<<<(unsigned)((NN + 255) / 256), 256, 0, s>>>(c.d_expm_ws + expm_result_slot(sq) * NN, N, c.d_F,
+                                                                 c.ldh, c.d_scal + 8);
   if (c.prof) {
     cudaEventRecord(e1, s);
     prof_record(c, PK_EXPM, e0, e1);
   }
-  c.launches += 10 + sq;
+  c.launches += 9 + sq;
   return cuda_status(cudaGetLastError());
 }
 

@@ -1,0 +1,154 @@
+// Device pieces of the Krylov side shared by the single-grid launchers
+// (krylov.cu) and the batched ensemble (ensemble.cu): fixed-order block
+// reductions and the exponential of the small augmented Hessenberg matrix.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+namespace swepi {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block sum in a fixed order; result valid in thread 0
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double ws[32];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) ws[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = (lane < (int)(blockDim.x >> 5)) ? ws[lane] : 0.0;
+    r = warp_sum(r);
+  }
+  return r;
+}
+
+// ------------------------------------------------------------ expm
+// F = exp(A), A = t [[H_j, e_1], [0, 0]] (order N = j + 1 <= MAX_EXPM): scaling
+// and squaring (Moler and Van Loan, "Nineteen dubious ways to compute the
+// exponential of a matrix, twenty-five years later", SIAM Rev. 45, 2003) with
+// the degree-16 Taylor polynomial, evaluated by the Paterson-Stockmeyer scheme
+// (SIAM J. Comput. 2, 1973) in blocks of four powers: 8 matrix products (the
+// first is the scaling), then s squarings, s = max(0, ceil(log2(||A||_1 / 0.8))).
+// At ||X||_1 <= 0.8 the truncated tail is below 0.8^17/17! = 6e-17.  The
+// matrices live in a workspace of XS_COUNT dense N x N slots.
+constexpr int MAX_EXPM = 160;
+constexpr double kTaylorTheta = 0.8;
+enum ExpmSlot { XS_A = 0, XS_X, XS_X2, XS_X3, XS_X4, XS_P0, XS_P1, XS_COUNT };
+
+struct MatEpi {
+  // C = alpha * A B + cI * I + c1 * M1 + c2 * M2 + c3 * M3 (slot -1: absent;
+  // A or B absent means the identity)
+  double cI, c1, c2, c3;
+  int s1, s2, s3;
+  double alpha;
+};
+
+struct ExpmProduct {
+  int c, a, b;
+  MatEpi e;
+};
+
+// the 8 products before the squarings, for s squarings
+inline void expm_products(int sq, ExpmProduct out[8]) {
+  double cf[17];
+  cf[0] = 1.0;
+  for (int k = 1; k <= 16; ++k) cf[k] = cf[k - 1] / k;   // 1/k!
+  const MatEpi none{0, 0, 0, 0, -1, -1, -1, 1.0};
+  MatEpi sc = none;
+  sc.alpha = std::ldexp(1.0, -sq);
+  out[0] = {XS_X, XS_A, -1, sc};                          // X = A / 2^s
+  out[1] = {XS_X2, XS_X, XS_X, none};
+  out[2] = {XS_X3, XS_X2, XS_X, none};
+  out[3] = {XS_X4, XS_X2, XS_X2, none};
+  // Paterson-Stockmeyer: T = B0 + X4 (B1 + X4 (B2 + X4 (B3 + c16 X4))), B_i = sum_k c_{4i+k} X^k
+  out[4] = {XS_P0, XS_X4, -1, {cf[12], cf[13], cf[14], cf[15], XS_X, XS_X2, XS_X3, cf[16]}};
+  out[5] = {XS_P1, XS_X4, XS_P0, {cf[8], cf[9], cf[10], cf[11], XS_X, XS_X2, XS_X3, 1.0}};
+  out[6] = {XS_P0, XS_X4, XS_P1, {cf[4], cf[5], cf[6], cf[7], XS_X, XS_X2, XS_X3, 1.0}};
+  out[7] = {XS_P1, XS_X4, XS_P0, {cf[0], cf[1], cf[2], cf[3], XS_X, XS_X2, XS_X3, 1.0}};
+}
+
+// number of squarings for ||A||_1 (-1: too large to be finite)
+inline int expm_squarings(double norm1) {
+  int sq = 0;
+  if (norm1 > kTaylorTheta) sq = (int)std::ceil(std::log2(norm1 / kTaylorTheta));
+  return (sq > 200) ? -1 : sq;
+}
+// squaring q reads slot expm_square_src(q) and writes the other one
+inline __host__ __device__ int expm_square_src(int q) { return (q % 2 == 0) ? XS_P1 : XS_P0; }
+inline __host__ __device__ int expm_square_dst(int q) { return (q % 2 == 0) ? XS_P0 : XS_P1; }
+// slot holding exp(A) after s squarings
+inline __host__ __device__ int expm_result_slot(int sq) { return expm_square_src(sq); }
+
+// one block: build A (dense, leading dimension N) in slot XS_A and its
+// 1-norm; stat[1] = j used, stat[2] = t, stat[4] = h_{j+1,j}, stat[5] = ||A||_1
+__device__ __forceinline__ void expm_prep_body(const double* __restrict__ H, int ldh, int j, double tau,
+                                               double tau_happy, const int* happy, double* A, double* stat) {
+  const int jj = happy[0] ? happy[1] : j;
+  const double t = happy[0] ? tau_happy : tau;
+  const int N = jj + 1;
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+    int r = i / N, c = i % N;
+    double v = 0.0;
+    if (r < jj && c < jj) v = H[(long long)r * ldh + c];
+    else if (r == 0 && c == jj) v = 1.0;
+    A[i] = t * v;
+  }
+  __syncthreads();
+  __shared__ double colsum[MAX_EXPM];
+  for (int c = threadIdx.x; c < N; c += blockDim.x) {
+    double sum = 0.0;
+    for (int r = 0; r < N; ++r) sum += fabs(A[r * N + c]);
+    colsum[c] = sum;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double nrm = 0.0;
+    for (int c = 0; c < N; ++c) nrm = fmax(nrm, colsum[c]);
+    stat[1] = (double)jj;
+    stat[2] = t;
+    stat[4] = happy[0] ? 0.0 : H[(long long)jj * ldh + jj - 1];   // h_{j+1,j}
+    stat[5] = nrm;
+  }
+}
+
+// entry (r, c) of one product in the workspace ws (slots of N x N)
+__device__ __forceinline__ void expm_gemm_entry(double* __restrict__ ws, int N, int sc, int sa, int sb,
+                                                const MatEpi& e, int r, int c) {
+  const long long NN = (long long)N * N;
+  const double* A = (sa >= 0) ? ws + sa * NN : nullptr;
+  const double* B = (sb >= 0) ? ws + sb * NN : nullptr;
+  double s = 0.0;
+  if (A && B) {
+    for (int k = 0; k < N; ++k) s = fma(A[r * N + k], B[k * N + c], s);
+  } else if (A) {
+    s = A[r * N + c];
+  } else if (B) {
+    s = B[r * N + c];
+  } else {
+    s = (r == c) ? 1.0 : 0.0;
+  }
+  const int i = r * N + c;
+  double v = (r == c) ? e.cI : 0.0;
+  if (e.s1 >= 0) v = fma(e.c1, ws[e.s1 * NN + i], v);
+  if (e.s2 >= 0) v = fma(e.c2, ws[e.s2 * NN + i], v);
+  if (e.s3 >= 0) v = fma(e.c3, ws[e.s3 * NN + i], v);
+  ws[sc * NN + i] = e.alpha * s + v;
+}
+
+// F (leading dimension ldh) = the result slot; stat[0] = F[j-1][j]
+__device__ __forceinline__ void expm_finish_entry(const double* __restrict__ P, int N, double* F, int ldh,
+                                                  double* stat, long long i) {
+  if (i < (long long)N * N) F[(i / N) * ldh + (i % N)] = P[i];
+  if (i == 0) stat[0] = P[(N - 2) * N + (N - 1)];
+}
+
+}  // namespace swepi

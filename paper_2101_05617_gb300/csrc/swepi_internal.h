@@ -161,6 +161,19 @@ void prof_record(Ctx& c, int kind, cudaEvent_t a, cudaEvent_t b);
 void prof_drain(Ctx& c);
 enum ProfKind { PK_FACE_JVP = 0, PK_VOL_JVP = 1, PK_FACE_RHS = 2, PK_VOL_RHS = 3, PK_EXPM = 4, PK_LIN = 5 };
 
+// ---- multistep EPI driver pieces (capi.cu), shared with the ensemble driver
+constexpr int EPI_STARTUP_SUBSTEPS = 8;   // EPI2 substeps of a start-up step (Sec. 4)
+struct Coefs {                            // Eq. 34-38: b_m = sum_i a[m][i] dt R(q_{n-1-i})
+  int M, P;
+  double a[4][4];
+};
+const Coefs* coefs_for(int order);        // orders 3..6, else null
+sw_kiops_opts default_opts();
+int ensure_epi(Ctx& c);
+int hist_slot(const Ctx& c, int i);       // slot of history entry i (1 = most recent)
+int push_history(Ctx& c, const double* q, const double* F, cudaStream_t s);
+void add_stats(sw_kiops_stats* acc, const sw_kiops_stats& s);
+
 // ---- geometry / tables (geom.cpp)
 int build_tables(Ctx& c);
 void node_unit_xyz(const Ctx& c, double* xyz);
@@ -243,3 +256,6 @@ int ensure_krylov(Ctx& c, int m_max);
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? SW_OK : SW_ECUDA; }
 
 }  // namespace swepi
+
+// the public context handle is the internal context
+struct sw_ctx : public swepi::Ctx {};

@@ -57,6 +57,22 @@ class sw_kiops_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class sw_ens_tiles(ctypes.Structure):
+    _fields_ = [("face_pts", ctypes.c_int), ("vol_tiles", ctypes.c_int), ("vec_len", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class sw_ens_stats(ctypes.Structure):
+    _fields_ = [("ticks", ctypes.c_longlong), ("reads", ctypes.c_longlong), ("expm_batches", ctypes.c_longlong),
+                ("launches", ctypes.c_longlong), ("iter_ms", ctypes.c_double), ("block", ctypes.c_int),
+                ("ctas", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -111,6 +127,17 @@ def lib():
     L.sw_kiops_log_clear.argtypes = [vp]
     L.sw_status_str.argtypes = [ip]
     L.sw_status_str.restype = ctypes.c_char_p
+    L.sw_ens_create.argtypes = [ip, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    L.sw_ens_free.argtypes = [vp]
+    L.sw_ens_set_block.argtypes = [vp, ip]
+    L.sw_ens_set_tiles.argtypes = [vp, ip, ctypes.POINTER(sw_ens_tiles)]
+    L.sw_ens_get_tiles.argtypes = [vp, ip, ctypes.POINTER(sw_ens_tiles)]
+    L.sw_ens_set_policy.argtypes = [vp, ctypes.c_double]
+    L.sw_ens_tune.argtypes = [vp, ctypes.POINTER(vp), ip, ctypes.POINTER(ctypes.c_int), vp]
+    L.sw_ens_epi_run.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int), dp, ctypes.POINTER(vp),
+                                 ctypes.POINTER(sw_kiops_opts), ctypes.POINTER(sw_kiops_stats), vp]
+    L.sw_ens_stats_read.argtypes = [vp, ctypes.POINTER(sw_ens_stats)]
+    L.sw_ens_profile.argtypes = [vp, ip]
     _lib = L
     return L
 
@@ -121,7 +148,9 @@ EXPORTED = ["sw_init", "sw_free", "sw_num_unknowns", "sw_grid_info", "sw_node_xy
             "sw_epi_reset", "sw_kernel_launches", "sw_profile", "sw_profile_read", "sw_fp64_fma_peak",
             "sw_status_str", "sw_mlp_create", "sw_mlp_free", "sw_mlp_set_params", "sw_mlp_get_params",
             "sw_mlp_forward", "sw_mlp_gradient", "sw_mlp_train", "sw_set_controller", "sw_kiops_log",
-            "sw_kiops_log_clear", "sw_diagnostics", "sw_error_norms"]
+            "sw_kiops_log_clear", "sw_diagnostics", "sw_error_norms", "sw_ens_create", "sw_ens_free",
+            "sw_ens_set_block", "sw_ens_set_tiles", "sw_ens_get_tiles", "sw_ens_set_policy", "sw_ens_tune",
+            "sw_ens_epi_run", "sw_ens_stats_read", "sw_ens_profile"]
 
 MLP_PARAMS = 5378
 MLP_NORM = 36
@@ -380,6 +409,114 @@ def sw_error_norms(ctx, q, q_ref, stream=None):
 
 def sw_status_str(status):
     return lib().sw_status_str(int(status)).decode()
+
+
+def sw_ens_create(ctxs):
+    arr = (ctypes.c_void_p * len(ctxs))(*[c for c in ctxs])
+    e = ctypes.c_void_p()
+    _check("sw_ens_create", lib().sw_ens_create(len(ctxs), arr, ctypes.byref(e)))
+    return e
+
+
+def sw_ens_free(e):
+    _check("sw_ens_free", lib().sw_ens_free(e))
+
+
+def sw_ens_set_block(e, block):
+    _check("sw_ens_set_block", lib().sw_ens_set_block(e, int(block)))
+
+
+def sw_ens_set_tiles(e, member, face_pts, vol_tiles, vec_len):
+    t = sw_ens_tiles(int(face_pts), int(vol_tiles), int(vec_len))
+    _check("sw_ens_set_tiles", lib().sw_ens_set_tiles(e, int(member), ctypes.byref(t)))
+
+
+def sw_ens_get_tiles(e, member):
+    t = sw_ens_tiles()
+    _check("sw_ens_get_tiles", lib().sw_ens_get_tiles(e, int(member), ctypes.byref(t)))
+    return t.as_dict()
+
+
+def sw_ens_set_policy(e, theta):
+    _check("sw_ens_set_policy", lib().sw_ens_set_policy(e, float(theta)))
+
+
+def _ptr_array(qs, sizes):
+    return (ctypes.c_void_p * len(qs))(*[_dev_ptr(q, n).value for q, n in zip(qs, sizes)])
+
+
+def sw_ens_tune(e, qs, sizes, iters=8, stream=None):
+    blk = ctypes.c_int(0)
+    _check("sw_ens_tune", lib().sw_ens_tune(e, _ptr_array(qs, sizes), int(iters), ctypes.byref(blk),
+                                            _stream(stream)))
+    return blk.value
+
+
+def sw_ens_epi_run(e, steps, orders, dts, qs, sizes, opts=None, stream=None):
+    k = len(qs)
+    o = opts if opts is not None else make_opts()
+    ords = (ctypes.c_int * k)(*[int(x) for x in orders])
+    dtv = np.ascontiguousarray(dts, dtype=np.float64).reshape(-1)
+    if dtv.size != k or len(orders) != k:
+        raise ValueError("one order and one dt per member")
+    st = (sw_kiops_stats * k)()
+    _check("sw_ens_epi_run", lib().sw_ens_epi_run(e, int(steps), ords, dtv.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                  _ptr_array(qs, sizes), ctypes.byref(o), st, _stream(stream)))
+    return [st[i].as_dict() for i in range(k)]
+
+
+def sw_ens_profile(e, enable=True):
+    _check("sw_ens_profile", lib().sw_ens_profile(e, int(bool(enable))))
+
+
+def sw_ens_stats_read(e):
+    st = sw_ens_stats()
+    _check("sw_ens_stats_read", lib().sw_ens_stats_read(e, ctypes.byref(st)))
+    return st.as_dict()
+
+
+class SWEnsemble:
+    """A batched ensemble over existing SWContext members (kept alive here)."""
+
+    def __init__(self, members):
+        self.members = list(members)
+        self.handle = sw_ens_create([m.handle for m in self.members])
+
+    def close(self):
+        if self.handle:
+            sw_ens_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_block(self, block):
+        sw_ens_set_block(self.handle, block)
+
+    def set_tiles(self, member, face_pts, vol_tiles, vec_len):
+        sw_ens_set_tiles(self.handle, member, face_pts, vol_tiles, vec_len)
+
+    def tiles(self, member):
+        return sw_ens_get_tiles(self.handle, member)
+
+    def set_policy(self, theta):
+        sw_ens_set_policy(self.handle, theta)
+
+    def tune(self, qs, iters=8, stream=None):
+        return sw_ens_tune(self.handle, qs, [m.n for m in self.members], iters, stream)
+
+    def epi_run(self, steps, orders, dts, qs, stream=None, **opts):
+        return sw_ens_epi_run(self.handle, steps, orders, dts, qs, [m.n for m in self.members], make_opts(**opts),
+                              stream)
+
+    def stats(self):
+        return sw_ens_stats_read(self.handle)
+
+    def profile(self, enable=True):
+        sw_ens_profile(self.handle, enable)
 
 
 class SWContext:

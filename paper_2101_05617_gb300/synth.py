@@ -182,6 +182,159 @@ def make_fields(workload, seed):
     return f
 
 
+# ---------------------------------------------------------------- ensemble
+# Members on uneven grids: every (n_e, p) class of ENSEMBLE_NE x ENSEMBLE_P
+# appears equally often, in a seeded order; each member draws its own grid
+# rotation, EPI order (4 or 5) and a degree <= 12 harmonic perturbation of 50 m
+# peak on top of the ensemble's shared degree <= 4, 100 m base field; the wind
+# is geostrophic for the member's total height anomaly.
+ENSEMBLE_NE = (8, 16, 24, 32)
+ENSEMBLE_P = (3, 4, 5)
+ENSEMBLE_BASE = (4, 100.0)      # degree, peak (m)
+ENSEMBLE_PERT = (12, 50.0)
+
+
+@dataclass
+class EnsembleMember:
+    index: int
+    ne: int
+    p: int
+    order: int
+    dt: float
+    seed: int
+
+    @property
+    def ns(self):
+        return self.p + 1
+
+    @property
+    def nodes(self):
+        return 6 * self.ne ** 2 * self.ns ** 2
+
+
+def ensemble_members(count=96, seed=0, ne_choices=ENSEMBLE_NE, p_choices=ENSEMBLE_P, orders=(4, 5), dt=900.0):
+    """The seeded member list (grid class, EPI order, member seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    classes = [(ne, p) for ne in ne_choices for p in p_choices]
+    reps = -(-count // len(classes))
+    pool = [classes[i % len(classes)] for i in range(reps * len(classes))]
+    perm = rng.permutation(len(pool))[:count]
+    out = []
+    for i, k in enumerate(perm):
+        ne, p = pool[k]
+        order = int(orders[rng.integers(len(orders))])
+        out.append(EnsembleMember(i, ne, p, order, dt, int(rng.integers(1 << 31))))
+    return out
+
+
+def _sph_sum(L, coef, xyz):
+    """sum over (l, m) of coef[(l, m)] Y_lm at unit vectors xyz[3, N] (same
+    harmonics and normalisation as real_sph_harm, accumulated degree by degree
+    instead of stored)."""
+    x, y, z = (np.asarray(c, dtype=float) for c in xyz)
+    ct = np.clip(z, -1.0, 1.0)
+    st = np.sqrt(np.maximum(0.0, 1.0 - ct * ct))
+    lon = np.arctan2(y, x)
+    s = np.zeros_like(ct)
+    pmm = np.full_like(ct, np.sqrt(1.0 / (4 * np.pi)))
+    for m in range(L + 1):
+        if m > 0:
+            pmm = pmm * np.sqrt((2 * m + 1) / (2.0 * m)) * st
+        acc_c = coef.get((m, m), 0.0) * pmm
+        acc_s = coef.get((m, -m), 0.0) * pmm if m > 0 else None
+        p2, p1 = None, pmm
+        for l in range(m + 1, L + 1):
+            if l == m + 1:
+                pl = np.sqrt(2 * m + 3.0) * ct * pmm
+            else:
+                a = np.sqrt((4.0 * l * l - 1) / (l * l - m * m))
+                b = np.sqrt(((l - 1.0) ** 2 - m * m) / (4.0 * (l - 1) ** 2 - 1))
+                pl = a * (ct * p1 - b * p2)
+            acc_c = acc_c + coef.get((l, m), 0.0) * pl
+            if m > 0:
+                acc_s = acc_s + coef.get((l, -m), 0.0) * pl
+            p2, p1 = p1, pl
+        if m == 0:
+            s = s + acc_c
+        else:
+            s = s + np.sqrt(2.0) * (acc_c * np.cos(m * lon) + acc_s * np.sin(m * lon))
+    return s
+
+
+class _SumField:
+    """A fixed harmonic sum (coefficients already scaled) and its surface gradient."""
+
+    def __init__(self, L, coef):
+        self.L, self.coef = L, coef
+
+    def __call__(self, xyz):
+        return _sph_sum(self.L, self.coef, np.asarray(xyz, dtype=float))
+
+    grad = HarmonicField.grad
+
+
+@dataclass
+class EnsembleFields:
+    member: EnsembleMember
+    rotation: tuple
+    anomaly: _SumField
+    h_mean: float = 8000.0
+
+    def evaluate(self, xyz):
+        """(h, h_B, V[3]) at unit vectors xyz[3, ...] (flat bottom)."""
+        shp = np.shape(xyz)[1:]
+        r = np.asarray(xyz, dtype=float).reshape(3, -1)
+        h = self.h_mean + self.anomaly(r)
+        V = GRAVITY / (2 * OMEGA * RADIUS) * np.cross(r, self.anomaly.grad(r), axis=0)
+        return h.reshape(shp), np.zeros(r.shape[1]).reshape(shp), V.reshape((3,) + shp)
+
+
+def _draw_rotation(rng):
+    return (rng.uniform(-np.pi, np.pi), rng.uniform(-np.pi / 3, np.pi / 3), rng.uniform(-np.pi, np.pi))
+
+
+def ensemble_rotation(member):
+    """The member's grid rotation (the first draws of its generator)."""
+    return _draw_rotation(np.random.Generator(np.random.PCG64(member.seed)))
+
+
+def ensemble_fields(member, ensemble_seed=0):
+    """Fields of one ensemble member: shared base plus the member's perturbation."""
+    sample = _latlon_sample()
+
+    def unit_peak(rng, L):
+        # the draws of HarmonicField, normalised to unit peak on the same sample
+        c = {(l, m): rng.standard_normal() for l in range(1, L + 1) for m in range(-l, l + 1)}
+        return c, 1.0 / np.max(np.abs(_sph_sum(L, c, sample)))
+
+    base, sb = unit_peak(np.random.Generator(np.random.PCG64(ensemble_seed)), ENSEMBLE_BASE[0])
+    rng = np.random.Generator(np.random.PCG64(member.seed))
+    rotation = _draw_rotation(rng)
+    pert, sp = unit_peak(rng, ENSEMBLE_PERT[0])
+    coef = {}
+    for c, amp in ((base, ENSEMBLE_BASE[1] * sb), (pert, ENSEMBLE_PERT[1] * sp)):
+        for k, v in c.items():
+            coef[k] = coef.get(k, 0.0) + amp * v
+    return EnsembleFields(member, rotation, _SumField(ENSEMBLE_PERT[0], coef))
+
+
+def _member_fields_job(args):
+    member, xyz, ensemble_seed = args
+    return ensemble_fields(member, ensemble_seed).evaluate(xyz)
+
+
+def ensemble_member_fields(members, xyz_list, ensemble_seed=0, workers=None):
+    """(h, h_B, V) of every member at its node positions xyz_list[i] (3 x nodes).
+    workers > 1 evaluates them in a pool of fresh ('spawn') processes, which is
+    safe after the parent has initialised CUDA."""
+    jobs = [(m, x, ensemble_seed) for m, x in zip(members, xyz_list)]
+    if not workers or workers <= 1 or len(jobs) <= 1:
+        return [_member_fields_job(j) for j in jobs]
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(workers, len(jobs))) as pool:
+        return pool.map(_member_fields_job, jobs, chunksize=1)
+
+
 def random_perturbation(n, seed, scale=1.0):
     """A seeded N(0, scale^2) vector (Krylov-like direction for JVP checks)."""
     rng = np.random.Generator(np.random.PCG64(seed))

@@ -1,0 +1,183 @@
+"""Batched ensemble (sw_ens_*): members on uneven grids advanced together.
+
+Each member must reproduce its own single-context EPI run (sw_epi_step, which
+the EPI parity tests pin to the oracle) with the same Krylov statistics, and
+the smallest members are compared with the oracle's EPI trajectory directly.
+Results may differ from the single runs only by the order of floating-point
+sums (different reduction partitions), so the bound is 1e-12 relative L2 per
+variable; tiles, threads per CTA and the scheduling policy must not change
+them beyond that."""
+import numpy as np
+import pytest
+
+from oracle import epi as oepi
+from oracle import fields as ofields
+from oracle import shallow_water as osw
+from paper_2101_05617_gb300 import synth
+from tests.gpu_common import rel_l2_per_var
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+SMALL = [(2, 3, 4), (3, 4, 5), (2, 5, 4), (4, 3, 5), (3, 5, 6), (2, 4, 3)]   # (n_e, p, EPI order)
+
+
+def _members(spec, dt=900.0, seed=7):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [synth.EnsembleMember(i, ne, p, order, dt, int(rng.integers(1 << 31)))
+            for i, (ne, p, order) in enumerate(spec)]
+
+
+def _setup(spec, **kw):
+    from paper_2101_05617_gb300 import ensemble
+    members = _members(spec, **kw)
+    ctxs, qs = ensemble.build(members, workers=1)
+    return members, ctxs, qs
+
+
+def _run_ens(members, ctxs, qs, steps, block=None, tiles=None, theta=None, tune=False):
+    from paper_2101_05617_gb300 import ensemble, swepi
+    ensemble.reset(ctxs)
+    ens = swepi.SWEnsemble(ctxs)
+    if block:
+        ens.set_block(block)
+    if tiles:
+        for i in range(len(ctxs)):
+            ens.set_tiles(i, *tiles)
+    if theta is not None:
+        ens.set_policy(theta)
+    if tune:
+        ens.tune(qs, iters=4)
+    ys = [q.clone() for q in qs]
+    st = ens.epi_run(steps, [m.order for m in members], [m.dt for m in members], ys, tol=TOL)
+    info = ens.stats()
+    ens.close()
+    return ys, st, info
+
+
+def _compare(ys, refs, bound=1e-12):
+    worst = 0.0
+    for y, r in zip(ys, refs):
+        worst = max(worst, max(rel_l2_per_var(y.cpu().numpy(), r.cpu().numpy())))
+    assert worst < bound, worst
+    return worst
+
+
+def test_ensemble_matches_single_members():
+    from paper_2101_05617_gb300 import ensemble
+    members, ctxs, qs = _setup(SMALL)
+    steps = 5   # start-up steps of EPI4-6 and multistep steps after them
+    ys, st, info = _run_ens(members, ctxs, qs, steps)
+    refs, ref_st, _ = ensemble.run_single(members, ctxs, qs, steps, tol=TOL)
+    _compare(ys, refs)
+    for a, b in zip(st, ref_st):
+        assert (a["krylov_iters"], a["rejects"], a["substeps"]) == (b["krylov_iters"], b["rejects"], b["substeps"])
+    # one graph replay served several members at a time
+    total = sum(a["krylov_iters"] for a in st)
+    assert max(a["krylov_iters"] for a in st) <= info["ticks"] < total
+    assert info["reads"] >= 1 and info["expm_batches"] >= 1 and info["launches"] > info["ticks"]
+
+
+@pytest.mark.parametrize("idx", [0, 2])
+def test_ensemble_member_vs_oracle(idx):
+    """The oracle's EPI trajectory of one member, run inside a mixed ensemble."""
+    from paper_2101_05617_gb300 import ensemble, swepi
+    members = _members(SMALL)
+    m = members[idx]
+    f = synth.ensemble_fields(m)
+    g = osw.Grid(m.ne, m.ns, f.rotation)
+    h, hB, V = f.evaluate(g.node_xyz())
+    q0 = ofields.state_from_fields(g, h, hB, V)
+    ctxs, qs = ensemble.build(members, workers=1)
+    qs[idx] = torch.tensor(q0.reshape(-1), device="cuda")
+    steps = 4
+    ys, _, _ = _run_ens(members, ctxs, qs, steps)
+    it = oepi.EPI(lambda x: osw.rhs_real(g, x.reshape(q0.shape)).reshape(-1),
+                  lambda x, v: osw.jvp(g, x.reshape(q0.shape), v.reshape(q0.shape)).reshape(-1), m.order, tol=TOL)
+    y = q0.reshape(-1).copy()
+    for _ in range(steps):
+        y = it.step(y, m.dt)
+    err = rel_l2_per_var(ys[idx].cpu().numpy(), y)
+    assert max(err) < 1e-11, err
+
+
+@pytest.mark.parametrize("block,tiles,theta", [(128, (128, 1, 512), 0.0), (512, (4096, 4, 32768), 1.0),
+                                               (256, (256, 2, 2048), 0.5)])
+def test_ensemble_tiles_and_policy_invariance(block, tiles, theta):
+    members, ctxs, qs = _setup(SMALL[:4])
+    base, st0, _ = _run_ens(members, ctxs, qs, 4)
+    ys, st, info = _run_ens(members, ctxs, qs, 4, block=block, tiles=tiles, theta=theta)
+    assert info["block"] == block
+    _compare(ys, base)
+    assert [a["krylov_iters"] for a in st] == [a["krylov_iters"] for a in st0]
+
+
+def test_ensemble_autotuner():
+    from paper_2101_05617_gb300 import swepi
+    members, ctxs, qs = _setup(SMALL)
+    base, _, _ = _run_ens(members, ctxs, qs, 3)
+    ens = swepi.SWEnsemble(ctxs)
+    block = ens.tune(qs, iters=4)
+    assert block in (128, 256, 512)
+    for i in range(len(ctxs)):
+        t = ens.tiles(i)
+        assert t["face_pts"] in (block, 2 * block, 4 * block, 8 * block)
+        assert t["vol_tiles"] in (1, 2, 4)
+        assert t["vec_len"] in (4 * block, 16 * block, 64 * block)
+    # same (n_e, p) class -> same tiles
+    ens.close()
+    ys, _, info = _run_ens(members, ctxs, qs, 3, tune=True)
+    assert info["block"] in (128, 256, 512)
+    _compare(ys, base)
+
+
+def test_ensemble_invalid_arguments():
+    from paper_2101_05617_gb300 import swepi
+    members, ctxs, qs = _setup(SMALL[:2])
+    with pytest.raises(swepi.SWError):
+        swepi.SWEnsemble([ctxs[0], ctxs[0]])                     # a context twice
+    c2 = swepi.SWContext(2, 2)                                   # p = 2: outside the batched kernel's range
+    with pytest.raises(swepi.SWError):
+        swepi.SWEnsemble([ctxs[0], c2])
+    ens = swepi.SWEnsemble(ctxs)
+    ys = [q.clone() for q in qs]
+    with pytest.raises(swepi.SWError):
+        ens.epi_run(1, [4, 4], [900.0, 900.0], ys, iop=3)         # the batched kernel fuses iop = 2 only
+    with pytest.raises(swepi.SWError):
+        ens.epi_run(1, [7, 4], [900.0, 900.0], ys)                # EPI order out of range
+    ctxs[1].set_jvp_mode(0)
+    with pytest.raises(swepi.SWError):
+        ens.epi_run(1, [4, 4], [900.0, 900.0], ys)                # members run the split FP64 JVP
+    ctxs[1].set_jvp_mode(1)
+    with pytest.raises(swepi.SWError):
+        ens.set_block(384)
+    with pytest.raises(swepi.SWError):
+        ens.set_tiles(0, 16, 1, 1024)
+    with pytest.raises(swepi.SWError):
+        ens.set_policy(1.5)
+    ens.close()
+
+
+def test_ensemble_full_size_sampled():
+    """The 96-member ensemble (n_e in {8, 16, 24, 32}, p in {3, 4, 5}, EPI4/5,
+    dt = 900 s) for two steps in the launch configuration the benchmark times
+    (autotuned); the smallest, a median and the largest member against their
+    single-context runs."""
+    from paper_2101_05617_gb300 import ensemble, swepi
+    members = synth.ensemble_members()
+    ctxs, qs = ensemble.build(members)
+    ens = swepi.SWEnsemble(ctxs)
+    ens.tune(qs, iters=4)
+    ys = [q.clone() for q in qs]
+    st = ens.epi_run(2, [m.order for m in members], [m.dt for m in members], ys, tol=TOL)
+    ens.close()
+    order = sorted(range(len(members)), key=lambda i: members[i].nodes)
+    pick = [order[0], order[len(order) // 2], order[-1]]
+    sub = [members[i] for i in pick]
+    refs, ref_st, _ = ensemble.run_single(sub, [ctxs[i] for i in pick], [qs[i] for i in pick], 2, tol=TOL)
+    _compare([ys[i] for i in pick], refs)
+    for i, r in zip(pick, ref_st):
+        assert st[i]["krylov_iters"] == r["krylov_iters"]
+    for y in ys:
+        assert torch.isfinite(y).all()
