@@ -268,8 +268,9 @@ def ensemble_form(args, dev, fp64_peak):
     for i, m in enumerate(members):
         pick.setdefault((m.ne, m.p), i)
     idx = sorted(pick.values())
-    refs, _, single_s = ensemble.run_single([members[i] for i in idx], [ctxs[i] for i in idx], [qs[i] for i in idx],
-                                            steps, tol=1e-10)
+    refs, ref_st, single_s = ensemble.run_single([members[i] for i in idx], [ctxs[i] for i in idx],
+                                                 [qs[i] for i in idx], steps, tol=1e-10)
+    same_krylov = sum(int(st[i]["krylov_iters"] == r["krylov_iters"]) for i, r in zip(idx, ref_st))
     diff = 0.0
     for i, r in zip(idx, refs):
         a, b = ys[i].view(3, -1), r.view(3, -1)
@@ -292,7 +293,7 @@ def ensemble_form(args, dev, fp64_peak):
                                  "frac": (achieved / fp64_peak) if achieved and fp64_peak else None},
             "single_member_path": {"members": len(idx), "seconds": single_s,
                                    "member_steps_per_s": len(idx) * steps / single_s},
-            "max_rel_l2_vs_single": diff, "build_s": build_s}
+            "max_rel_l2_vs_single": diff, "members_with_equal_krylov_count": same_krylov, "build_s": build_s}
 
 
 def run_reference(args, world, rank):

@@ -512,6 +512,13 @@ struct Ens {
   int last_block = -1;
   double theta = 0.5;
   sw_ens_stats st{};
+  // per-member streams: a member's own kernels (RHS, linearisation, remainders,
+  // norms, combinations) overlap with other members'; the shared stream waits
+  // on a member's stream (event) before any batched work that touches it
+  std::vector<cudaStream_t> mstream;
+  std::vector<cudaEvent_t> mevent;
+  std::vector<char> dirty;
+  cudaEvent_t start_event = nullptr;   // member streams wait for the caller's stream at a run's start
   // event timing of the batched iterations (sw_ens_profile)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -581,6 +588,27 @@ int upload_j(Ens& e, int m, int j, cudaStream_t s) {
   return upload(e, &e.d_dyn[m].j, &e.hdyn[m].j, sizeof(int), s);
 }
 
+// the stream of member m's own kernels (marks it as having unjoined work)
+cudaStream_t member_stream(Ens& e, int m) {
+  e.dirty[m] = 1;
+  return e.mstream[m];
+}
+
+// make the shared stream s wait for member m's issued work
+int join_member(Ens& e, int m, cudaStream_t s) {
+  if (!e.dirty[m]) return SW_OK;
+  e.dirty[m] = 0;
+  if (cudaEventRecord(e.mevent[m], e.mstream[m]) != cudaSuccess) return SW_ECUDA;
+  return cuda_rc(cudaStreamWaitEvent(s, e.mevent[m], 0));
+}
+
+int join_all(Ens& e, cudaStream_t s) {
+  int rc;
+  for (int m = 0; m < e.count; ++m)
+    if ((rc = join_member(e, m, s))) return rc;
+  return SW_OK;
+}
+
 template <int BLOCK>
 int capture_block(Ens& e, int bi) {
   int nb = 0;
@@ -612,6 +640,10 @@ int ensure_graph(Ens& e, int block) {
 // one batched Krylov iteration of the members in `ids` (graph replay)
 int launch_iteration(Ens& e, const std::vector<int>& ids, cudaStream_t s) {
   if (ids.empty()) return SW_OK;
+  for (int m : ids) {
+    int rc = join_member(e, m, s);
+    if (rc) return rc;
+  }
   if (ids != e.last_ids || e.list_dirty || e.last_block != e.block) {
     EnsList& L = e.hlist;
     L.count = (int)ids.size();
@@ -669,6 +701,8 @@ void drain_events(Ens& e) {
 
 // one read-back of every member's scalars and flags (a full synchronisation)
 int gather(Ens& e, cudaStream_t s) {
+  int rc = join_all(e, s);
+  if (rc) return rc;
   ens_gather_kernel<<<(e.count * ENS_GATHER + 255) / 256, 256, 0, s>>>(e.d_gsrc, e.count, e.d_ctl, e.d_gather);
   e.st.launches++;
   if (cudaGetLastError() != cudaSuccess) return SW_ECUDA;
@@ -688,6 +722,7 @@ int call_start(Ens& e, int m, double dt, int nb, const double* const* b, double*
                cudaStream_t s) {
   Member& M = e.mem[m];
   Ctx& c = *M.c;
+  const cudaStream_t ms = member_stream(e, m);   // s: the shared stream (uploads)
   M.o = o0;
   if (c.m_warm > 0) M.o.m_init = c.m_warm;   // warm start from the previous call (as phi_call)
   const long long n = c.n;
@@ -703,15 +738,15 @@ int call_start(Ens& e, int m, double dt, int nb, const double* const* b, double*
   int rc;
   for (int k = 1; k <= p; ++k) {
     if (M.bk[k]) {
-      if ((rc = launch_norm1(c, M.bk[k], n, c.d_scal + S_NORMB + k, s))) return rc;
-    } else if (cudaMemsetAsync(c.d_scal + S_NORMB + k, 0, sizeof(double), s) != cudaSuccess) {
+      if ((rc = launch_norm1(c, M.bk[k], n, c.d_scal + S_NORMB + k, ms))) return rc;
+    } else if (cudaMemsetAsync(c.d_scal + S_NORMB + k, 0, sizeof(double), ms) != cudaSuccess) {
       return SW_ECUDA;
     }
   }
   if (M.bk[0]) {
-    if (cudaMemcpyAsync(c.d_X, M.bk[0], sizeof(double) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    if (cudaMemcpyAsync(c.d_X, M.bk[0], sizeof(double) * n, cudaMemcpyDeviceToDevice, ms) != cudaSuccess)
       return SW_ECUDA;
-  } else if (cudaMemsetAsync(c.d_X, 0, sizeof(double) * n, s) != cudaSuccess) {
+  } else if (cudaMemsetAsync(c.d_X, 0, sizeof(double) * n, ms) != cudaSuccess) {
     return SW_ECUDA;
   }
   M.cst = CS_SETUP1;
@@ -724,10 +759,11 @@ int epi_after_call(Ens& e, int m, const sw_kiops_opts& o, cudaStream_t s);
 int attempt(Ens& e, int m, const sw_kiops_opts& o, cudaStream_t s) {
   Member& M = e.mem[m];
   Ctx& c = *M.c;
+  const cudaStream_t ms = member_stream(e, m);   // s: the shared stream (uploads)
   KiopsController& K = M.K;
   int rc;
   if (K.done()) {
-    if (cudaMemcpyAsync(M.w, c.d_X, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    if (cudaMemcpyAsync(M.w, c.d_X, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, ms) != cudaSuccess)
       return SW_ECUDA;
     sw_kiops_stats st{};
     kiops_finish_call(c, K, M.feat, M.o, &st);
@@ -740,10 +776,10 @@ int attempt(Ens& e, int m, const sw_kiops_opts& o, cudaStream_t s) {
   const int j = K.j;
   M.m_cur = K.m;
   if (j == 0) {
-    if ((rc = launch_norm2(c, c.d_X, N, c.d_scal + S_BETA, 0.0, nullptr, 0, nullptr, s))) return rc;
-    if ((rc = launch_scale_inv(c, c.d_V, c.d_X, c.d_scal + S_BETA, N, nullptr, s))) return rc;
-    if (cudaMemsetAsync(c.d_flags, 0, sizeof(int) * 2, s) != cudaSuccess) return SW_ECUDA;
-    if (cudaMemsetAsync(c.d_H, 0, sizeof(double) * c.ldh * c.ldh, s) != cudaSuccess) return SW_ECUDA;
+    if ((rc = launch_norm2(c, c.d_X, N, c.d_scal + S_BETA, 0.0, nullptr, 0, nullptr, ms))) return rc;
+    if ((rc = launch_scale_inv(c, c.d_V, c.d_X, c.d_scal + S_BETA, N, nullptr, ms))) return rc;
+    if (cudaMemsetAsync(c.d_flags, 0, sizeof(int) * 2, ms) != cudaSuccess) return SW_ECUDA;
+    if (cudaMemsetAsync(c.d_H, 0, sizeof(double) * c.ldh * c.ldh, ms) != cudaSuccess) return SW_ECUDA;
   }
   if (j < M.m_cur) {
     if (M.j_dev != j && (rc = upload_j(e, m, j, s))) return rc;
@@ -760,6 +796,7 @@ int attempt(Ens& e, int m, const sw_kiops_opts& o, cudaStream_t s) {
 int on_read(Ens& e, int m, const double* g, const sw_kiops_opts& o, std::vector<int>& evals, cudaStream_t s) {
   Member& M = e.mem[m];
   Ctx& c = *M.c;
+  const cudaStream_t ms = member_stream(e, m);   // s: the shared stream (uploads)
   int rc;
   switch (M.cst) {
     case CS_SETUP1: {
@@ -776,8 +813,8 @@ int on_read(Ens& e, int m, const double* g, const sw_kiops_opts& o, std::vector<
       }
       double tail[MAX_NB] = {};
       tail[M.p - 1] = M.mu;
-      if ((rc = launch_set_tail(c, c.d_X, c.n, M.p, tail, s))) return rc;
-      if ((rc = launch_norm2(c, c.d_X, c.n + M.p, c.d_scal + S_BETA0, 0.0, nullptr, 0, nullptr, s))) return rc;
+      if ((rc = launch_set_tail(c, c.d_X, c.n, M.p, tail, ms))) return rc;
+      if ((rc = launch_norm2(c, c.d_X, c.n + M.p, c.d_scal + S_BETA0, 0.0, nullptr, 0, nullptr, ms))) return rc;
       M.cst = CS_SETUP2;
       M.wait = W_READ;
       return SW_OK;
@@ -817,12 +854,12 @@ int on_read(Ens& e, int m, const double* g, const sw_kiops_opts& o, std::vector<
       KiopsController& K = M.K;
       const bool happy = g[32] != 0.0;
       if ((rc = K.decide(happy, happy ? (int)g[33] : M.m_cur, g[S_BETA], g[S_STAT + 4], g[S_STAT + 0]))) return rc;
-      if (K.accept && (rc = launch_combine(c, K.j_used, c.n, s))) return rc;
+      if (K.accept && (rc = launch_combine(c, K.j_used, c.n, ms))) return rc;
       if ((rc = K.finish(kMaxSubsteps, kMaxRejects))) return rc;
       if (K.accept) {
         double tv[MAX_NB];
         K.tail(M.p, M.mu, tv);
-        if ((rc = launch_set_tail(c, c.d_X, c.n, M.p, tv, s))) return rc;
+        if ((rc = launch_set_tail(c, c.d_X, c.n, M.p, tv, ms))) return rc;
       }
       return attempt(e, m, o, s);
     }
@@ -837,12 +874,13 @@ int epi_begin_step(Ens& e, int m, const sw_kiops_opts& o, cudaStream_t s);
 int epi2_start(Ens& e, int m, double h, const sw_kiops_opts& o, cudaStream_t s) {
   Member& M = e.mem[m];
   Ctx& c = *M.c;
+  const cudaStream_t ms = member_stream(e, m);   // s: the shared stream (uploads)
   int rc;
   M.h = h;
   const double* xs[1] = {c.d_Fn};
   double cf[1] = {h};
-  if ((rc = launch_lincomb(c, c.d_b[0], c.n, 1, xs, cf, s))) return rc;
-  if ((rc = launch_linearize(c, M.q, s))) return rc;
+  if ((rc = launch_lincomb(c, c.d_b[0], c.n, 1, xs, cf, ms))) return rc;
+  if ((rc = launch_linearize(c, M.q, ms))) return rc;
   const double* b[2] = {nullptr, c.d_b[0]};
   return call_start(e, m, h, 2, b, c.d_tmp, o, s);
 }
@@ -850,11 +888,12 @@ int epi2_start(Ens& e, int m, double h, const sw_kiops_opts& o, cudaStream_t s) 
 int epi_begin_step(Ens& e, int m, const sw_kiops_opts& o, cudaStream_t s) {
   Member& M = e.mem[m];
   Ctx& c = *M.c;
+  const cudaStream_t ms = member_stream(e, m);   // s: the shared stream (uploads)
   const long long n = c.n;
   int rc;
   c.epi_order = M.order;
   c.epi_stage = 0;
-  if ((rc = launch_rhs(c, M.q, c.d_Fn, s))) return rc;
+  if ((rc = launch_rhs(c, M.q, c.d_Fn, ms))) return rc;
   if (M.order == 2) {
     M.kind = 0;
     return epi2_start(e, m, M.dt, o, s);
@@ -862,7 +901,7 @@ int epi_begin_step(Ens& e, int m, const sw_kiops_opts& o, cudaStream_t s) {
   const Coefs* A = coefs_for(M.order);
   if (c.hist_count < A->P) {
     // start-up: EPI2 with smaller substeps (Sec. 4)
-    if ((rc = push_history(c, M.q, c.d_Fn, s))) return rc;
+    if ((rc = push_history(c, M.q, c.d_Fn, ms))) return rc;
     c.epi_stage = 1;
     M.kind = 1;
     M.sub = 0;
@@ -870,17 +909,17 @@ int epi_begin_step(Ens& e, int m, const sw_kiops_opts& o, cudaStream_t s) {
   }
   M.kind = 2;
   // remainders R(q_{n-i}) = F(q_{n-i}) - F_n - J_n (q_{n-i} - q_n)  (Eq. 33)
-  if ((rc = launch_linearize(c, M.q, s))) return rc;
+  if ((rc = launch_linearize(c, M.q, ms))) return rc;
   for (int i = 1; i <= A->P; ++i) {
     const int slot = hist_slot(c, i);
     const double* d1[2] = {c.d_hq[slot], M.q};
     double c1[2] = {1.0, -1.0};
-    if ((rc = launch_lincomb(c, c.d_tmp, n, 2, d1, c1, s))) return rc;
+    if ((rc = launch_lincomb(c, c.d_tmp, n, 2, d1, c1, ms))) return rc;
     AugEpilogue ep;
-    if ((rc = launch_jvp_lin(c, c.d_tmp, c.d_tmp2, ep, s, false))) return rc;
+    if ((rc = launch_jvp_lin(c, c.d_tmp, c.d_tmp2, ep, ms, false))) return rc;
     const double* d2[3] = {c.d_hF[slot], c.d_Fn, c.d_tmp2};
     double c2[3] = {1.0, -1.0, -1.0};
-    if ((rc = launch_lincomb(c, c.d_R[i - 1], n, 3, d2, c2, s))) return rc;
+    if ((rc = launch_lincomb(c, c.d_R[i - 1], n, 3, d2, c2, ms))) return rc;
   }
   // b_1 = dt F_n + v_1, b_m = v_m with v_m = sum_i alpha_{m,i} dt R_i  (Eq. 34-35)
   for (int k = 0; k < A->M; ++k) {
@@ -897,7 +936,7 @@ int epi_begin_step(Ens& e, int m, const sw_kiops_opts& o, cudaStream_t s) {
       cf[t] = A->a[k][i] * M.dt;
       ++t;
     }
-    if ((rc = launch_lincomb(c, c.d_b[k], n, t, xs, cf, s))) return rc;
+    if ((rc = launch_lincomb(c, c.d_b[k], n, t, xs, cf, ms))) return rc;
   }
   const double* b[MAX_NB] = {nullptr};
   for (int k = 0; k < A->M; ++k) b[k + 1] = c.d_b[k];
@@ -907,13 +946,14 @@ int epi_begin_step(Ens& e, int m, const sw_kiops_opts& o, cudaStream_t s) {
 int epi_after_call(Ens& e, int m, const sw_kiops_opts& o, cudaStream_t s) {
   Member& M = e.mem[m];
   Ctx& c = *M.c;
+  const cudaStream_t ms = member_stream(e, m);   // s: the shared stream (uploads)
   int rc;
   const double* ys[2] = {M.q, c.d_tmp};
   double one[2] = {1.0, 1.0};
-  if (M.kind == 2 && (rc = push_history(c, M.q, c.d_Fn, s))) return rc;
-  if ((rc = launch_lincomb(c, M.q, c.n, 2, ys, one, s))) return rc;
+  if (M.kind == 2 && (rc = push_history(c, M.q, c.d_Fn, ms))) return rc;
+  if ((rc = launch_lincomb(c, M.q, c.n, 2, ys, one, ms))) return rc;
   if (M.kind == 1 && ++M.sub < EPI_STARTUP_SUBSTEPS) {
-    if ((rc = launch_rhs(c, M.q, c.d_Fn, s))) return rc;
+    if ((rc = launch_rhs(c, M.q, c.d_Fn, ms))) return rc;
     return epi2_start(e, m, M.h, o, s);
   }
   if (M.kind == 1) c.epi_stage = 0;
@@ -933,6 +973,8 @@ int launch_prep_batch(Ens& e, std::vector<ExpmJob>& jobs, std::vector<int>& ids,
     if (M.wait != W_PREP) continue;
     Ctx& c = *M.c;
     if (M.m_cur + 1 > MAX_EXPM) return SW_EINVAL;
+    int rc = join_member(e, m, s);
+    if (rc) return rc;
     ExpmJob jb{c.d_H, c.ldh, M.m_cur, M.K.tau, M.K.tau_end - M.K.tau_now, c.d_flags, c.d_expm_ws, c.d_scal + S_STAT,
                c.d_F, 0, 0};
     jobs.push_back(jb);
@@ -954,6 +996,8 @@ int launch_eval_batch(Ens& e, const std::vector<int>& evals, cudaStream_t s) {
   for (int m : evals) {
     Member& M = e.mem[m];
     Ctx& c = *M.c;
+    int rcj = join_member(e, m, s);
+    if (rcj) return rcj;
     ExpmJob jb{c.d_H, c.ldh, M.m_cur, 0.0, 0.0, c.d_flags, c.d_expm_ws, c.d_scal + S_STAT, c.d_F, M.ne_expm, M.sq};
     jobs.push_back(jb);
     maxN = std::max(maxN, M.ne_expm);
@@ -1014,6 +1058,10 @@ int ens_run(Ens& e, int steps, const int* orders, const double* dts, double* con
     M.wait = W_DONE;
     M.j_dev = -1;
   }
+  // the caller's earlier work on s (e.g. the initial states) comes first
+  if (cudaEventRecord(e.start_event, s) != cudaSuccess) return SW_ECUDA;
+  for (int m = 0; m < e.count; ++m)
+    if (cudaStreamWaitEvent(e.mstream[m], e.start_event, 0) != cudaSuccess) return SW_ECUDA;
   for (int m = 0; m < e.count; ++m) {
     if (steps == 0) break;
     // the lin tables are allocated by the first linearisation: start each member, then refresh its tables
@@ -1079,6 +1127,7 @@ int ens_run(Ens& e, int steps, const int* orders, const double* dts, double* con
       if ((rc = launch_eval_batch(e, evals, s))) return rc;
     }
   }
+  if ((rc = join_all(e, s))) return rc;
   if (cudaStreamSynchronize(s) != cudaSuccess) return SW_ECUDA;
   e.ring_off = 0;
   drain_events(e);
@@ -1259,6 +1308,11 @@ void ens_release(sw_ens* e) {
   cudaFree(e->d_jobs);
   cudaFree(e->d_upart);
   for (cudaEvent_t ev : e->ev_pool) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : e->mevent)
+    if (ev) cudaEventDestroy(ev);
+  if (e->start_event) cudaEventDestroy(e->start_event);
+  for (cudaStream_t st : e->mstream)
+    if (st) cudaStreamDestroy(st);
   if (e->h_gather) cudaFreeHost(e->h_gather);
   if (e->h_ring) cudaFreeHost(e->h_ring);
   delete e;
@@ -1337,6 +1391,13 @@ int sw_ens_create(int members, const sw_ctx_t* ctxs, sw_ens_t* out) {
        cudaMemset(e->d_list, 0, sizeof(EnsList)) == cudaSuccess &&
        cudaMemcpy(e->d_gsrc, gsrc.data(), sizeof(GatherSrc) * members, cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+  e->mstream.assign(members, nullptr);
+  e->mevent.assign(members, nullptr);
+  e->dirty.assign(members, 0);
+  ok = ok && cudaEventCreateWithFlags(&e->start_event, cudaEventDisableTiming) == cudaSuccess;
+  for (int m = 0; m < members && ok; ++m)
+    ok = cudaStreamCreateWithFlags(&e->mstream[m], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&e->mevent[m], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     ens_release(e);
     return SW_ECUDA;

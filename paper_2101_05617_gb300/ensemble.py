@@ -50,3 +50,43 @@ def run_single(members, ctxs, qs, steps, **opts):
         stats.append(tot)
     torch.cuda.synchronize()
     return outs, stats, time.perf_counter() - t0
+
+
+def main():
+    """Run a seeded ensemble and print one JSON line (members/s, statistics)."""
+    import argparse
+    import json
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--members", type=int, default=96)
+    ap.add_argument("--one-per-class", action="store_true", help="keep the first member of each (n_e, p) class")
+    ap.add_argument("--steps", type=int, default=24)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--m-max", type=int, default=128)
+    ap.add_argument("--no-tune", action="store_true")
+    args = ap.parse_args()
+    members = synth.ensemble_members(args.members, seed=args.seed)
+    if args.one_per_class:
+        seen, keep = set(), []
+        for m in members:
+            if (m.ne, m.p) not in seen:
+                seen.add((m.ne, m.p))
+                keep.append(m)
+        members = keep
+    ctxs, qs = build(members)
+    ens = swepi.SWEnsemble(ctxs)
+    block = None if args.no_tune else ens.tune(qs, iters=4)
+    ys = [q.clone() for q in qs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = ens.epi_run(args.steps, [m.order for m in members], [m.dt for m in members], ys, m_max=args.m_max)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    out = {"members": len(members), "steps": args.steps, "seconds": sec, "members_per_s": len(members) / sec,
+           "krylov_iters": sum(s["krylov_iters"] for s in st), "tuned_block": block, **ens.stats()}
+    ens.close()
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

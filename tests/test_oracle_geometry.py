@@ -3,6 +3,7 @@ import numpy as np
 import pytest
 
 from oracle import geometry as geo
+from tests.golden_tables import entries, golden_app_c
 
 ROTATIONS = [(0.0, 0.0, 0.0), (0.0, np.pi / 4, 0.0), (0.7, -0.4, 1.9), (-2.5, 0.9, -0.3)]
 
@@ -145,21 +146,12 @@ def test_interfaces_coincide(rot):
 
 def _appc(pa, pb, s):
     """The printed App. C contravariant relations A_(p) = T A_(q), Eq. (100)-(135),
-    keyed by interface; s = 2Z/(1+Z^2) with Z the along-edge tan-coordinate of the
-    panel named in the paper.  Returns (p, q, T)."""
-    one, zero = np.ones_like(s), np.zeros_like(s)
-    if pb == 4 or pb == 5:
-        q = pa
-        tabs = {
-            (4, 0): [[one, -s], [zero, one]], (4, 1): [[zero, -one], [one, -s]],
-            (4, 2): [[-one, s], [zero, -one]], (4, 3): [[zero, one], [-one, s]],
-            (5, 0): [[one, s], [zero, one]], (5, 1): [[zero, one], [-one, -s]],
-            (5, 2): [[-one, -s], [zero, -one]], (5, 3): [[zero, -one], [one, s]],
-        }
-        return pb, q, np.array(tabs[(pb, q)])
-    # ring (p, q) = (0,1), (1,2), (2,3), (3,0)
-    p, q = (pa, pb) if pb == pa + 1 else (pb, pa)
-    return p, q, np.array([[one, zero], [s, one]])
+    read from tests/golden/app_c_relations.txt for the interface {pa, pb};
+    s = 2Z/(1+Z^2) with Z the tan-coordinate named by the paper.  Returns (p, q, T)."""
+    for row in golden_app_c():
+        if {row["p"], row["q"]} == {pa, pb}:
+            return row["p"], row["q"], entries(row["M"], s)
+    raise KeyError((pa, pb))
 
 
 @pytest.mark.parametrize("rot", ROTATIONS[:2])
