@@ -294,13 +294,16 @@ long long sw_kernel_launches(sw_ctx_t ctx);
  * pending events and returns per-family launch counts and summed device
  * milliseconds since the last sw_profile(ctx, 1).  kind: 0 = face flux (JVP),
  * 1 = volume (JVP), 2 = face flux (RHS), 3 = volume (RHS), 4 = exponential,
- * 5 = linearisation of the split JVP. */
-#define SW_PROF_KINDS 6
+ * 5 = linearisation of the split JVP, 6 = the two vector passes of the fused
+ * orthogonalisation (update + norm, scale + dot). */
+#define SW_PROF_KINDS 7
 typedef struct {
   long long count[SW_PROF_KINDS];
   double ms[SW_PROF_KINDS];
 } sw_profile_stats;
 int sw_profile(sw_ctx_t ctx, int enable);
+/* time only the kinds whose bit (1 << kind) is set in mask (0 = off); resets the counts */
+int sw_profile_kinds(sw_ctx_t ctx, unsigned mask);
 int sw_profile_read(sw_ctx_t ctx, sw_profile_stats* out);
 
 /* Measured FP64 fused-multiply-add throughput of the current device in

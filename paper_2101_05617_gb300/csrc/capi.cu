@@ -168,7 +168,18 @@ extern "C" {
 int sw_profile(sw_ctx_t c, int enable) {
   if (!c) return SW_EINVAL;
   prof_drain(*c);
-  c->prof = enable != 0;
+  c->prof = enable ? (1u << SW_PROF_KINDS) - 1u : 0u;
+  for (int k = 0; k < SW_PROF_KINDS; ++k) {
+    c->prof_count[k] = 0;
+    c->prof_ms[k] = 0.0;
+  }
+  return SW_OK;
+}
+
+int sw_profile_kinds(sw_ctx_t c, unsigned mask) {
+  if (!c || (mask >> SW_PROF_KINDS)) return SW_EINVAL;
+  prof_drain(*c);
+  c->prof = mask;
   for (int k = 0; k < SW_PROF_KINDS; ++k) {
     c->prof_count[k] = 0;
     c->prof_ms[k] = 0.0;

@@ -183,24 +183,28 @@ static int launch_ns(Ctx& c, const double* q, const double* v, double eps, doubl
   FaceArgs fa{q, v, eps, c.nodes, c.d_lines, c.d_face_coef, c.nfacepts, c.d_fb, ep.skip};
   int fthreads = 128;
   long long fblocks = (c.nfacepts + fthreads - 1) / fthreads;
+  const bool jvp = v != nullptr;
+  const int kf = jvp ? PK_FACE_JVP : PK_FACE_RHS, kv = jvp ? PK_VOL_JVP : PK_VOL_RHS;
+  const bool pf = prof_on(c, kf), pv = prof_on(c, kv);
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
-  if (c.prof) {
+  if (pf) {
     e0 = prof_event(c);
-    e1 = prof_event(c);
-    e2 = prof_event(c);
     cudaEventRecord(e0, s);
   }
   face_flux_kernel<T, NS><<<(unsigned)fblocks, fthreads, 0, s>>>(fa, c.dc);
-  if (c.prof) cudaEventRecord(e1, s);
+  if (pf || pv) {
+    e1 = prof_event(c);
+    cudaEventRecord(e1, s);
+  }
   VolArgs va{q, v, eps, c.nodes, c.nelem, c.d_node_coef, c.d_fb, out, ep};
   long long vblocks = (c.nelem + VolShape<NS>::EPB - 1) / VolShape<NS>::EPB;
   volume_kernel<T, NS><<<(unsigned)vblocks, VolShape<NS>::THREADS, 0, s>>>(va, c.dc);
-  if (c.prof) {
+  if (pv) {
+    e2 = prof_event(c);
     cudaEventRecord(e2, s);
-    const bool jvp = v != nullptr;
-    prof_record(c, jvp ? PK_FACE_JVP : PK_FACE_RHS, e0, e1);
-    prof_record(c, jvp ? PK_VOL_JVP : PK_VOL_RHS, e1, e2);
+    prof_record(c, kv, e1, e2);
   }
+  if (pf) prof_record(c, kf, e0, e1);
   c.launches += 2;
   return cuda_status(cudaGetLastError());
 }

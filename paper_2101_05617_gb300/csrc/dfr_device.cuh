@@ -139,18 +139,23 @@ struct VolShape {
 // out = scale * res + nu * sum_l y_l b_{p-l} (the augmented operator of the
 // phi-function solver), the shift of the augmented tail, and -- when dotB is
 // set -- the window dot products of the incomplete orthogonalisation.
-template <int THREADS>
+// SCALED: the caller has already multiplied res by scale.
+template <int THREADS, bool SCALED = false>
 __device__ __forceinline__ void volume_epilogue(const AugEpilogue& ep, bool active, long long idx, long long N,
                                                 const double res[3], double* __restrict__ out, unsigned int blk,
                                                 unsigned int nblk) {
+  // the tail coefficients nu * y_l, once per block
+  __shared__ double coef[MAX_NB];
+  if (threadIdx.x < MAX_NB) {
+    const int l = threadIdx.x;
+    coef[l] = (l < ep.p && ep.b[l]) ? ep.nu * ep.tail_in[l] : 0.0;
+  }
+  __syncthreads();
   double da = 0.0, db = 0.0;
   if (active) {
-    double coef[MAX_NB];
-#pragma unroll
-    for (int l = 0; l < MAX_NB; ++l) coef[l] = (l < ep.p && ep.b[l]) ? ep.nu * ep.tail_in[l] : 0.0;
 #pragma unroll
     for (int mu = 0; mu < 3; ++mu) {
-      double o = ep.scale * res[mu];
+      double o = SCALED ? res[mu] : ep.scale * res[mu];
 #pragma unroll
       for (int l = 0; l < MAX_NB; ++l)
         if (l < ep.p && ep.b[l]) o = fma(coef[l], ep.b[l][idx + mu * N], o);

@@ -141,24 +141,27 @@ int linearize_ns(Ctx& c, const double* q, cudaStream_t s) {
 template <typename T, int NS>
 int tangent_ns(Ctx& c, const double* v, double* out, const AugEpilogue& ep, const T* ln, const T* lf, T* fb,
                cudaStream_t s) {
+  const bool pf = prof_on(c, PK_FACE_JVP), pv = prof_on(c, PK_VOL_JVP);
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
-  if (c.prof) {
+  if (pf) {
     e0 = prof_event(c);
-    e1 = prof_event(c);
-    e2 = prof_event(c);
     cudaEventRecord(e0, s);
   }
   TanFaceArgs<T> fa{v, c.nodes, c.d_lines, c.d_face_coef, lf, c.nfacepts, fb, ep.skip};
   face_tangent_kernel<T, NS><<<(unsigned)((c.nfacepts + 127) / 128), 128, 0, s>>>(fa, c.dc);
-  if (c.prof) cudaEventRecord(e1, s);
+  if (pf || pv) {
+    e1 = prof_event(c);
+    cudaEventRecord(e1, s);
+  }
   TanVolArgs<T> va{v, c.nodes, c.nelem, ln, fb, out, ep};
   const long long vblocks = (c.nelem + VolShape<NS>::EPB - 1) / VolShape<NS>::EPB;
   volume_tangent_kernel<T, NS><<<(unsigned)vblocks, VolShape<NS>::THREADS, 0, s>>>(va, c.dc);
-  if (c.prof) {
+  if (pv) {
+    e2 = prof_event(c);
     cudaEventRecord(e2, s);
-    prof_record(c, PK_FACE_JVP, e0, e1);
     prof_record(c, PK_VOL_JVP, e1, e2);
   }
+  if (pf) prof_record(c, PK_FACE_JVP, e0, e1);
   c.launches += 2;
   return cuda_status(cudaGetLastError());
 }
@@ -178,7 +181,8 @@ int launch_linearize(Ctx& c, const double* q, cudaStream_t s) {
   if (!c.d_lin_face && cudaMalloc(&c.d_lin_face, sizeof(double) * 18 * c.nfacepts) != cudaSuccess)
     return SW_ENOMEM;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (c.prof) {
+  const bool pl = prof_on(c, PK_LIN);
+  if (pl) {
     e0 = prof_event(c);
     e1 = prof_event(c);
     cudaEventRecord(e0, s);
@@ -206,7 +210,7 @@ int launch_linearize(Ctx& c, const double* q, cudaStream_t s) {
     c.launches += 2;
     rc = cuda_status(cudaGetLastError());
   }
-  if (c.prof) {
+  if (pl) {
     cudaEventRecord(e1, s);
     prof_record(c, PK_LIN, e0, e1);
   }

@@ -110,8 +110,12 @@ __device__ __forceinline__ void volume_tangent_body(const TanVolArgs<T>& a, cons
   auto& sF = sm.sF;
   auto& sB = sm.sB;
   auto& sD = sm.sD;
+  // derivative matrix pre-multiplied by -(2/dx) * scale (Eq. 14 and the
+  // augmented operator's dt): each output is then one chain of fused
+  // multiply-adds started from scale * source
+  const double dscale = -dc.two_over_dx * a.ep.scale;
   for (int t = threadIdx.x; t < NS * (NS + 2); t += BLOCK)
-    sD[t / (NS + 2)][t % (NS + 2)] = T(dc.D[t / (NS + 2)][t % (NS + 2)]);
+    sD[t / (NS + 2)][t % (NS + 2)] = T(dscale * dc.D[t / (NS + 2)][t % (NS + 2)]);
   const int le = threadIdx.x / NN, node = threadIdx.x % NN;
   const long long elem = (long long)blk * EPB + le;
   const bool active = threadIdx.x < EPB * NN && elem < a.nelem;
@@ -152,20 +156,22 @@ __device__ __forceinline__ void volume_tangent_body(const TanVolArgs<T>& a, cons
       Da[n] = sD[k1][n];
       Db[n] = sD[k2][n];
     }
-    const T tdx = T(dc.two_over_dx);
+    const T sc = T(a.ep.scale);
 #pragma unroll
     for (int mu = 0; mu < 3; ++mu) {
-      T d1 = Da[0] * sB[le][0][mu][k2] + Da[NS + 1] * sB[le][1][mu][k2];
-      T d2 = Db[0] * sB[le][2][mu][k1] + Db[NS + 1] * sB[le][3][mu][k1];
+      T acc = (mu == 0) ? T(0) : sc * src[mu];
+      acc = fma(Da[0], sB[le][0][mu][k2], acc);
+      acc = fma(Da[NS + 1], sB[le][1][mu][k2], acc);
 #pragma unroll
-      for (int l = 0; l < NS; ++l) {
-        d1 = fma(Da[l + 1], sF[le][0][mu][k2 * NS + l], d1);
-        d2 = fma(Db[l + 1], sF[le][1][mu][l * NS + k1], d2);
-      }
-      res[mu] = double(-tdx * (d1 + d2) + src[mu]);
+      for (int l = 0; l < NS; ++l) acc = fma(Da[l + 1], sF[le][0][mu][k2 * NS + l], acc);
+      acc = fma(Db[0], sB[le][2][mu][k1], acc);
+      acc = fma(Db[NS + 1], sB[le][3][mu][k1], acc);
+#pragma unroll
+      for (int l = 0; l < NS; ++l) acc = fma(Db[l + 1], sF[le][1][mu][l * NS + k1], acc);
+      res[mu] = double(acc);
     }
   }
-  volume_epilogue<BLOCK>(a.ep, active, idx, N, res, a.out, blk, nblk);
+  volume_epilogue<BLOCK, true>(a.ep, active, idx, N, res, a.out, blk, nblk);
 }
 
 }  // namespace swepi

@@ -268,13 +268,7 @@ __device__ void update_task(const EnsDesc& d, EnsDyn& y, unsigned int local, Ens
     const double h1 = VA ? __ldcg(d.H + (long long)(j - 1) * d.ldh + j) : 0.0;
     const double h2 = __ldcg(d.H + (long long)j * d.ldh + j);
     const long long i0 = (long long)local * d.vec_len, i1 = min(i0 + d.vec_len, N);
-    for (long long i = i0 + threadIdx.x; i < i1; i += BLOCK) {
-      double v = __ldcg(z + i);
-      if (VA) v = fma(-h1, VA[i], v);
-      v = fma(-h2, VB[i], v);
-      z[i] = v;
-      acc = fma(v, v, acc);
-    }
+    acc = mgs_update_range(z, VA, VB, h1, h2, i0 + threadIdx.x, i1, BLOCK);
   }
   const double b = block_sum(acc);
   __shared__ bool last;
@@ -319,11 +313,7 @@ __device__ void scale_task(const EnsDesc& d, EnsDyn& y, unsigned int local, EnsC
     const double* VB = d.V + (long long)j * d.ldv;
     const double r = 1.0 / __ldcg(d.H + (long long)(j + 1) * d.ldh + j);
     const long long i0 = (long long)local * d.vec_len, i1 = min(i0 + d.vec_len, N);
-    for (long long i = i0 + threadIdx.x; i < i1; i += BLOCK) {
-      const double v = __ldcg(z + i) * r;
-      z[i] = v;
-      acc = fma(v, VB[i], acc);
-    }
+    acc = scale_dot_range(z, VB, r, i0 + threadIdx.x, i1, BLOCK);
   }
   const double b = block_sum(acc);
   __shared__ bool last;

@@ -148,14 +148,8 @@ __global__ void __launch_bounds__(RED_THREADS) update_norm_kernel(double* __rest
                                                                   int* happy, int happy_value) {
   if (happy[0]) return;
   const double h1 = VA ? *h1p : 0.0, h2 = *h2p;
-  double acc = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double v = z[i];
-    if (VA) v = fma(-h1, VA[i], v);
-    v = fma(-h2, VB[i], v);
-    z[i] = v;
-    acc = fma(v, v, acc);
-  }
+  const double acc = mgs_update_range(z, VA, VB, h1, h2, (long long)blockIdx.x * blockDim.x + threadIdx.x, n,
+                                      (long long)gridDim.x * blockDim.x);
   double b = block_sum(acc);
   __shared__ bool last;
   if (threadIdx.x == 0) {
@@ -187,12 +181,8 @@ __global__ void __launch_bounds__(RED_THREADS) scale_dot_kernel(double* __restri
                                                                 unsigned int* ticket, double* c_out, const int* happy) {
   if (happy[0]) return;
   const double r = 1.0 / *hsub;
-  double acc = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const double v = z[i] * r;
-    z[i] = v;
-    acc = fma(v, VB[i], acc);
-  }
+  const double acc = scale_dot_range(z, VB, r, (long long)blockIdx.x * blockDim.x + threadIdx.x, n,
+                                     (long long)gridDim.x * blockDim.x);
   double b = block_sum(acc);
   __shared__ bool last;
   if (threadIdx.x == 0) {
@@ -303,17 +293,37 @@ int launch_scale_inv(Ctx& c, double* y, const double* x, const double* s_dev, lo
 
 int launch_update_norm(Ctx& c, double* z, const double* VA, const double* VB, const double* h1, const double* h2,
                        long long N, double* hsub, double tol, int happy_value, cudaStream_t s) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (prof_on(c, PK_ORTH)) {
+    e0 = prof_event(c);
+    e1 = prof_event(c);
+    cudaEventRecord(e0, s);
+  }
   update_norm_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(z, VA, VB, h1, h2, N, c.d_partials,
                                                        (unsigned int*)(c.d_flags + 8), hsub, tol, c.d_flags,
                                                        happy_value);
+  if (prof_on(c, PK_ORTH)) {
+    cudaEventRecord(e1, s);
+    prof_record(c, PK_ORTH, e0, e1);
+  }
   c.launches++;
   return cuda_status(cudaGetLastError());
 }
 
 int launch_scale_dot(Ctx& c, double* z, const double* VB, const double* hsub, long long N, double* c_out,
                      cudaStream_t s) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (prof_on(c, PK_ORTH)) {
+    e0 = prof_event(c);
+    e1 = prof_event(c);
+    cudaEventRecord(e0, s);
+  }
   scale_dot_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(z, VB, hsub, N, c.d_partials, (unsigned int*)(c.d_flags + 8),
                                                      c_out, c.d_flags);
+  if (prof_on(c, PK_ORTH)) {
+    cudaEventRecord(e1, s);
+    prof_record(c, PK_ORTH, e0, e1);
+  }
   c.launches++;
   return cuda_status(cudaGetLastError());
 }
@@ -346,13 +356,13 @@ int launch_combine(Ctx& c, int j, long long n, cudaStream_t s) {
 int launch_expm_prep(Ctx& c, int j, double tau, double tau_happy, cudaStream_t s) {
   if (j + 1 > MAX_EXPM) return SW_EINVAL;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (c.prof) {
+  if (prof_on(c, PK_EXPM)) {
     e0 = prof_event(c);
     e1 = prof_event(c);
     cudaEventRecord(e0, s);
   }
   expm_prep_kernel<<<1, 256, 0, s>>>(c.d_H, c.ldh, j, tau, tau_happy, c.d_flags, c.d_expm_ws, c.d_scal + 8);
-  if (c.prof) {
+  if (prof_on(c, PK_EXPM)) {
     cudaEventRecord(e1, s);
     prof_record(c, PK_EXPM, e0, e1);
   }
@@ -367,7 +377,7 @@ int launch_expm_eval(Ctx& c, int N, double norm1, int* squarings, cudaStream_t s
   if (squarings) *squarings = sq;
   const long long NN = (long long)N * N;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (c.prof) {
+  if (prof_on(c, PK_EXPM)) {
     e0 = prof_event(c);
     e1 = prof_event(c);
     cudaEventRecord(e0, s);
@@ -383,7 +393,7 @@ int launch_expm_eval(Ctx& c, int N, double norm1, int* squarings, cudaStream_t s
   }
   expm_finish_kernel<<<(unsigned)((NN + 255) / 256), 256, 0, s>>>(c.d_expm_ws + expm_result_slot(sq) * NN, N, c.d_F,
                                                                  c.ldh, c.d_scal + 8);
-  if (c.prof) {
+  if (prof_on(c, PK_EXPM)) {
     cudaEventRecord(e1, s);
     prof_record(c, PK_EXPM, e0, e1);
   }

@@ -31,6 +31,67 @@ __device__ __forceinline__ double block_sum(double v) {
   return r;
 }
 
+// ------------------------------------------------------------ orthogonalisation passes
+// The two vector passes of the window-2 modified Gram-Schmidt step over the
+// indices i0, i0 + stride, ... < i1 of one thread, four elements in flight
+// (z was written by another kernel or CTA: read through L2).
+//   z -= h1 VA + h2 VB (VA may be null); returns the thread's sum of z_i^2
+__device__ __forceinline__ double mgs_update_range(double* __restrict__ z, const double* __restrict__ VA,
+                                                   const double* __restrict__ VB, double h1, double h2, long long i,
+                                                   long long i1, long long stride) {
+  double acc = 0.0;
+  for (; i + 3 * stride < i1; i += 4 * stride) {
+    double v[4], b[4], a[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[k] = __ldcg(z + i + k * stride);
+      b[k] = VB[i + k * stride];
+      if (VA) a[k] = VA[i + k * stride];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (VA) v[k] = fma(-h1, a[k], v[k]);
+      v[k] = fma(-h2, b[k], v[k]);
+      z[i + k * stride] = v[k];
+      acc = fma(v[k], v[k], acc);
+    }
+  }
+  for (; i < i1; i += stride) {
+    double v = __ldcg(z + i);
+    if (VA) v = fma(-h1, VA[i], v);
+    v = fma(-h2, VB[i], v);
+    z[i] = v;
+    acc = fma(v, v, acc);
+  }
+  return acc;
+}
+
+//   z *= r; returns the thread's sum of z_i VB_i
+__device__ __forceinline__ double scale_dot_range(double* __restrict__ z, const double* __restrict__ VB, double r,
+                                                  long long i, long long i1, long long stride) {
+  double acc = 0.0;
+  for (; i + 3 * stride < i1; i += 4 * stride) {
+    double v[4], b[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[k] = __ldcg(z + i + k * stride);
+      b[k] = VB[i + k * stride];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[k] *= r;
+      z[i + k * stride] = v[k];
+      acc = fma(v[k], b[k], acc);
+    }
+  }
+  for (; i < i1; i += stride) {
+    const double v = __ldcg(z + i) * r;
+    z[i] = v;
+    acc = fma(v, VB[i], acc);
+  }
+  return acc;
+}
+
 // ------------------------------------------------------------ expm
 // F = exp(A), A = t [[H_j, e_1], [0, 0]] (order N = j + 1 <= MAX_EXPM): scaling
 // and squaring (Moler and Van Loan, "Nineteen dubious ways to compute the

@@ -135,12 +135,12 @@ struct Ctx {
   void* d_diag_flags = nullptr;
   std::vector<double> hB_h;        // nodal bottom (host copy)
   // event profiling (sw_profile)
-  bool prof = false;
+  unsigned prof = 0;               // bit k: time kernels of kind k (ProfKind)
   struct ProfRec { int kind; cudaEvent_t a, b; };
   std::vector<ProfRec> prof_pending;
   std::vector<cudaEvent_t> prof_pool;
-  long long prof_count[6] = {};
-  double prof_ms[6] = {};
+  long long prof_count[SW_PROF_KINDS] = {};
+  double prof_ms[SW_PROF_KINDS] = {};
 };
 
 // learned Krylov control (mlp.cu)
@@ -159,7 +159,10 @@ int mlp_predict_host(Mlp* m, const float* feat, float* out2, cudaStream_t s);
 cudaEvent_t prof_event(Ctx& c);
 void prof_record(Ctx& c, int kind, cudaEvent_t a, cudaEvent_t b);
 void prof_drain(Ctx& c);
-enum ProfKind { PK_FACE_JVP = 0, PK_VOL_JVP = 1, PK_FACE_RHS = 2, PK_VOL_RHS = 3, PK_EXPM = 4, PK_LIN = 5 };
+enum ProfKind {
+  PK_FACE_JVP = 0, PK_VOL_JVP = 1, PK_FACE_RHS = 2, PK_VOL_RHS = 3, PK_EXPM = 4, PK_LIN = 5, PK_ORTH = 6
+};
+inline bool prof_on(const Ctx& c, int kind) { return (c.prof >> kind) & 1u; }
 
 // ---- multistep EPI driver pieces (capi.cu), shared with the ensemble driver
 constexpr int EPI_STARTUP_SUBSTEPS = 8;   // EPI2 substeps of a start-up step (Sec. 4)
@@ -220,7 +223,7 @@ int launch_jvp_fb(Ctx& c, const double* q, const double* v, double eps, double* 
                   cudaStream_t s);
 
 // ---- Krylov kernels (krylov.cu)
-constexpr int RED_BLOCKS = 456;   // 3 x 152 SMs
+constexpr int RED_BLOCKS = 608;   // 4 x 152 SMs
 int launch_dot(Ctx& c, const double* x, const double* y, long long n, double* dst, const int* skip,
                cudaStream_t s);
 int launch_norm2(Ctx& c, const double* x, long long n, double* dst, double tol, int* happy,

@@ -41,9 +41,9 @@ class sw_kiops_opts(ctypes.Structure):
 
 
 class sw_profile_stats(ctypes.Structure):
-    _fields_ = [("count", ctypes.c_longlong * 6), ("ms", ctypes.c_double * 6)]
+    _fields_ = [("count", ctypes.c_longlong * 7), ("ms", ctypes.c_double * 7)]
 
-    KINDS = ("face_jvp", "volume_jvp", "face_rhs", "volume_rhs", "expm", "linearize")
+    KINDS = ("face_jvp", "volume_jvp", "face_rhs", "volume_rhs", "expm", "linearize", "orthogonalisation")
 
     def as_dict(self):
         return {k: {"count": int(self.count[i]), "ms": float(self.ms[i])} for i, k in enumerate(self.KINDS)}
@@ -109,6 +109,7 @@ def lib():
     L.sw_kernel_launches.argtypes = [vp]
     L.sw_kernel_launches.restype = ll
     L.sw_profile.argtypes = [vp, ip]
+    L.sw_profile_kinds.argtypes = [vp, ctypes.c_uint]
     L.sw_profile_read.argtypes = [vp, ctypes.POINTER(sw_profile_stats)]
     L.sw_fp64_fma_peak.argtypes = [dp]
     fp = ctypes.POINTER(ctypes.c_float)
@@ -145,7 +146,7 @@ def lib():
 EXPORTED = ["sw_init", "sw_free", "sw_num_unknowns", "sw_grid_info", "sw_node_xyz", "sw_state_from_fields",
             "sw_set_bottom", "sw_rhs", "sw_jvp", "sw_jvp_static_scratch", "sw_linearize", "sw_jvp_linearized",
             "sw_set_jvp_mode", "sw_kiops_phi", "sw_epi_step", "sw_epi_set_history",
-            "sw_epi_reset", "sw_kernel_launches", "sw_profile", "sw_profile_read", "sw_fp64_fma_peak",
+            "sw_epi_reset", "sw_kernel_launches", "sw_profile", "sw_profile_kinds", "sw_profile_read", "sw_fp64_fma_peak",
             "sw_status_str", "sw_mlp_create", "sw_mlp_free", "sw_mlp_set_params", "sw_mlp_get_params",
             "sw_mlp_forward", "sw_mlp_gradient", "sw_mlp_train", "sw_set_controller", "sw_kiops_log",
             "sw_kiops_log_clear", "sw_diagnostics", "sw_error_norms", "sw_ens_create", "sw_ens_free",
@@ -296,6 +297,10 @@ def sw_kernel_launches(ctx):
 
 def sw_profile(ctx, enable=True):
     _check("sw_profile", lib().sw_profile(ctx, 1 if enable else 0))
+
+
+def sw_profile_kinds(ctx, mask):
+    _check("sw_profile_kinds", lib().sw_profile_kinds(ctx, int(mask)))
 
 
 def sw_profile_read(ctx):
@@ -592,6 +597,13 @@ class SWContext:
 
     def profile(self, enable=True):
         sw_profile(self.handle, enable)
+
+    def profile_kinds(self, *kinds):
+        """Time only the named kernel families (sw_profile_stats.KINDS)."""
+        mask = 0
+        for k in kinds:
+            mask |= 1 << sw_profile_stats.KINDS.index(k)
+        sw_profile_kinds(self.handle, mask)
 
     def profile_read(self):
         return sw_profile_read(self.handle)
