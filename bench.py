@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
-    ap.add_argument("--control", default="learned", choices=["learned", "plain"])
+    ap.add_argument("--control", default="plain", choices=["learned", "plain"])
     ap.add_argument("--jvp-mode", type=int, default=1, choices=[0, 1],
                     help="0: full complex-step evaluation per JVP, 1: split (default)")
     return ap.parse_args()
@@ -483,10 +483,10 @@ def main():
                "forms": {"timed": ("learned control + FP64 split complex-step JVP" if ctl is not None
                                    else "plain control + FP64 split complex-step JVP")}}
         if not args.no_forms:
-            if ctl is not None:
-                from paper_2101_05617_gb300 import learned
-                out["forms"]["learned_vs_plain_same_start"] = learned.evaluate(ctl, args.workload, args.steps,
-                                                                               seed=args.seed + 1)
+            from paper_2101_05617_gb300 import learned
+            lc = ctl if ctl is not None else learned.Controller.load()
+            out["forms"]["learned_vs_plain_same_start"] = learned.evaluate(lc, args.workload, args.steps,
+                                                                           seed=args.seed + 1)
             out["forms"]["complex64_bulk_ne30_p5"] = fp32_form_comparison(args, dev)
             if world == 1 and not args.no_ensemble:
                 out["forms"]["ensemble_96"] = ensemble_form(args, dev, peak)
