@@ -48,9 +48,9 @@ def flops_per_jvp(ne, ns, p=4, dots=True):
 
 # DRAM bytes (read + write) of one launch of the dominant kernel,
 # volume_tangent_kernel<double, 6>, on the 6 x 60 x 60, p = 5 workload inside
-# the phi-function solver (p = 4, with dots): one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum = 136.94 MB + 10.42 MB).
-TRAFFIC_BYTES = {"ne60_p5": 147.36e6}
+# the phi-function solver (p = 4, with dots): mean of two launches of one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum = 136.96 MB + 8.35 MB).
+TRAFFIC_BYTES = {"ne60_p5": 145.31e6}
 
 
 def parse():
