@@ -181,6 +181,31 @@ def oracle_sample(wl, seed, krylov_per_step, P, budget_s=15.0):
             "jvp_dof_per_s": wl.n_unknowns / t_one}
 
 
+def hbm_peak_gbs():
+    """The measured HBM copy bandwidth of the GB300s (GB/s), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def ortho_roofline(prof_all, wl):
+    """The two vector passes of the window-2 orthogonalisation against HBM:
+    algorithmic bytes per Krylov iteration = (read z, V_{j-1}, V_j, write z) +
+    (read z, V_j, write z) = 56 B per unknown of the augmented vector."""
+    o = prof_all["orthogonalisation"]
+    if not o["count"]:
+        return None
+    pairs = o["count"] / 2.0
+    t = o["ms"] * 1e-3 / pairs
+    nbytes = 56.0 * (wl.n_unknowns + 4)
+    peak, src = hbm_peak_gbs()
+    return {"bound": "hbm", "bytes_per_iteration": nbytes, "avg_ms_per_iteration": t * 1e3,
+            "achieved_gbs": nbytes / t / 1e9, "peak_gbs": peak, "frac": nbytes / t / 1e9 / peak,
+            "peak_source": src}
+
+
 def fp32_form_comparison(args, dev):
     """The complex64-bulk form against the FP64 path on its own workload
     (6 x 30 x 30, p = 5, EPI5, dt = 1800 s): steps/s of both, the FP32-vs-FP64
@@ -456,7 +481,8 @@ def main():
                                    "face": {"flops": ff, "avg_ms": t_face * 1e3, "launches": fj["count"],
                                             "tflops": ff / t_face / 1e12 if t_face else None},
                                    "expm": {"avg_ms": prof_all["expm"]["ms"] / max(1, prof_all["expm"]["count"]),
-                                            "launches": prof_all["expm"]["count"]}},
+                                            "launches": prof_all["expm"]["count"]},
+                                   "orthogonalisation": ortho_roofline(prof_all, wl)},
                     "share_of_step": {k: prof_all[k]["ms"] / breakdown_ms
                                       for k in ("volume_jvp", "face_jvp", "orthogonalisation", "expm", "linearize")},
                     "share_note": "the last warm-up EPI step of the end-to-end replay with every kernel family "
