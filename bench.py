@@ -263,33 +263,32 @@ def ortho_roofline(prof_all, wl):
             "peak_source": src}
 
 
-def fp32_form_comparison(args, dev):
-    """The complex64-bulk form against the FP64 path on its own workload
-    (6 x 30 x 30, p = 5, EPI5, dt = 1800 s): steps/s of both, the FP32-vs-FP64
-    state difference after the run and the EPI time-discretisation error (FP64
-    at dt against dt/4).  On the n_e = 60 grid the form is not used: the
-    incomplete orthogonalisation amplifies its FP32 noise beyond the step's
-    accuracy (DESIGN.md)."""
+def fp32_form_comparison(args, dev, workload="ne30_p5", variants=(("fp64", 1, 2), ("complex64_bulk", 2, 2))):
+    """The complex64-bulk form against the FP64 path: steps/s of each variant
+    (name, JVP mode, orthogonalisation window) from the same start, each
+    variant's state difference to the first (the FP64 path, window 2) after the
+    run, and the EPI time-discretisation error (FP64 at dt against dt/4)."""
     import torch
 
     from paper_2101_05617_gb300 import swepi, synth
-    wl = synth.WORKLOADS["ne30_p5"]
+    wl = synth.WORKLOADS[workload]
     f = synth.make_fields(wl, args.seed)
     res = {}
     states = {}
-    for name, mode, dt, mult in (("fp64", 1, wl.dt, 1), ("complex64_bulk", 2, wl.dt, 1), ("fp64_dt4", 1, wl.dt / 4, 4)):
+    runs = [(name, mode, iop, wl.dt, 1) for name, mode, iop in variants] + [("fp64_dt4", 1, 2, wl.dt / 4, 4)]
+    for name, mode, iop, dt, mult in runs:
         ctx = swepi.SWContext(wl.ne, wl.p, f.rotation)
         h, hB, V = f.evaluate(ctx.node_xyz())
         q = torch.tensor(ctx.state_from_fields(h, hB, V), device=dev)
         ctx.set_jvp_mode(mode)
         for _ in range(args.warmup * mult):
-            ctx.epi_step(wl.order, dt, q, tol=wl.tol)
+            ctx.epi_step(wl.order, dt, q, tol=wl.tol, iop=iop)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(args.steps * mult):
-            ctx.epi_step(wl.order, dt, q, tol=wl.tol)
+            ctx.epi_step(wl.order, dt, q, tol=wl.tol, iop=iop)
         e1.record()
         torch.cuda.synchronize()
         res[name] = args.steps * mult / (e0.elapsed_time(e1) * 1e-3)
@@ -298,12 +297,17 @@ def fp32_form_comparison(args, dev):
 
     def rel(a, b):
         return [float(torch.linalg.norm(a[k] - b[k]) / torch.linalg.norm(b[k])) for k in range(3)]
-    return {"workload": "ne30_p5: 6x30x30 elements, p=5, EPI5, dt=1800 s, KIOPS tol 1e-10",
-            "fp64_steps_per_s": res["fp64"], "complex64_bulk_steps_per_s": res["complex64_bulk"],
-            "speedup": res["complex64_bulk"] / res["fp64"],
-            "err_vs_fp64_rel_l2": rel(states["complex64_bulk"], states["fp64"]),
-            "time_discretisation_err_rel_l2": rel(states["fp64"], states["fp64_dt4"]),
-            "steps": args.warmup + args.steps}
+    base = variants[0][0]
+    out = {"workload": f"{workload}: 6x{wl.ne}x{wl.ne} elements, p={wl.p}, EPI{wl.order}, dt={wl.dt:g} s, "
+                       f"KIOPS tol {wl.tol:g}, plain rule",
+           "steps": args.warmup + args.steps,
+           "time_discretisation_err_rel_l2": rel(states[base], states["fp64_dt4"])}
+    for name, mode, iop in variants:
+        out[name] = {"jvp": "FP64" if mode == 1 else "complex64 bulk (FP32 imaginary half)", "window": iop,
+                     "steps_per_s": res[name], "speedup_vs_" + base: res[name] / res[base]}
+        if name != base:
+            out[name]["err_vs_" + base + "_rel_l2"] = rel(states[name], states[base])
+    return out
 
 
 # Krylov iterations per EPI5 step of the GPU path on the default workload and
@@ -572,6 +576,10 @@ def main():
             out["forms"]["learned_vs_plain_same_start"] = learned.evaluate(lc, args.workload, args.steps,
                                                                            seed=args.seed + 1)
             out["forms"]["complex64_bulk_ne30_p5"] = fp32_form_comparison(args, dev)
+            if args.workload == "ne60_p5":
+                # on this grid the form needs the orthogonalisation window of three
+                out["forms"]["complex64_bulk_ne60_p5"] = fp32_form_comparison(
+                    args, dev, "ne60_p5", (("fp64", 1, 2), ("fp64_window3", 1, 3), ("complex64_bulk_window3", 2, 3)))
             if world == 1 and not args.no_ensemble:
                 out["forms"]["ensemble_96"] = ensemble_form(args, dev, peak)
         if world == 1 and not args.no_cpu_baseline:

@@ -245,7 +245,7 @@ void sw_free(sw_ctx_t c) {
   if (!c) return;
   double* ptrs[] = {c->d_node_coef, c->d_face_coef, c->d_fb, c->d_V, c->d_X, c->d_H, c->d_F, c->d_expm_ws,
                     c->d_partials, c->d_scal, c->d_Fn, c->d_tmp, c->d_tmp2, c->d_lin_node, c->d_lin_face,
-                    c->d_vpart, c->d_cdot, c->d_diag_tab, c->d_diag_part, c->d_diag_out};
+                    c->d_vpart, c->d_cdot, c->d_cdot2, c->d_diag_tab, c->d_diag_part, c->d_diag_out};
   if (c->d_diag_flags) cudaFree(c->d_diag_flags);
   if (c->d_lin_node32) cudaFree(c->d_lin_node32);
   if (c->d_lin_face32) cudaFree(c->d_lin_face32);

@@ -94,7 +94,7 @@ struct VolArgs {
   AugEpilogue ep;
 };
 
-template <typename T, int NS>
+template <typename T, int NS, bool W3 = false>
 __global__ void __launch_bounds__(VolShape<NS>::THREADS) volume_kernel(VolArgs a, DfrConst dc) {
   constexpr int EPB = VolShape<NS>::EPB;
   constexpr int NN = NS * NS;
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(VolShape<NS>::THREADS) volume_kernel(VolArgs a
 #pragma unroll
     for (int mu = 0; mu < 3; ++mu) res[mu] *= sc;
   }
-  volume_epilogue<VolShape<NS>::THREADS>(a.ep, active, idx, a.nodes, res, a.out, blockIdx.x, gridDim.x);
+  volume_epilogue<VolShape<NS>::THREADS, false, W3>(a.ep, active, idx, a.nodes, res, a.out, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -198,7 +198,10 @@ static int launch_ns(Ctx& c, const double* q, const double* v, double eps, doubl
   }
   VolArgs va{q, v, eps, c.nodes, c.nelem, c.d_node_coef, c.d_fb, out, ep};
   long long vblocks = (c.nelem + VolShape<NS>::EPB - 1) / VolShape<NS>::EPB;
-  volume_kernel<T, NS><<<(unsigned)vblocks, VolShape<NS>::THREADS, 0, s>>>(va, c.dc);
+  if (ep.dotC)
+    volume_kernel<T, NS, true><<<(unsigned)vblocks, VolShape<NS>::THREADS, 0, s>>>(va, c.dc);
+  else
+    volume_kernel<T, NS, false><<<(unsigned)vblocks, VolShape<NS>::THREADS, 0, s>>>(va, c.dc);
   if (pv) {
     e2 = prof_event(c);
     cudaEventRecord(e2, s);

@@ -138,9 +138,11 @@ struct VolShape {
 // this block's index and the number of blocks working on the same vector):
 // out = scale * res + nu * sum_l y_l b_{p-l} (the augmented operator of the
 // phi-function solver), the shift of the augmented tail, and -- when dotB is
-// set -- the window dot products of the incomplete orthogonalisation.
-// SCALED: the caller has already multiplied res by scale.
-template <int THREADS, bool SCALED = false>
+// set -- the window dot products of the incomplete orthogonalisation (two or
+// three vectors; see AugEpilogue).
+// SCALED: the caller has already multiplied res by scale.  W3: compiled for
+// the window of three (dotC may be set); W3 = false drops that code.
+template <int THREADS, bool SCALED = false, bool W3 = false>
 __device__ __forceinline__ void volume_epilogue(const AugEpilogue& ep, bool active, long long idx, long long N,
                                                 const double res[3], double* __restrict__ out, unsigned int blk,
                                                 unsigned int nblk) {
@@ -151,7 +153,7 @@ __device__ __forceinline__ void volume_epilogue(const AugEpilogue& ep, bool acti
     coef[l] = (l < ep.p && ep.b[l]) ? ep.nu * ep.tail_in[l] : 0.0;
   }
   __syncthreads();
-  double da = 0.0, db = 0.0;
+  double da = 0.0, db = 0.0, dcc = 0.0;
   if (active) {
 #pragma unroll
     for (int mu = 0; mu < 3; ++mu) {
@@ -163,6 +165,7 @@ __device__ __forceinline__ void volume_epilogue(const AugEpilogue& ep, bool acti
       if (ep.dotB) {
         db = fma(o, ep.dotB[idx + mu * N], db);
         if (ep.dotA) da = fma(o, ep.dotA[idx + mu * N], da);
+        if (W3 && ep.dotC) dcc = fma(o, ep.dotC[idx + mu * N], dcc);
       }
     }
   }
@@ -174,24 +177,33 @@ __device__ __forceinline__ void volume_epilogue(const AugEpilogue& ep, bool acti
       const double zt = (l + 1 < ep.p) ? ep.tail_in[l + 1] : 0.0;
       db = fma(zt, ep.dotB[ep.n + l], db);
       if (ep.dotA) da = fma(zt, ep.dotA[ep.n + l], da);
+      if (W3 && ep.dotC) dcc = fma(zt, ep.dotC[ep.n + l], dcc);
     }
   }
-  __shared__ double sa[THREADS], sb[THREADS];
+  __shared__ double sa[THREADS], sb[THREADS], sc[W3 ? THREADS : 1];
   __shared__ bool last;
+  const bool three = W3 && ep.dotC != nullptr;   // uniform over the grid
   sa[threadIdx.x] = da;
   sb[threadIdx.x] = db;
+  if (three) sc[threadIdx.x] = dcc;
   __syncthreads();
   if (threadIdx.x < 32) {
-    double a = 0.0, b = 0.0;
-    for (int k = threadIdx.x; k < THREADS; k += 32) { a += sa[k]; b += sb[k]; }
+    double a = 0.0, b = 0.0, c3 = 0.0;
+    for (int k = threadIdx.x; k < THREADS; k += 32) {
+      a += sa[k];
+      b += sb[k];
+      if (three) c3 += sc[k];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       a += __shfl_down_sync(0xffffffffu, a, o);
       b += __shfl_down_sync(0xffffffffu, b, o);
+      if (three) c3 += __shfl_down_sync(0xffffffffu, c3, o);
     }
     if (threadIdx.x == 0) {
-      ep.dpart[2 * blk] = a;
-      ep.dpart[2 * blk + 1] = b;
+      ep.dpart[3 * blk] = a;
+      ep.dpart[3 * blk + 1] = b;
+      ep.dpart[3 * blk + 2] = c3;
       __threadfence();
       const unsigned int t = atomicAdd(ep.dticket, 1u);
       last = (t == nblk - 1);
@@ -200,25 +212,40 @@ __device__ __forceinline__ void volume_epilogue(const AugEpilogue& ep, bool acti
   __syncthreads();
   if (!last) return;
   __threadfence();
-  double a = 0.0, b = 0.0;
+  double a = 0.0, b = 0.0, c3 = 0.0;
   for (int k = threadIdx.x; k < (int)nblk; k += THREADS) {
-    a += __ldcg(ep.dpart + 2 * k);
-    b += __ldcg(ep.dpart + 2 * k + 1);
+    a += __ldcg(ep.dpart + 3 * k);
+    b += __ldcg(ep.dpart + 3 * k + 1);
+    if (three) c3 += __ldcg(ep.dpart + 3 * k + 2);
   }
   sa[threadIdx.x] = a;
   sb[threadIdx.x] = b;
+  if (three) sc[threadIdx.x] = c3;
   __syncthreads();
   if (threadIdx.x < 32) {
     a = 0.0;
     b = 0.0;
-    for (int k = threadIdx.x; k < THREADS; k += 32) { a += sa[k]; b += sb[k]; }
+    c3 = 0.0;
+    for (int k = threadIdx.x; k < THREADS; k += 32) {
+      a += sa[k];
+      b += sb[k];
+      if (three) c3 += sc[k];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       a += __shfl_down_sync(0xffffffffu, a, o);
       b += __shfl_down_sync(0xffffffffu, b, o);
+      if (three) c3 += __shfl_down_sync(0xffffffffu, c3, o);
     }
     if (threadIdx.x == 0) {
-      if (ep.dotA) {
+      // modified Gram-Schmidt coefficients, oldest vector first
+      if (three) {
+        const double h0 = c3;                               // V_{j-2} . z
+        const double h1 = a - h0 * (*ep.cprevAC);            // V_{j-1} . (z - h0 V_{j-2})
+        *ep.h0_out = h0;
+        *ep.h1_out = h1;
+        *ep.h2_out = b - h0 * (*ep.cprevC) - h1 * (*ep.cprev);
+      } else if (ep.dotA) {
         *ep.h1_out = a;
         *ep.h2_out = b - a * (*ep.cprev);   // V_j . (z - h1 V_{j-1})
       } else {

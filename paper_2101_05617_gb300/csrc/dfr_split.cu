@@ -116,11 +116,12 @@ __global__ void __launch_bounds__(128) face_tangent_kernel(TanFaceArgs<T> a, Dfr
   face_tangent_body<T, NS>(a, dc, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-template <typename T, int NS>
+// W3: with the orthogonalisation window of three in the epilogue
+template <typename T, int NS, bool W3>
 __global__ void __launch_bounds__(VolShape<NS>::THREADS) volume_tangent_kernel(TanVolArgs<T> a, DfrConst dc) {
   if (a.ep.skip && *a.ep.skip) return;
   __shared__ VolSmem<T, NS, VolShape<NS>::EPB> sm;
-  volume_tangent_body<T, NS, VolShape<NS>::EPB>(a, dc, blockIdx.x, gridDim.x, sm);
+  volume_tangent_body<T, NS, VolShape<NS>::EPB, VolShape<NS>::THREADS, W3>(a, dc, blockIdx.x, gridDim.x, sm);
 }
 
 __global__ void to_float_kernel(const double* __restrict__ src, float* __restrict__ dst, long long n) {
@@ -155,7 +156,10 @@ int tangent_ns(Ctx& c, const double* v, double* out, const AugEpilogue& ep, cons
   }
   TanVolArgs<T> va{v, c.nodes, c.nelem, ln, fb, out, ep};
   const long long vblocks = (c.nelem + VolShape<NS>::EPB - 1) / VolShape<NS>::EPB;
-  volume_tangent_kernel<T, NS><<<(unsigned)vblocks, VolShape<NS>::THREADS, 0, s>>>(va, c.dc);
+  if (ep.dotC)
+    volume_tangent_kernel<T, NS, true><<<(unsigned)vblocks, VolShape<NS>::THREADS, 0, s>>>(va, c.dc);
+  else
+    volume_tangent_kernel<T, NS, false><<<(unsigned)vblocks, VolShape<NS>::THREADS, 0, s>>>(va, c.dc);
   if (pv) {
     e2 = prof_event(c);
     cudaEventRecord(e2, s);

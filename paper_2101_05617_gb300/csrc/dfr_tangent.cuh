@@ -102,7 +102,7 @@ struct VolSmem {
 // imaginary half of EPB elements per block: block blk of nblk working on one
 // grid; the block has BLOCK >= EPB * NS^2 threads (one per solution point, the
 // rest idle), all of which call this function
-template <typename T, int NS, int EPB, int BLOCK = EPB * NS * NS>
+template <typename T, int NS, int EPB, int BLOCK = EPB * NS * NS, bool W3 = false>
 __device__ __forceinline__ void volume_tangent_body(const TanVolArgs<T>& a, const DfrConst& dc, unsigned int blk,
                                                     unsigned int nblk, VolSmem<T, NS, EPB>& sm) {
   constexpr int NN = NS * NS;
@@ -171,7 +171,7 @@ __device__ __forceinline__ void volume_tangent_body(const TanVolArgs<T>& a, cons
       res[mu] = double(acc);
     }
   }
-  volume_epilogue<BLOCK, true>(a.ep, active, idx, N, res, a.out, blk, nblk);
+  volume_epilogue<BLOCK, true, W3>(a.ep, active, idx, N, res, a.out, blk, nblk);
 }
 
 }  // namespace swepi

@@ -10,7 +10,8 @@
 //    and the start vector [b_0; 0, .., 0, mu];
 //  * each substep builds a fresh basis from the current augmented vector; the
 //    new vector is orthogonalised against the last `iop` basis vectors
-//    (modified Gram-Schmidt, oldest first); ||z|| < tol is a happy breakdown,
+//    (modified Gram-Schmidt, oldest first; windows of two and three fused into
+//    the JVP epilogue and two vector passes); ||z|| < tol is a happy breakdown,
 //    after which the projection is exact and the rest of the interval is taken;
 //  * err = beta h_{j+1,j} |F[j-1, j]| with F = exp(tau [[H_j, e_1], [0, 0]])
 //    (device exponential, krylov.cu; the host reads the order and 1-norm of
@@ -69,10 +70,12 @@ int ensure_krylov(Ctx& c, int m_max) {
   if (cudaMalloc(&c.d_H, sizeof(double) * c.ldh * c.ldh) != cudaSuccess) return SW_ENOMEM;
   if (cudaMalloc(&c.d_F, sizeof(double) * c.ldh * c.ldh) != cudaSuccess) return SW_ENOMEM;
   if (cudaMalloc(&c.d_expm_ws, sizeof(double) * 8 * 160 * 160) != cudaSuccess) return SW_ENOMEM;
-  if (!c.d_partials && cudaMalloc(&c.d_partials, sizeof(double) * RED_BLOCKS) != cudaSuccess) return SW_ENOMEM;
-  if (!c.d_vpart && cudaMalloc(&c.d_vpart, sizeof(double) * 2 * (c.nelem + 1)) != cudaSuccess) return SW_ENOMEM;
+  if (!c.d_partials && cudaMalloc(&c.d_partials, sizeof(double) * 2 * RED_BLOCKS) != cudaSuccess) return SW_ENOMEM;
+  if (!c.d_vpart && cudaMalloc(&c.d_vpart, sizeof(double) * 3 * (c.nelem + 1)) != cudaSuccess) return SW_ENOMEM;
   free_ptr(c.d_cdot);
   if (cudaMalloc(&c.d_cdot, sizeof(double) * c.ldh) != cudaSuccess) return SW_ENOMEM;
+  free_ptr(c.d_cdot2);
+  if (cudaMalloc(&c.d_cdot2, sizeof(double) * c.ldh) != cudaSuccess) return SW_ENOMEM;
   if (!c.d_scal && cudaMalloc(&c.d_scal, sizeof(double) * 64) != cudaSuccess) return SW_ENOMEM;
   if (!c.d_flags) {
     if (cudaMalloc(&c.d_flags, sizeof(int) * 16) != cudaSuccess) return SW_ENOMEM;
@@ -172,13 +175,18 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
       double* Vn = V + (it + 1) * ldv;
       ep.tail_in = Vi + n;
       ep.tail_out = Vn + n;
-      if (o.iop == 2) {
+      if (o.iop == 2 || o.iop == 3) {
         // orthogonalisation fused into the JVP epilogue (dots) and two passes
         double* hB = c.d_H + (long long)it * c.ldh + it;
         double* hA = (it >= 1) ? c.d_H + (long long)(it - 1) * c.ldh + it : nullptr;
+        double* hC = (o.iop == 3 && it >= 2) ? c.d_H + (long long)(it - 2) * c.ldh + it : nullptr;
         ep.dotA = (it >= 1) ? V + (it - 1) * ldv : nullptr;
         ep.dotB = Vi;
+        ep.dotC = hC ? V + (it - 2) * ldv : nullptr;
         ep.cprev = c.d_cdot + it;
+        ep.cprevC = c.d_cdot2 + it;
+        ep.cprevAC = (it >= 1) ? c.d_cdot + it - 1 : nullptr;
+        ep.h0_out = hC;
         ep.h1_out = hA;
         ep.h2_out = hB;
         ep.dpart = c.d_vpart;
@@ -187,11 +195,13 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
         rc = use_lin ? launch_jvp_lin(c, Vi, Vn, ep, s, c.jvp_mode == 2) : launch_jvp(c, q_lin, Vi, kEpsJvp, Vn, ep, s);
         if (rc) return rc;
         double* hs = c.d_H + (long long)(it + 1) * c.ldh + it;
-        if ((rc = launch_update_norm(c, Vn, ep.dotA, Vi, hA, hB, N, hs, o.tol, it + 1, s))) return rc;
-        if ((rc = launch_scale_dot(c, Vn, Vi, hs, N, c.d_cdot + it + 1, s))) return rc;
+        if ((rc = launch_update_norm(c, Vn, ep.dotA, Vi, hA, hB, N, hs, o.tol, it + 1, s, ep.dotC, hC))) return rc;
+        // V_{j+1} . V_{j-1} is needed by the window of three two iterations later
+        const double* Vprev = (o.iop == 3 && it >= 1) ? V + (it - 1) * ldv : nullptr;
+        if ((rc = launch_scale_dot(c, Vn, Vi, hs, N, c.d_cdot + it + 1, s, Vprev, c.d_cdot2 + it + 1))) return rc;
         continue;
       }
-      ep.dotA = ep.dotB = nullptr;
+      ep.dotA = ep.dotB = ep.dotC = nullptr;
       rc = use_lin ? launch_jvp_lin(c, Vi, Vn, ep, s, c.jvp_mode == 2) : launch_jvp(c, q_lin, Vi, kEpsJvp, Vn, ep, s);
       if (rc) return rc;
       for (int i = std::max(0, it - o.iop + 1); i <= it; ++i) {

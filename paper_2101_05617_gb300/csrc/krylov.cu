@@ -139,17 +139,19 @@ __global__ void expm_finish_kernel(const double* __restrict__ P, int N, double* 
     expm_finish_entry(P, N, F, ldh, stat, i);
 }
 
-// z -= h1 V_A + h2 V_B (the two modified Gram-Schmidt updates, in that order),
-// then ||z||_2 -> *hsub with the happy-breakdown flag below tol
+// z -= h0 V_C + h1 V_A + h2 V_B (the modified Gram-Schmidt updates, oldest
+// first; V_C, V_A may be absent), then ||z||_2 -> *hsub with the
+// happy-breakdown flag below tol
 __global__ void __launch_bounds__(RED_THREADS) update_norm_kernel(double* __restrict__ z, const double* __restrict__ VA,
                                                                   const double* __restrict__ VB, const double* h1p,
                                                                   const double* h2p, long long n, double* partials,
                                                                   unsigned int* ticket, double* hsub, double tol,
-                                                                  int* happy, int happy_value) {
+                                                                  int* happy, int happy_value,
+                                                                  const double* __restrict__ VC, const double* h0p) {
   if (happy[0]) return;
-  const double h1 = VA ? *h1p : 0.0, h2 = *h2p;
+  const double h1 = VA ? *h1p : 0.0, h2 = *h2p, h0 = VC ? *h0p : 0.0;
   const double acc = mgs_update_range(z, VA, VB, h1, h2, (long long)blockIdx.x * blockDim.x + threadIdx.x, n,
-                                      (long long)gridDim.x * blockDim.x);
+                                      (long long)gridDim.x * blockDim.x, VC, h0);
   double b = block_sum(acc);
   __shared__ bool last;
   if (threadIdx.x == 0) {
@@ -174,30 +176,39 @@ __global__ void __launch_bounds__(RED_THREADS) update_norm_kernel(double* __rest
   }
 }
 
-// V_next = z / *hsub in place, and V_next . V_B -> *c_out (used by the next
-// iteration's orthogonalisation)
+// V_next = z / *hsub in place, V_next . V_B -> *c_out and, with V_A, V_next .
+// V_A -> *c2_out (used by the next iterations' orthogonalisation)
 __global__ void __launch_bounds__(RED_THREADS) scale_dot_kernel(double* __restrict__ z, const double* __restrict__ VB,
                                                                 const double* hsub, long long n, double* partials,
-                                                                unsigned int* ticket, double* c_out, const int* happy) {
+                                                                unsigned int* ticket, double* c_out, const int* happy,
+                                                                const double* __restrict__ VA, double* c2_out) {
   if (happy[0]) return;
   const double r = 1.0 / *hsub;
+  double acc2 = 0.0;
   const double acc = scale_dot_range(z, VB, r, (long long)blockIdx.x * blockDim.x + threadIdx.x, n,
-                                     (long long)gridDim.x * blockDim.x);
-  double b = block_sum(acc);
+                                     (long long)gridDim.x * blockDim.x, VA, &acc2);
+  const double b = block_sum(acc);
+  const double b2 = VA ? block_sum(acc2) : 0.0;   // uniform condition
   __shared__ bool last;
   if (threadIdx.x == 0) {
-    partials[blockIdx.x] = b;
+    partials[2 * blockIdx.x] = b;
+    partials[2 * blockIdx.x + 1] = b2;
     __threadfence();
     last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
-  double sum = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) sum += __ldcg(partials + i);
+  double sum = 0.0, sum2 = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    sum += __ldcg(partials + 2 * i);
+    if (VA) sum2 += __ldcg(partials + 2 * i + 1);
+  }
   sum = block_sum(sum);
+  if (VA) sum2 = block_sum(sum2);
   if (threadIdx.x == 0) {
     *c_out = sum;
+    if (VA) *c2_out = sum2;
     *ticket = 0u;
   }
 }
@@ -292,7 +303,8 @@ int launch_scale_inv(Ctx& c, double* y, const double* x, const double* s_dev, lo
 }
 
 int launch_update_norm(Ctx& c, double* z, const double* VA, const double* VB, const double* h1, const double* h2,
-                       long long N, double* hsub, double tol, int happy_value, cudaStream_t s) {
+                       long long N, double* hsub, double tol, int happy_value, cudaStream_t s, const double* VC,
+                       const double* h0) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (prof_on(c, PK_ORTH)) {
     e0 = prof_event(c);
@@ -301,7 +313,7 @@ int launch_update_norm(Ctx& c, double* z, const double* VA, const double* VB, co
   }
   update_norm_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(z, VA, VB, h1, h2, N, c.d_partials,
                                                        (unsigned int*)(c.d_flags + 8), hsub, tol, c.d_flags,
-                                                       happy_value);
+                                                       happy_value, VC, h0);
   if (prof_on(c, PK_ORTH)) {
     cudaEventRecord(e1, s);
     prof_record(c, PK_ORTH, e0, e1);
@@ -311,7 +323,7 @@ int launch_update_norm(Ctx& c, double* z, const double* VA, const double* VB, co
 }
 
 int launch_scale_dot(Ctx& c, double* z, const double* VB, const double* hsub, long long N, double* c_out,
-                     cudaStream_t s) {
+                     cudaStream_t s, const double* VA, double* c2_out) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (prof_on(c, PK_ORTH)) {
     e0 = prof_event(c);
@@ -319,7 +331,7 @@ int launch_scale_dot(Ctx& c, double* z, const double* VB, const double* hsub, lo
     cudaEventRecord(e0, s);
   }
   scale_dot_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(z, VB, hsub, N, c.d_partials, (unsigned int*)(c.d_flags + 8),
-                                                     c_out, c.d_flags);
+                                                     c_out, c.d_flags, VA, c2_out);
   if (prof_on(c, PK_ORTH)) {
     cudaEventRecord(e1, s);
     prof_record(c, PK_ORTH, e0, e1);

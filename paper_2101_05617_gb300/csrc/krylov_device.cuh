@@ -35,21 +35,25 @@ __device__ __forceinline__ double block_sum(double v) {
 // The two vector passes of the window-2 modified Gram-Schmidt step over the
 // indices i0, i0 + stride, ... < i1 of one thread, four elements in flight
 // (z was written by another kernel or CTA: read through L2).
-//   z -= h1 VA + h2 VB (VA may be null); returns the thread's sum of z_i^2
+//   z -= h0 VC + h1 VA + h2 VB (VC, VA may be null; oldest first); returns the
+//   thread's sum of z_i^2
 __device__ __forceinline__ double mgs_update_range(double* __restrict__ z, const double* __restrict__ VA,
                                                    const double* __restrict__ VB, double h1, double h2, long long i,
-                                                   long long i1, long long stride) {
+                                                   long long i1, long long stride,
+                                                   const double* __restrict__ VC = nullptr, double h0 = 0.0) {
   double acc = 0.0;
   for (; i + 3 * stride < i1; i += 4 * stride) {
-    double v[4], b[4], a[4] = {0.0, 0.0, 0.0, 0.0};
+    double v[4], b[4], a[4] = {0.0, 0.0, 0.0, 0.0}, c[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       v[k] = __ldcg(z + i + k * stride);
       b[k] = VB[i + k * stride];
       if (VA) a[k] = VA[i + k * stride];
+      if (VC) c[k] = VC[i + k * stride];
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
+      if (VC) v[k] = fma(-h0, c[k], v[k]);
       if (VA) v[k] = fma(-h1, a[k], v[k]);
       v[k] = fma(-h2, b[k], v[k]);
       z[i + k * stride] = v[k];
@@ -58,6 +62,7 @@ __device__ __forceinline__ double mgs_update_range(double* __restrict__ z, const
   }
   for (; i < i1; i += stride) {
     double v = __ldcg(z + i);
+    if (VC) v = fma(-h0, VC[i], v);
     if (VA) v = fma(-h1, VA[i], v);
     v = fma(-h2, VB[i], v);
     z[i] = v;
@@ -66,9 +71,38 @@ __device__ __forceinline__ double mgs_update_range(double* __restrict__ z, const
   return acc;
 }
 
-//   z *= r; returns the thread's sum of z_i VB_i
+//   z *= r; returns the thread's sum of z_i VB_i, and with VA also the sum of
+//   z_i VA_i in *za
 __device__ __forceinline__ double scale_dot_range(double* __restrict__ z, const double* __restrict__ VB, double r,
-                                                  long long i, long long i1, long long stride) {
+                                                  long long i, long long i1, long long stride,
+                                                  const double* __restrict__ VA = nullptr, double* za = nullptr) {
+  if (VA) {
+    double acc = 0.0, acc2 = 0.0;
+    for (; i + 3 * stride < i1; i += 4 * stride) {
+      double v[4], b[4], a[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        v[k] = __ldcg(z + i + k * stride);
+        b[k] = VB[i + k * stride];
+        a[k] = VA[i + k * stride];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        v[k] *= r;
+        z[i + k * stride] = v[k];
+        acc = fma(v[k], b[k], acc);
+        acc2 = fma(v[k], a[k], acc2);
+      }
+    }
+    for (; i < i1; i += stride) {
+      const double v = __ldcg(z + i) * r;
+      z[i] = v;
+      acc = fma(v, VB[i], acc);
+      acc2 = fma(v, VA[i], acc2);
+    }
+    *za = acc2;
+    return acc;
+  }
   double acc = 0.0;
   for (; i + 3 * stride < i1; i += 4 * stride) {
     double v[4], b[4];

@@ -98,6 +98,7 @@ struct Ctx {
   double* d_partials = nullptr;   // reduction partials
   double* d_vpart = nullptr;      // partials of the epilogue dot products (2 per volume block)
   double* d_cdot = nullptr;       // V_j . V_{j-1} per basis index
+  double* d_cdot2 = nullptr;      // V_j . V_{j-2} per basis index (window of three)
   double* d_scal = nullptr;       // device scalars (see kiops.cu)
   int* d_flags = nullptr;         // happy flag, happy size
   double* h_pinned = nullptr;     // pinned read-back area
@@ -199,15 +200,23 @@ struct AugEpilogue {
   const double* tail_in = nullptr;  // p doubles (device)
   double* tail_out = nullptr;       // p doubles (device): (tail_in[1..p-1], 0)
   const int* skip = nullptr;        // if non-null and *skip != 0 the kernels return
-  // incomplete orthogonalisation fused into the epilogue (window of two): with
-  // dotB set, h2 = V_B . z - h1 (V_B . V_A) and h1 = V_A . z are formed over the
-  // augmented length n + p (block partials, last block finalises)
+  // incomplete orthogonalisation fused into the epilogue (window of two or
+  // three): with dotB set, the modified Gram-Schmidt coefficients of z against
+  // V_C = V_{j-2}, V_A = V_{j-1}, V_B = V_j (oldest first) are formed from the
+  // dots z . V over the augmented length n + p and the stored V . V products:
+  //   h0 = V_C . z,  h1 = V_A . z - h0 (V_A . V_C),
+  //   h2 = V_B . z - h0 (V_B . V_C) - h1 (V_B . V_A)
+  // (block partials, last block finalises); absent vectors drop their terms
   const double* dotA = nullptr;     // V_{j-1} (null for the first basis vector)
   const double* dotB = nullptr;     // V_j
+  const double* dotC = nullptr;     // V_{j-2} (window of three, j >= 2)
   const double* cprev = nullptr;    // V_j . V_{j-1}
+  const double* cprevC = nullptr;   // V_j . V_{j-2}
+  const double* cprevAC = nullptr;  // V_{j-1} . V_{j-2}
+  double* h0_out = nullptr;
   double* h1_out = nullptr;
   double* h2_out = nullptr;
-  double* dpart = nullptr;          // 2 doubles per block
+  double* dpart = nullptr;          // 3 doubles per block
   unsigned int* dticket = nullptr;
   long long n = 0;
 };
@@ -238,13 +247,15 @@ int launch_scale_inv(Ctx& c, double* y, const double* x, const double* s_dev, lo
 int launch_expm_prep(Ctx& c, int j, double tau, double tau_happy, cudaStream_t s);
 int launch_expm_eval(Ctx& c, int N, double norm1, int* squarings, cudaStream_t s);
 int launch_combine(Ctx& c, int j, long long n, cudaStream_t s);
-// fused incomplete orthogonalisation (window two) after an epilogue with dots:
-// z -= h1 V_A + h2 V_B and ||z|| -> *hsub (happy flag below tol), then
-// V_next = z / *hsub and V_next . V_B -> *c_out
+// fused incomplete orthogonalisation (window two or three) after an epilogue
+// with dots: z -= h0 V_C + h1 V_A + h2 V_B and ||z|| -> *hsub (happy flag below
+// tol), then V_next = z / *hsub, V_next . V_B -> *c_out and, with V_A given,
+// V_next . V_A -> *c2_out
 int launch_update_norm(Ctx& c, double* z, const double* VA, const double* VB, const double* h1, const double* h2,
-                       long long N, double* hsub, double tol, int happy_value, cudaStream_t s);
+                       long long N, double* hsub, double tol, int happy_value, cudaStream_t s,
+                       const double* VC = nullptr, const double* h0 = nullptr);
 int launch_scale_dot(Ctx& c, double* z, const double* VB, const double* hsub, long long N, double* c_out,
-                     cudaStream_t s);
+                     cudaStream_t s, const double* VA = nullptr, double* c2_out = nullptr);
 double fp64_fma_peak_tflops();
 int launch_set_tail(Ctx& c, double* x, long long n, int p, const double* vals, cudaStream_t s);
 int launch_lincomb(Ctx& c, double* out, long long n, int k, const double* const* xs,

@@ -88,3 +88,23 @@ def test_epi_parity_small(order, steps, mode):
         y = it.step(y, dt)
     err = rel_l2_per_var(qd.cpu().numpy(), y)
     assert max(err) < 1e-11, err
+
+
+@pytest.mark.parametrize("mode", [1, 0])
+def test_epi_parity_window_three(mode):
+    """EPI5 on the small configuration with the orthogonalisation window of three
+    (fused into the JVP epilogue and two vector passes): GPU trajectory vs the
+    oracle's with the same window, relative L2 per variable <= 1e-11."""
+    _, g, q, _ = oracle_case(4, 4, seed=0)
+    dt, tol = 900.0, 1e-12
+    ctx = _ctx(g)
+    ctx.set_jvp_mode(mode)
+    qd = torch.tensor(q.reshape(-1), device="cuda")
+    it = oepi.EPI(lambda x: osw.rhs_real(g, x.reshape(q.shape)).reshape(-1),
+                  lambda x, v: osw.jvp(g, x.reshape(q.shape), v.reshape(q.shape)).reshape(-1), 5, tol=tol, iop=3)
+    y = q.reshape(-1).copy()
+    for k in range(5):
+        ctx.epi_step(5, dt, qd, tol=tol, iop=3)
+        y = it.step(y, dt)
+    err = rel_l2_per_var(qd.cpu().numpy(), y)
+    assert max(err) < 1e-11, err
