@@ -63,8 +63,9 @@ typedef struct {
 
 /* Options of the adaptive Krylov phi-function solver (Eq. 29).  tol is relative
  * to the 2-norm of the initial augmented vector; m_* bound the Krylov size;
- * iop is the incomplete-orthogonalisation window; tau_init <= 0 means "start
- * with the whole interval". */
+ * iop is the incomplete-orthogonalisation window (2 and 3 run fused into the
+ * JVP epilogue and two vector passes, wider windows with separate dot and axpy
+ * launches); tau_init <= 0 means "start with the whole interval". */
 typedef struct {
   double tol;
   int m_init, m_min, m_max, iop;
