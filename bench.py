@@ -265,24 +265,30 @@ def ortho_roofline(prof_all, wl):
 
 def fp32_form_comparison(args, dev, workload="ne30_p5", variants=(("fp64", 1, 2), ("complex64_bulk", 2, 2))):
     """The complex64-bulk form against the FP64 path: steps/s of each variant
-    (name, JVP mode, orthogonalisation window) from the same start, each
-    variant's state difference to the first (the FP64 path, window 2) after the
-    run, and the EPI time-discretisation error (FP64 at dt against dt/4)."""
+    (name, JVP mode, orthogonalisation window[, "learned": the learned initial
+    substep after the warm-up]) from the same start, each variant's state
+    difference to the first (the FP64 path, window 2) after the run, and the EPI
+    time-discretisation error (FP64 at dt against dt/4)."""
     import torch
 
-    from paper_2101_05617_gb300 import swepi, synth
+    from paper_2101_05617_gb300 import learned, swepi, synth
     wl = synth.WORKLOADS[workload]
     f = synth.make_fields(wl, args.seed)
     res = {}
     states = {}
-    runs = [(name, mode, iop, wl.dt, 1) for name, mode, iop in variants] + [("fp64_dt4", 1, 2, wl.dt / 4, 4)]
-    for name, mode, iop, dt, mult in runs:
+    runs = [(v[0], v[1], v[2], wl.dt, 1, len(v) > 3 and v[3] == "learned") for v in variants]
+    runs.append(("fp64_dt4", 1, 2, wl.dt / 4, 4, False))
+    ctl = None
+    for name, mode, iop, dt, mult, use_ctl in runs:
         ctx = swepi.SWContext(wl.ne, wl.p, f.rotation)
         h, hB, V = f.evaluate(ctx.node_xyz())
         q = torch.tensor(ctx.state_from_fields(h, hB, V), device=dev)
         ctx.set_jvp_mode(mode)
         for _ in range(args.warmup * mult):
             ctx.epi_step(wl.order, dt, q, tol=wl.tol, iop=iop)
+        if use_ctl:
+            ctl = ctl or learned.Controller.load()
+            swepi.sw_set_controller(ctx.handle, ctl.handle)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -293,6 +299,7 @@ def fp32_form_comparison(args, dev, workload="ne30_p5", variants=(("fp64", 1, 2)
         torch.cuda.synchronize()
         res[name] = args.steps * mult / (e0.elapsed_time(e1) * 1e-3)
         states[name] = q.view(3, -1).clone()
+        swepi.sw_set_controller(ctx.handle, None)
         ctx.close()
 
     def rel(a, b):
@@ -302,8 +309,10 @@ def fp32_form_comparison(args, dev, workload="ne30_p5", variants=(("fp64", 1, 2)
                        f"KIOPS tol {wl.tol:g}, plain rule",
            "steps": args.warmup + args.steps,
            "time_discretisation_err_rel_l2": rel(states[base], states["fp64_dt4"])}
-    for name, mode, iop in variants:
+    for v in variants:
+        name, mode, iop = v[0], v[1], v[2]
         out[name] = {"jvp": "FP64" if mode == 1 else "complex64 bulk (FP32 imaginary half)", "window": iop,
+                     "control": v[3] if len(v) > 3 else "plain",
                      "steps_per_s": res[name], "speedup_vs_" + base: res[name] / res[base]}
         if name != base:
             out[name]["err_vs_" + base + "_rel_l2"] = rel(states[name], states[base])
@@ -579,7 +588,8 @@ def main():
             if args.workload == "ne60_p5":
                 # on this grid the form needs the orthogonalisation window of three
                 out["forms"]["complex64_bulk_ne60_p5"] = fp32_form_comparison(
-                    args, dev, "ne60_p5", (("fp64", 1, 2), ("fp64_window3", 1, 3), ("complex64_bulk_window3", 2, 3)))
+                    args, dev, "ne60_p5", (("fp64", 1, 2), ("fp64_window3", 1, 3), ("complex64_bulk_window3", 2, 3),
+                                           ("complex64_bulk_window3_learned", 2, 3, "learned")))
             if world == 1 and not args.no_ensemble:
                 out["forms"]["ensemble_96"] = ensemble_form(args, dev, peak)
         if world == 1 and not args.no_cpu_baseline:
