@@ -64,6 +64,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--large", action="store_true",
+                    help="also run the 6x90x90, p=6 EPI6 instance (FP64 and complex64-bulk, per-kernel rooflines)")
+    ap.add_argument("--only-forms", default="",
+                    help="comma-separated forms to run (learned, ne30, ne60, ensemble, large); default all")
     ap.add_argument("--control", default="plain", choices=["learned", "plain"])
     ap.add_argument("--jvp-mode", type=int, default=1, choices=[0, 1],
                     help="0: full complex-step evaluation per JVP, 1: split (default)")
@@ -263,12 +267,64 @@ def ortho_roofline(prof_all, wl):
             "peak_source": src}
 
 
-def fp32_form_comparison(args, dev, workload="ne30_p5", variants=(("fp64", 1, 2), ("complex64_bulk", 2, 2))):
+def kernel_rooflines(prof, wl, mode, iop, step_ms, fp64_peak):
+    """Per-kernel figures of one EPI step with every kernel family bracketed by
+    events.  FP64 kernels: algorithmic flops (flops_per_jvp, 6 more per node for
+    the third dot of window 3) against the measured FP64 peak.  HBM: the
+    algorithmic vector bytes against the measured copy bandwidth; the volume
+    kernel reads v, the 4 augmented-operator vectors and the iop dot operands and
+    writes Jv (24 (6 + iop) B per node), plus its 11 split-JVP coefficients per
+    node (8 B each in FP64, 4 B in the complex64-bulk form); the two vector passes
+    move (read z and the iop basis vectors, write z) + (read z and iop - 1 basis
+    vectors, write V_{j+1}) = 8 (4 iop + 3) B per unknown of the augmented vector."""
+    hbm, _ = hbm_peak_gbs()
+    nodes = 6 * wl.ne * wl.ne * wl.ns * wl.ns
+    fv, ff = flops_per_jvp(wl.ne, wl.ns)
+    fv += 6 * nodes * (iop - 2)
+    out = {}
+
+    def avg(kind):
+        k = prof[kind]
+        return k["ms"] / k["count"] * 1e-3 if k["count"] else None
+    tv, tf, to = avg("volume_jvp"), avg("face_jvp"), avg("orthogonalisation")
+    if tv:
+        vbytes = nodes * (24 * (6 + iop) + 11 * (8 if mode == 1 else 4))
+        v = {"avg_us": tv * 1e6, "launches": prof["volume_jvp"]["count"], "flops": fv,
+             "bytes": vbytes, "gbs": vbytes / tv / 1e9, "hbm_frac": vbytes / tv / 1e9 / hbm}
+        if mode == 1:
+            v.update({"tflops": fv / tv / 1e12, "fp64_frac": fv / tv / 1e12 / fp64_peak})
+        else:
+            v["fp32_tflops"] = fv / tv / 1e12
+        out["volume"] = v
+    if tf:
+        f = {"avg_us": tf * 1e6, "launches": prof["face_jvp"]["count"], "flops": ff}
+        if mode == 1:
+            f.update({"tflops": ff / tf / 1e12, "fp64_frac": ff / tf / 1e12 / fp64_peak})
+        else:
+            f["fp32_tflops"] = ff / tf / 1e12
+        out["face"] = f
+    if to:
+        t = 2.0 * to   # one update-and-norm plus one scale-and-dot pass per Krylov iteration
+        obytes = 8.0 * (4 * iop + 3) * (wl.n_unknowns + 4)
+        out["orthogonalisation"] = {"avg_us_per_iteration": t * 1e6, "bytes_per_iteration": obytes,
+                                    "gbs": obytes / t / 1e9, "hbm_frac": obytes / t / 1e9 / hbm}
+    if prof["expm"]["count"]:
+        out["expm"] = {"avg_us": avg("expm") * 1e6, "launches": prof["expm"]["count"]}
+    out["share_of_step"] = {k: prof[k]["ms"] / step_ms
+                            for k in ("volume_jvp", "face_jvp", "orthogonalisation", "expm", "linearize")}
+    out["peaks"] = {"fp64_tflops": fp64_peak, "hbm_gbs": hbm}
+    return out
+
+
+def fp32_form_comparison(args, dev, workload="ne30_p5", variants=(("fp64", 1, 2), ("complex64_bulk", 2, 2)),
+                         fp64_peak=None):
     """The complex64-bulk form against the FP64 path: steps/s of each variant
     (name, JVP mode, orthogonalisation window[, "learned": the learned initial
     substep after the warm-up]) from the same start, each variant's state
     difference to the first (the FP64 path, window 2) after the run, and the EPI
-    time-discretisation error (FP64 at dt against dt/4)."""
+    time-discretisation error (FP64 at dt against dt/4).  With fp64_peak, each
+    variant then takes one more step with every kernel family bracketed by
+    events (after its state was kept) and reports per-kernel rooflines."""
     import torch
 
     from paper_2101_05617_gb300 import learned, swepi, synth
@@ -276,13 +332,16 @@ def fp32_form_comparison(args, dev, workload="ne30_p5", variants=(("fp64", 1, 2)
     f = synth.make_fields(wl, args.seed)
     res = {}
     states = {}
+    kernels = {}
     runs = [(v[0], v[1], v[2], wl.dt, 1, len(v) > 3 and v[3] == "learned") for v in variants]
     runs.append(("fp64_dt4", 1, 2, wl.dt / 4, 4, False))
     ctl = None
+    fields = None   # the same grid and rotation for every run: evaluate the fields once
     for name, mode, iop, dt, mult, use_ctl in runs:
         ctx = swepi.SWContext(wl.ne, wl.p, f.rotation)
-        h, hB, V = f.evaluate(ctx.node_xyz())
-        q = torch.tensor(ctx.state_from_fields(h, hB, V), device=dev)
+        if fields is None:
+            fields = f.evaluate(ctx.node_xyz())
+        q = torch.tensor(ctx.state_from_fields(*fields), device=dev)
         ctx.set_jvp_mode(mode)
         try:
             for _ in range(args.warmup * mult):
@@ -300,6 +359,16 @@ def fp32_form_comparison(args, dev, workload="ne30_p5", variants=(("fp64", 1, 2)
             torch.cuda.synchronize()
             res[name] = args.steps * mult / (e0.elapsed_time(e1) * 1e-3)
             states[name] = q.view(3, -1).clone()
+            if fp64_peak is not None and mult == 1:
+                ctx.profile(True)
+                b0 = torch.cuda.Event(enable_timing=True)
+                b1 = torch.cuda.Event(enable_timing=True)
+                b0.record()
+                ctx.epi_step(wl.order, dt, q, tol=wl.tol, iop=iop)
+                b1.record()
+                torch.cuda.synchronize()
+                kernels[name] = kernel_rooflines(ctx.profile_read(), wl, mode, iop, b0.elapsed_time(b1), fp64_peak)
+                ctx.profile(False)
         except Exception as e:   # e.g. a variant that left the finite range: reported per variant
             res[name] = f"{type(e).__name__}: {e}"[:200]
             states[name] = None
@@ -327,6 +396,8 @@ def fp32_form_comparison(args, dev, workload="ne30_p5", variants=(("fp64", 1, 2)
             out[name]["speedup_vs_" + base] = res[name] / res[base]
             if name != base:
                 out[name]["err_vs_" + base + "_rel_l2"] = rel(states[name], states[base])
+        if name in kernels:
+            out[name]["kernels"] = kernels[name]
     return out
 
 
@@ -593,7 +664,13 @@ def main():
         if not args.no_forms:
             from paper_2101_05617_gb300 import learned
 
+            only = {x.strip() for x in args.only_forms.split(",") if x.strip()}
+            short = {"learned_vs_plain_same_start": "learned", "complex64_bulk_ne30_p5": "ne30",
+                     "complex64_bulk_ne60_p5": "ne60", "ensemble_96": "ensemble", "large_ne90_p6": "large"}
+
             def form(name, fn):
+                if only and short[name] not in only:
+                    return
                 # a form that fails is reported, not allowed to lose the benchmark line
                 try:
                     out["forms"][name] = fn()
@@ -612,6 +689,11 @@ def main():
                                            ("complex64_bulk_window3_learned", 2, 3, "learned"))))
             if world == 1 and not args.no_ensemble:
                 form("ensemble_96", lambda: ensemble_form(args, dev, peak))
+            if world == 1 and (args.large or "large" in only):
+                # the large single instance: 6 x 90 x 90 elements, p = 6, bottom topography, EPI6
+                # (opt-in: several minutes, most of it the host-side field evaluation)
+                form("large_ne90_p6", lambda: fp32_form_comparison(
+                    args, dev, "ne90_p6", (("fp64", 1, 2), ("complex64_bulk_window3", 2, 3)), fp64_peak=peak))
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = oracle_sample(wl, args.seed, krylov / args.steps, P)
             out["cpu_baseline_all_cores"] = oracle_sample_all_cores(wl, args.seed, krylov / args.steps, P,
