@@ -8,7 +8,7 @@ State layout: q[var, panel, e2, e1, k2, k1] with var 0 = sqrt(g) H,
 var i = sqrt(g) H u^i (the tensor density q^mu of App. D), x^i angular
 cubed-sphere coordinates in [-pi/4, pi/4], H = h - h_B.
 
-Readings of passages the paper leaves open (each also listed in the design doc):
+Readings of passages the paper leaves open:
   * metric at interface points: evaluated analytically at the point;
   * each interface flux is computed once, in the coordinates of the side with
     the lower panel index (within a panel: the lower element), and handed to

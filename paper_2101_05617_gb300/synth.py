@@ -2,7 +2,7 @@
 
 This module holds no arithmetic of the numerical method: it only draws random
 numbers and evaluates smooth fields (real spherical-harmonic sums) at Cartesian
-unit vectors supplied by the caller.  Both the CUDA path and the CPU checker
+unit vectors supplied by the caller.  Both the CUDA path and the CPU oracle
 evaluate the fields at their own node positions and convert them to the state
 with their own geometry.
 
