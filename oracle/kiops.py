@@ -164,7 +164,8 @@ def kiops(tau_out, matvec, b, tol=1e-10, m_init=10, m_min=10, m_max=128, iop=2,
         last_err = err
         if trace is not None:
             trace.append(dict(j=j, m=m, tau=tau, omega=omega, accept=accept, happy=happy,
-                              m_new=m_new, tau_new=tau_new))
+                              m_new=m_new, tau_new=tau_new, beta=beta,
+                              hsub=0.0 if happy else H[j, j - 1], Fjj=0.0 if happy else F[j - 1, j]))
         if accept:
             w = beta * (V[:j, :n].T @ F[:j, 0])
             tau_now += tau
