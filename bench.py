@@ -691,7 +691,7 @@ def main():
                 form("ensemble_96", lambda: ensemble_form(args, dev, peak))
             if world == 1 and (args.large or "large" in only):
                 # the large single instance: 6 x 90 x 90 elements, p = 6, bottom topography, EPI6
-                # (opt-in: several minutes, most of it the host-side field evaluation)
+                # (opt-in: minutes, most of them the host-side evaluation of its degree-32 fields)
                 form("large_ne90_p6", lambda: fp32_form_comparison(
                     args, dev, "ne90_p6", (("fp64", 1, 2), ("complex64_bulk_window3", 2, 3)), fp64_peak=peak))
         if world == 1 and not args.no_cpu_baseline:

@@ -89,6 +89,9 @@ def real_sph_harm(L, xyz):
     return out
 
 
+_SUM_CHUNK = 1 << 15   # points per chunk of a harmonic sum (its work arrays stay in cache)
+
+
 class HarmonicField:
     """Seeded sum of real spherical harmonics of degree 1..L, unit peak."""
 
@@ -100,11 +103,15 @@ class HarmonicField:
         self.scale = 1.0 / peak
 
     def raw(self, xyz):
-        Y = real_sph_harm(self.L, xyz)
-        s = np.zeros(np.shape(xyz)[1:])
-        for k, c in self.coef.items():
-            s = s + c * Y[k]
-        return s
+        # the harmonics of real_sph_harm, accumulated degree by degree over
+        # cache-sized chunks of points instead of stored (equal to rounding)
+        r = np.asarray(xyz, dtype=float)
+        flat = r.reshape(3, -1)
+        n = flat.shape[1]
+        if n <= _SUM_CHUNK:
+            return _sph_sum(self.L, self.coef, flat).reshape(r.shape[1:])
+        parts = [_sph_sum(self.L, self.coef, flat[:, i:i + _SUM_CHUNK]) for i in range(0, n, _SUM_CHUNK)]
+        return np.concatenate(parts).reshape(r.shape[1:])
 
     def __call__(self, xyz):
         return self.scale * self.raw(xyz)

@@ -1,6 +1,6 @@
-"""Seeded inputs of the batched ensemble (host only): the member list and the
-member fields.  The fields are evaluated by an accumulating spherical-harmonic
-sum; it must equal the sum over the stored harmonics."""
+"""Seeded inputs (host only): the ensemble's member list and member fields,
+and the workload fields.  Both are evaluated by an accumulating
+spherical-harmonic sum; it must equal the sum over the stored harmonics."""
 import numpy as np
 
 from paper_2101_05617_gb300 import synth
@@ -19,6 +19,20 @@ def test_accumulated_harmonic_sum_equals_stored_harmonics():
         Y = synth.real_sph_harm(L, xyz)
         ref = sum(c * Y[k] for k, c in coef.items())
         np.testing.assert_allclose(synth._sph_sum(L, coef, xyz), ref, rtol=0, atol=1e-12 * np.max(np.abs(ref)))
+
+
+def test_workload_field_is_the_stored_harmonic_sum_over_chunks():
+    """The workload fields (HarmonicField) accumulate their sum over chunks of
+    points: over several chunks and a ragged tail, and for an input of more than
+    one dimension, the result equals the sum over the stored harmonics."""
+    n = 2 * synth._SUM_CHUNK + 1234
+    xyz = _unit_vectors(n, 7)
+    f = synth.HarmonicField(np.random.Generator(np.random.PCG64(11)), 16)
+    Y = synth.real_sph_harm(16, xyz)
+    ref = f.scale * sum(c * Y[k] for k, c in f.coef.items())
+    got = f(xyz)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.max(np.abs(ref)))
+    assert f(xyz.reshape(3, 2, -1)).shape == (2, n // 2) and np.array_equal(f(xyz.reshape(3, 2, -1)).ravel(), got)
 
 
 def test_member_list_is_balanced_and_seeded():
