@@ -652,6 +652,7 @@ def main():
                           "l2": "inputs larger than L2 (Krylov basis ~2.4 GB per KIOPS call)"},
                "jvp_dof_per_s": wl.n_unknowns / t_jvp,
                "jvp_dof_per_s_total": world * wl.n_unknowns / t_jvp,
+               "jvp_nodes_per_s": wl.n_unknowns / 3 / t_jvp,   # the paper's DOF count: one per solution point
                "krylov_iters_per_step": krylov / args.steps,
                "krylov_iters_each_step": krylov_list,
                "clocks": clock_info,
