@@ -43,3 +43,8 @@ def golden_epi_coefficients():
         P = max(c for _, c in d)
         out[order] = [[d[(r, c)] for c in range(1, P + 1)] for r in range(1, M + 1)]
     return out
+
+
+def golden_dfr_orders():
+    """Table 1: {N_s: (L1, L2, Linf) order of accuracy}."""
+    return {int(t[0]): tuple(float(x) for x in t[1:4]) for t in _rows("dfr_orders_table1.txt")}
