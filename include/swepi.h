@@ -183,6 +183,14 @@ int sw_kiops_phi(sw_ctx_t ctx, const double* q_lin_dev, double dt, double tau_ou
 int sw_epi_step(sw_ctx_t ctx, int order, double dt, double* q_dev, const sw_kiops_opts* opts,
                 sw_kiops_stats* st, void* stream);
 
+/* sw_epi_step on a state held in HOST memory: q_host (n doubles, caller-owned,
+ * pinned or pageable) is copied to a library-owned device buffer (allocated on
+ * first use), advanced by one step exactly as sw_epi_step does, and copied back
+ * on `stream`; returns after the copy back.  On an error status q_host is left
+ * unchanged.  Same history, statistics and errors as sw_epi_step. */
+int sw_epi_step_host(sw_ctx_t ctx, int order, double dt, double* q_host, const sw_kiops_opts* opts,
+                     sw_kiops_stats* st, void* stream);
+
 /* Seed history entry i (1 = most recent) with (q_{n-i}, F(q_{n-i})) device
  * vectors (copied); F_dev NULL computes it.  i <= 4. */
 int sw_epi_set_history(sw_ctx_t ctx, int i, const double* q_dev, const double* F_dev, void* stream);

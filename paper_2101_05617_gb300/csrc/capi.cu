@@ -245,7 +245,7 @@ void sw_free(sw_ctx_t c) {
   if (!c) return;
   double* ptrs[] = {c->d_node_coef, c->d_face_coef, c->d_fb, c->d_V, c->d_X, c->d_H, c->d_F, c->d_expm_ws,
                     c->d_partials, c->d_scal, c->d_Fn, c->d_tmp, c->d_tmp2, c->d_lin_node, c->d_lin_face,
-                    c->d_vpart, c->d_cdot, c->d_cdot2, c->d_diag_tab, c->d_diag_part, c->d_diag_out};
+                    c->d_vpart, c->d_cdot, c->d_cdot2, c->d_diag_tab, c->d_diag_part, c->d_diag_out, c->d_qhost};
   if (c->d_diag_flags) cudaFree(c->d_diag_flags);
   if (c->d_lin_node32) cudaFree(c->d_lin_node32);
   if (c->d_lin_face32) cudaFree(c->d_lin_face32);
@@ -436,6 +436,20 @@ int sw_epi_step(sw_ctx_t c, int order, double dt, double* q, const sw_kiops_opts
   const double* ys[2] = {q, c->d_tmp};
   double one[2] = {1.0, 1.0};
   if ((rc = launch_lincomb(*c, q, n, 2, ys, one, s))) return rc;
+  return cuda_status(cudaStreamSynchronize(s));
+}
+
+int sw_epi_step_host(sw_ctx_t c, int order, double dt, double* q_host, const sw_kiops_opts* opts,
+                     sw_kiops_stats* st, void* stream) {
+  if (!c || !q_host) return SW_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  int rc = alloc_vec(c->d_qhost, c->n);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(c->d_qhost, q_host, sizeof(double) * c->n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return SW_ECUDA;
+  if ((rc = sw_epi_step(c, order, dt, c->d_qhost, opts, st, stream))) return rc;
+  if (cudaMemcpyAsync(q_host, c->d_qhost, sizeof(double) * c->n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return SW_ECUDA;
   return cuda_status(cudaStreamSynchronize(s));
 }
 

@@ -107,6 +107,7 @@ struct Ctx {
   double* d_Fn = nullptr;
   double* d_tmp = nullptr;
   double* d_tmp2 = nullptr;
+  double* d_qhost = nullptr;     // device copy of the state of sw_epi_step_host
   double* d_R[MAX_HIST] = {};
   double* d_b[MAX_NB] = {};
   double* d_hq[MAX_HIST] = {};    // history ring: q_{n-i}

@@ -104,6 +104,8 @@ def lib():
                                ctypes.POINTER(sw_kiops_opts), vp, ctypes.POINTER(sw_kiops_stats), vp]
     L.sw_epi_step.argtypes = [vp, ip, ctypes.c_double, vp, ctypes.POINTER(sw_kiops_opts),
                               ctypes.POINTER(sw_kiops_stats), vp]
+    L.sw_epi_step_host.argtypes = [vp, ip, ctypes.c_double, vp, ctypes.POINTER(sw_kiops_opts),
+                                   ctypes.POINTER(sw_kiops_stats), vp]
     L.sw_epi_set_history.argtypes = [vp, ip, vp, vp, vp]
     L.sw_epi_reset.argtypes = [vp]
     L.sw_kernel_launches.argtypes = [vp]
@@ -145,7 +147,7 @@ def lib():
 
 EXPORTED = ["sw_init", "sw_free", "sw_num_unknowns", "sw_grid_info", "sw_node_xyz", "sw_state_from_fields",
             "sw_set_bottom", "sw_rhs", "sw_jvp", "sw_jvp_static_scratch", "sw_linearize", "sw_jvp_linearized",
-            "sw_set_jvp_mode", "sw_kiops_phi", "sw_epi_step", "sw_epi_set_history",
+            "sw_set_jvp_mode", "sw_kiops_phi", "sw_epi_step", "sw_epi_step_host", "sw_epi_set_history",
             "sw_epi_reset", "sw_kernel_launches", "sw_profile", "sw_profile_kinds", "sw_profile_read", "sw_fp64_fma_peak",
             "sw_status_str", "sw_mlp_create", "sw_mlp_free", "sw_mlp_set_params", "sw_mlp_get_params",
             "sw_mlp_forward", "sw_mlp_gradient", "sw_mlp_train", "sw_set_controller", "sw_kiops_log",
@@ -278,6 +280,25 @@ def sw_epi_step(ctx, order, dt, q, opts=None, stream=None):
     o = opts if opts is not None else make_opts()
     _check("sw_epi_step", lib().sw_epi_step(ctx, int(order), float(dt), _dev_ptr(q, n), ctypes.byref(o),
                                             ctypes.byref(st), _stream(stream)))
+    return st.as_dict()
+
+
+def _host_ptr(t, n):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError("expected a contiguous float64 host tensor")
+    if t.numel() < n:
+        raise ValueError(f"tensor has {t.numel()} elements, need {n}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def sw_epi_step_host(ctx, order, dt, q_host, opts=None, stream=None):
+    """sw_epi_step on a host tensor (pinned or pageable), copied in and back by the library."""
+    n = sw_num_unknowns(ctx)
+    st = sw_kiops_stats()
+    o = opts if opts is not None else make_opts()
+    _check("sw_epi_step_host", lib().sw_epi_step_host(ctx, int(order), float(dt), _host_ptr(q_host, n),
+                                                      ctypes.byref(o), ctypes.byref(st), _stream(stream)))
     return st.as_dict()
 
 
@@ -585,6 +606,9 @@ class SWContext:
 
     def epi_step(self, order, dt, q, stream=None, **opts):
         return sw_epi_step(self.handle, order, dt, q, make_opts(**opts), stream)
+
+    def epi_step_host(self, order, dt, q_host, stream=None, **opts):
+        return sw_epi_step_host(self.handle, order, dt, q_host, make_opts(**opts), stream)
 
     def epi_set_history(self, i, q, F=None, stream=None):
         sw_epi_set_history(self.handle, i, q, F, stream)

@@ -108,3 +108,22 @@ def test_epi_parity_window_three(mode):
         y = it.step(y, dt)
     err = rel_l2_per_var(qd.cpu().numpy(), y)
     assert max(err) < 1e-11, err
+
+
+def test_epi_step_host_equals_device_step():
+    """sw_epi_step_host (the state in host memory, pinned or pageable, copied in
+    and back by the library) takes the device-pointer call's trajectory bit for
+    bit, start-up steps included, with the same statistics."""
+    _, g, q, _ = oracle_case(4, 4, seed=0)
+    ctxs = [_ctx(g) for _ in range(3)]
+    qd = torch.tensor(q.reshape(-1), device="cuda")
+    qpin = torch.tensor(q.reshape(-1)).pin_memory()
+    qpage = torch.tensor(q.reshape(-1))
+    for _ in range(4):
+        sd = ctxs[0].epi_step(4, 900.0, qd, tol=1e-12)
+        sp = ctxs[1].epi_step_host(4, 900.0, qpin, tol=1e-12)
+        sg = ctxs[2].epi_step_host(4, 900.0, qpage, tol=1e-12)
+        assert sd == sp == sg, (sd, sp, sg)
+    ref = qd.cpu()
+    assert torch.equal(ref, qpin) and torch.equal(ref, qpage)
+    assert not torch.equal(ref, torch.tensor(q.reshape(-1)))
