@@ -131,6 +131,8 @@ def kiops(tau_out, matvec, b, tol=1e-10, m_init=10, m_min=10, m_max=128, iop=2,
         else:
             err = beta * H[j, j - 1] * abs(F[j - 1, j])
             omega = (tau_end / tau) * err / (tol * beta0)
+            if not math.isfinite(omega):
+                raise KiopsError("non-finite error estimate")
             accept = omega <= DELTA
             if prev is not None and prev[0] == m and prev[1] != tau:
                 order = max(1.0, math.log(omega / prev[2]) / math.log(tau / prev[1]))

@@ -98,3 +98,22 @@ def test_substepping_on_stiff_operator():
     w, st = kiops(1.0, lambda v: 0.01 * (A @ v), b, tol=1e-10, m_max=40)
     assert st['substeps'] > 1
     assert np.linalg.norm(w - ref) < 1e-8 * np.linalg.norm(ref)
+
+
+@pytest.mark.filterwarnings("ignore::RuntimeWarning")
+def test_non_finite_error_estimate_stops_the_solve():
+    """An operator that produces a non-finite value ends the solve with an error
+    at the first attempt (the library returns SW_ENONFINITE there) instead of
+    rejecting substeps until the limit."""
+    n = 20
+    calls = []
+
+    def matvec(x):
+        calls.append(1)
+        y = -x.copy()
+        y[3] = np.inf
+        return y
+    from oracle.kiops import KiopsError
+    with pytest.raises(KiopsError, match="non-finite"):
+        kiops(1.0, matvec, [np.zeros(n), np.ones(n)], max_rejects=50)
+    assert len(calls) <= 10
