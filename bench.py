@@ -685,7 +685,7 @@ def main():
                 # on this grid the form needs the orthogonalisation window of three
                 form("complex64_bulk_ne60_p5", lambda: fp32_form_comparison(
                     args, dev, "ne60_p5", (("fp64", 1, 2), ("fp64_window3", 1, 3), ("complex64_bulk_window3", 2, 3),
-                                           ("complex64_bulk_window3_learned", 2, 3, "learned"))))
+                                           ("complex64_bulk_window3_learned", 2, 3, "learned")), fp64_peak=peak))
             if world == 1 and not args.no_ensemble:
                 form("ensemble_96", lambda: ensemble_form(args, dev, peak))
             if world == 1 and (args.large or "large" in only):
