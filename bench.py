@@ -360,14 +360,18 @@ def fp32_form_comparison(args, dev, workload="ne30_p5", variants=(("fp64", 1, 2)
             res[name] = args.steps * mult / (e0.elapsed_time(e1) * 1e-3)
             states[name] = q.view(3, -1).clone()
             if fp64_peak is not None and mult == 1:
-                ctx.profile(True)
-                b0 = torch.cuda.Event(enable_timing=True)
-                b1 = torch.cuda.Event(enable_timing=True)
-                b0.record()
-                ctx.epi_step(wl.order, dt, q, tol=wl.tol, iop=iop)
-                b1.record()
-                torch.cuda.synchronize()
-                kernels[name] = kernel_rooflines(ctx.profile_read(), wl, mode, iop, b0.elapsed_time(b1), fp64_peak)
+                try:   # a failure here leaves the variant's timing and state in place
+                    ctx.profile(True)
+                    b0 = torch.cuda.Event(enable_timing=True)
+                    b1 = torch.cuda.Event(enable_timing=True)
+                    b0.record()
+                    ctx.epi_step(wl.order, dt, q, tol=wl.tol, iop=iop)
+                    b1.record()
+                    torch.cuda.synchronize()
+                    kernels[name] = kernel_rooflines(ctx.profile_read(), wl, mode, iop, b0.elapsed_time(b1),
+                                                     fp64_peak)
+                except Exception as e:
+                    kernels[name] = {"error": f"{type(e).__name__}: {e}"[:200]}
                 ctx.profile(False)
         except Exception as e:   # e.g. a variant that left the finite range: reported per variant
             res[name] = f"{type(e).__name__}: {e}"[:200]
