@@ -55,6 +55,36 @@ def test_flop_counts():
     assert fv == 6 * 3600 * 36 * 165 and ff == 12 * 3600 * 6 * 112
 
 
+def test_kernel_rooflines_arithmetic():
+    """Per-kernel figures of a profiled EPI step: algorithmic flops and bytes per
+    launch (the volume kernel's vectors 24 (6 + window) B/node plus its 11
+    coefficients, the vector passes 8 (4 window + 3) B per unknown), divided by
+    the average event time, against the given peaks."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2101_05617_gb300 import synth
+    wl = synth.WORKLOADS["ne60_p5"]
+    nodes = 6 * 60 * 60 * 36
+    prof = {k: {"ms": 0.0, "count": 0} for k in ("volume_jvp", "face_jvp", "orthogonalisation", "expm", "linearize")}
+    prof["volume_jvp"] = {"ms": 2.0, "count": 10}       # 0.2 ms per launch
+    prof["face_jvp"] = {"ms": 0.5, "count": 10}
+    prof["orthogonalisation"] = {"ms": 1.0, "count": 20}  # two passes per iteration: 0.1 ms per iteration
+    for mode, iop, coef in ((1, 2, 8), (1, 3, 8), (2, 3, 4)):
+        r = bench.kernel_rooflines(prof, wl, mode, iop, 10.0, 1.25)
+        vb = nodes * (24 * (6 + iop) + 11 * coef)
+        assert r["volume"]["bytes"] == vb
+        assert abs(r["volume"]["gbs"] - vb / 2e-4 / 1e9) < 1e-9 * r["volume"]["gbs"]
+        ob = 8.0 * (4 * iop + 3) * (wl.n_unknowns + 4)
+        assert r["orthogonalisation"]["bytes_per_iteration"] == ob
+        assert abs(r["orthogonalisation"]["gbs"] - ob / 1e-4 / 1e9) < 1e-9 * ob
+        fv = bench.flops_per_jvp(60, 6)[0] + 6 * nodes * (iop - 2)
+        if mode == 1:
+            assert abs(r["volume"]["fp64_frac"] - fv / 2e-4 / 1e12 / 1.25) < 1e-12
+        else:
+            assert "fp64_frac" not in r["volume"] and "fp32_tflops" in r["volume"]
+        assert r["share_of_step"]["volume_jvp"] == 0.2 and "expm" not in r
+
+
 def test_reference_arm_runs_on_cpu():
     """--impl reference times the oracle on the host (small bounded sample)."""
     sys.path.insert(0, ROOT)
