@@ -6,7 +6,8 @@ Test infrastructure only (see ``oracle/__init__.py``).
 Readings: v_m carries the factor Delta t as in Eq. (35) (the step list after
 Eq. 38 writes it without Delta t and multiplies w_n by Delta t instead, which
 is the same update); the first P steps use N_sub = 8 EPI2 substeps of
-Delta t / N_sub each (the paper says only "a smaller time step").
+Delta t / N_sub each (the paper fixes only that the start-up steps are
+shorter, not by how much).
 """
 from fractions import Fraction as Fr
 

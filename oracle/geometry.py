@@ -16,7 +16,8 @@ def panel_angles(lam0, phi0, alpha0):
     """(lambda_p, phi_p, alpha_p) of the six panels from panel 0's rotation.
 
     Eq. (81)-(95), reading every tan^{-1}(num/den) as atan2(num, den) (the
-    "correct branch" the paper asks for after Eq. 95), and the special case
+    paper requires the branch that puts the angle in the right quadrant, after
+    Eq. 95), and the special case
     phi_0 = alpha_0 = 0 given there.
     """
     cl, sl = np.cos(lam0), np.sin(lam0)
