@@ -375,6 +375,7 @@ int sw_epi_set_history(sw_ctx_t c, int i, const double* q, const double* F, void
 int sw_epi_step(sw_ctx_t c, int order, double dt, double* q, const sw_kiops_opts* opts, sw_kiops_stats* st,
                 void* stream) {
   if (!c || !q || order < 2 || order > 6 || !std::isfinite(dt) || !(dt > 0)) return SW_EINVAL;
+  TraceRange trace("EPI step");
   cudaStream_t s = as_stream(stream);
   sw_kiops_opts o = opts ? *opts : default_opts();
   int rc = ensure_epi(*c);

@@ -1445,6 +1445,7 @@ int sw_ens_epi_run(sw_ens_t e, int steps, const int* orders, const double* dts, 
     // members run the FP64 split JVP with the plain adaptive rule
     if (c.jvp_mode != 1 || c.controller) return SW_EINVAL;
   }
+  TraceRange trace("ensemble EPI run");
   return ens_run(*e, steps, orders, dts, q_dev, o, stats, as_stream(stream));
 }
 

@@ -91,6 +91,7 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
   if (nb < 1 || nb > MAX_NB || !(tau_out > 0) || o.m_min < 1 || o.m_max < o.m_min || o.m_max > 150 || o.iop < 1 ||
       !(o.tol > 0))
     return SW_EINVAL;
+  TraceRange trace("phi-function call");
   int rc = ensure_krylov(c, o.m_max);
   if (rc) return rc;
   const long long n = c.n;
@@ -163,6 +164,7 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
   const long long ldv = c.ldv;
 
   while (!K.done()) {
+    TraceRange attempt("substep attempt");
     const int j = K.j, m_cur = K.m;
     if (j == 0) {
       if ((rc = launch_norm2(c, c.d_X, N, c.d_scal + S_BETA, 0.0, nullptr, 0, nullptr, s))) return rc;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <vector>
@@ -10,6 +11,16 @@
 #include "../../include/swepi.h"
 
 namespace swepi {
+
+// Named range for tracing tools (NVTX): EPI steps, phi-function calls and
+// their substep attempts show up on a profiler's timeline; without a tool
+// attached the push and pop return at once.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 constexpr int MAX_NS = 8;   // p <= 7
 constexpr int MAX_NB = 8;   // phi_0 .. phi_7
