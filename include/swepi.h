@@ -179,7 +179,12 @@ int sw_kiops_phi(sw_ctx_t ctx, const double* q_lin_dev, double dt, double tau_ou
  * place by dt.  The context keeps the history (q_{n-i}, F(q_{n-i})); while it
  * holds fewer than P entries the step is taken by 8 EPI2 substeps of dt/8
  * (Sec. 4 start-up).  The KIOPS size warm-starts from the previous call.
- * st (may be NULL) accumulates the step's KIOPS statistics.  Synchronises. */
+ * st (may be NULL) accumulates the step's KIOPS statistics.  Synchronises.
+ * Errors: SW_EINVAL (order, dt, pointers, options), SW_ENONFINITE (a non-finite
+ * phi-vector or error estimate), SW_EKRYLOV (substep or rejection cap),
+ * SW_ENOMEM / SW_ECUDA.  After an error q_dev and the history may hold part of
+ * the step (the start-up substeps advance q_dev one by one): restart from a
+ * saved state after sw_epi_reset. */
 int sw_epi_step(sw_ctx_t ctx, int order, double dt, double* q_dev, const sw_kiops_opts* opts,
                 sw_kiops_stats* st, void* stream);
 
