@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <stdexcept>
 #include <vector>
 
 #include "swepi_internal.h"
@@ -232,7 +233,18 @@ int sw_init(int n_e, int p, const sw_params* prm, sw_ctx_t* out) {
   c->ne = n_e;
   c->ns = p + 1;
   c->prm = *prm;
-  int rc = build_tables(*c);
+  // the host tables of a very large grid can exceed host memory: no exception
+  // may cross the C ABI
+  int rc;
+  try {
+    rc = build_tables(*c);
+  } catch (const std::bad_alloc&) {
+    rc = SW_ENOMEM;
+  } catch (const std::length_error&) {
+    rc = SW_ENOMEM;
+  } catch (...) {
+    rc = SW_EINVAL;
+  }
   if (rc) {
     sw_free(c);
     return rc;
