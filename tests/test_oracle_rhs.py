@@ -145,6 +145,41 @@ def test_ausm_consistency_and_mirror_symmetry():
     np.testing.assert_allclose(np.real(f_m[2]), -np.real(f_lr[2]), rtol=1e-12, atol=1e-12 * np.abs(f_lr[2]).max())
 
 
+def test_ausm_supersonic_states_take_the_upwind_flux():
+    """With both sides supersonic in the same normal direction (|M| > 1, the
+    branches the subsonic workloads never reach) the split flux is the upwind
+    side's physical flux of Eq. (136): the left one for M > 1, the right one for
+    M < -1; and the Mach and pressure splittings are continuous at |M| = 1."""
+    rng = np.random.default_rng(8)
+    n = 40
+    g = 9.80616
+    sqrtg = rng.uniform(2e13, 4e13, n)
+    hdd = rng.uniform(2e-14, 4e-14, n)
+    h1d, h2d = hdd, rng.uniform(-1e-14, 1e-14, n)
+
+    def state(H, mach, tang):
+        a = np.sqrt(hdd * g * H)
+        return [sqrtg * H, sqrtg * H * mach * a, sqrtg * H * tang * a]
+
+    def phys(q):
+        return [q[1], q[1] * q[1] / q[0] + g * q[0] ** 2 / (2 * sqrtg) * h1d,
+                q[2] * q[1] / q[0] + g * q[0] ** 2 / (2 * sqrtg) * h2d]
+    HL, HR = rng.uniform(7000, 9000, n), rng.uniform(7000, 9000, n)
+    for sgn in (1.0, -1.0):
+        qL = state(HL, sgn * rng.uniform(1.1, 3.0, n), rng.uniform(-0.5, 0.5, n))
+        qR = state(HR, sgn * rng.uniform(1.1, 3.0, n), rng.uniform(-0.5, 0.5, n))
+        f = sw.ausm_flux(qL, qR, 1, sqrtg, hdd, h1d, h2d, g)
+        ref = phys(qL if sgn > 0 else qR)
+        for a, b in zip(f, ref):
+            np.testing.assert_allclose(np.real(a), b, rtol=1e-13, atol=1e-13 * np.max(np.abs(b)))
+    for m in (-1.0, 1.0):
+        for eps in (1e-12, -1e-12):
+            lo, hi = np.array(sw.split_mach(m + eps)), np.array(sw.split_mach(m - eps))
+            assert np.max(np.abs(lo - hi)) < 1e-10
+            lo, hi = np.array(sw.split_pressure(m + eps)), np.array(sw.split_pressure(m - eps))
+            assert np.max(np.abs(lo - hi)) < 1e-10
+
+
 def test_flux_jacobian_eigenvalues():
     """The complex-step Jacobian of the physical flux sqrt(g) T^{mu 1}(q) is
     Eq. (146) with eigenvalues u^1, u^1 +- sqrt(h^11 g_r H) (Eq. 147)."""
