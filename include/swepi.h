@@ -203,6 +203,22 @@ int sw_epi_set_history(sw_ctx_t ctx, int i, const double* q_dev, const double* F
 /* Forget the EPI history and the KIOPS warm start. */
 int sw_epi_reset(sw_ctx_t ctx);
 
+/* The EPI coefficient matrix of order 3..6 as sw_epi_step uses it (Eq. 30,
+ * 36-38; alpha_{m,i} of Eq. 35): *M rows (phi_1 .. phi_M) by *P columns
+ * (R(q_{n-1}) .. R(q_{n-P})), row-major into A_host (at least 16 doubles).
+ * Host only: no CUDA call, no context. */
+int sw_epi_coefficients(int order, int* M, int* P, double* A_host);
+
+/* The DFR operators of degree p (N_s = p + 1, Sec. 3.1) exactly as sw_init
+ * builds them: Gauss-Legendre points xi_host[N_s] (ascending) and weights
+ * w_host[N_s] on [-1, 1]; D_ext_host[N_s][N_s + 2] (row-major), the derivative
+ * at xi_k of the Lagrange basis on the extended nodes {-1, xi_1 .. xi_Ns, +1}
+ * (Eq. 13); l_minus_host, l_plus_host [N_s], the Lagrange basis of xi at -1 and
+ * +1 (the trace rows of Eq. 8).  Any pointer may be NULL.  0 <= p <= 7.  Host
+ * only: no CUDA call, no context. */
+int sw_dfr_operators(int p, double* xi_host, double* w_host, double* D_ext_host, double* l_minus_host,
+                     double* l_plus_host);
+
 /* ---- Learned Krylov control (the adaptive rule stays in charge) ----------
  * A 16 -> 64 -> 64 -> 2 perceptron with GELU hidden layers, BF16 weights and
  * FP32 accumulation predicts, per phi-function call, the initial substep

@@ -466,6 +466,16 @@ int sw_epi_step_host(sw_ctx_t c, int order, double dt, double* q_host, const sw_
   return cuda_status(cudaStreamSynchronize(s));
 }
 
+int sw_epi_coefficients(int order, int* M, int* P, double* A) {
+  const Coefs* cf = coefs_for(order);
+  if (!cf || !M || !P || !A) return SW_EINVAL;
+  *M = cf->M;
+  *P = cf->P;
+  for (int m = 0; m < cf->M; ++m)
+    for (int i = 0; i < cf->P; ++i) A[m * cf->P + i] = cf->a[m][i];
+  return SW_OK;
+}
+
 long long sw_kernel_launches(sw_ctx_t c) { return c ? c->launches : -1; }
 
 // sw_mlp_t is an opaque handle to a swepi::Mlp

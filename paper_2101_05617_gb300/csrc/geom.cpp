@@ -188,6 +188,30 @@ void appc_transform(int pa, int pb, double Z, double T[2][2]) {
   }
 }
 
+// Gauss-Legendre points and weights of ns points, the DFR derivative matrix
+// (Eq. 13: derivatives at the solution points of the Lagrange basis on the
+// extended nodes {-1, xi, +1}, ns x (ns + 2) row-major) and the trace rows
+// l_k(-1), l_k(+1) (Eq. 8).
+void dfr_operators(int ns, std::vector<double>& xi, std::vector<double>& w, std::vector<double>& D,
+                   std::vector<double>& lm, std::vector<double>& lp) {
+  gauss_legendre(ns, xi, w);
+  std::vector<double> ext(ns + 2);
+  ext[0] = -1.0;
+  for (int k = 0; k < ns; ++k) ext[k + 1] = xi[k];
+  ext[ns + 1] = 1.0;
+  std::vector<double> De = bary_diff(ext);
+  D.assign((size_t)ns * (ns + 2), 0.0);
+  for (int k = 0; k < ns; ++k)
+    for (int m = 0; m < ns + 2; ++m) D[(size_t)k * (ns + 2) + m] = De[(k + 1) * (ns + 2) + m];
+  if (ns == 1) {
+    lm.assign(1, 1.0);
+    lp.assign(1, 1.0);
+  } else {
+    lm = bary_eval(xi, -1.0);
+    lp = bary_eval(xi, 1.0);
+  }
+}
+
 }  // namespace
 
 int build_tables(Ctx& c) {
@@ -196,23 +220,16 @@ int build_tables(Ctx& c) {
   c.nelem = 6LL * ne * ne;
   c.nodes = c.nelem * ns * ns;
   c.n = 3 * c.nodes;
-  gauss_legendre(ns, c.xi, c.wq);
-  make_frames(c);
-
   // DFR matrices: extended nodes {-1, xi, +1} (Sec. 3.1)
-  std::vector<double> ext(ns + 2);
-  ext[0] = -1.0;
-  for (int k = 0; k < ns; ++k) ext[k + 1] = c.xi[k];
-  ext[ns + 1] = 1.0;
-  std::vector<double> De = bary_diff(ext);
+  std::vector<double> D, lm, lp;
+  dfr_operators(ns, c.xi, c.wq, D, lm, lp);
+  make_frames(c);
   std::memset(&c.dc, 0, sizeof(c.dc));
   for (int k = 0; k < ns; ++k)
-    for (int m = 0; m < ns + 2; ++m) c.dc.D[k][m] = De[(k + 1) * (ns + 2) + m];
-  if (ns == 1) {
-    c.dc.lm[0] = c.dc.lp[0] = 1.0;
-  } else {
-    std::vector<double> lm = bary_eval(c.xi, -1.0), lp = bary_eval(c.xi, 1.0);
-    for (int k = 0; k < ns; ++k) { c.dc.lm[k] = lm[k]; c.dc.lp[k] = lp[k]; }
+    for (int m = 0; m < ns + 2; ++m) c.dc.D[k][m] = D[(size_t)k * (ns + 2) + m];
+  for (int k = 0; k < ns; ++k) {
+    c.dc.lm[k] = lm[k];
+    c.dc.lp[k] = lp[k];
   }
   c.Dg = (ns == 1) ? std::vector<double>(1, 0.0) : bary_diff(c.xi);
   for (int k = 0; k < ns; ++k)
@@ -450,3 +467,23 @@ int fields_to_state(const Ctx& c, const double* h, const double* hB, const doubl
 }
 
 }  // namespace swepi
+
+extern "C" int sw_dfr_operators(int p, double* xi, double* w, double* D_ext, double* l_minus, double* l_plus) {
+  if (p < 0 || p > swepi::MAX_NS - 1) return SW_EINVAL;
+  const int ns = p + 1;
+  std::vector<double> x, wq, D, lm, lp;
+  try {
+    swepi::dfr_operators(ns, x, wq, D, lm, lp);
+  } catch (...) {
+    return SW_ENOMEM;
+  }
+  for (int k = 0; k < ns; ++k) {
+    if (xi) xi[k] = x[k];
+    if (w) w[k] = wq[k];
+    if (l_minus) l_minus[k] = lm[k];
+    if (l_plus) l_plus[k] = lp[k];
+  }
+  if (D_ext)
+    for (size_t i = 0; i < D.size(); ++i) D_ext[i] = D[i];
+  return SW_OK;
+}

@@ -107,6 +107,8 @@ def lib():
     L.sw_epi_step_host.argtypes = [vp, ip, ctypes.c_double, vp, ctypes.POINTER(sw_kiops_opts),
                                    ctypes.POINTER(sw_kiops_stats), vp]
     L.sw_epi_set_history.argtypes = [vp, ip, vp, vp, vp]
+    L.sw_epi_coefficients.argtypes = [ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), dp]
+    L.sw_dfr_operators.argtypes = [ip, dp, dp, dp, dp, dp]
     L.sw_epi_reset.argtypes = [vp]
     L.sw_kernel_launches.argtypes = [vp]
     L.sw_kernel_launches.restype = ll
@@ -148,7 +150,7 @@ def lib():
 EXPORTED = ["sw_init", "sw_free", "sw_num_unknowns", "sw_grid_info", "sw_node_xyz", "sw_state_from_fields",
             "sw_set_bottom", "sw_rhs", "sw_jvp", "sw_jvp_static_scratch", "sw_linearize", "sw_jvp_linearized",
             "sw_set_jvp_mode", "sw_kiops_phi", "sw_epi_step", "sw_epi_step_host", "sw_epi_set_history",
-            "sw_epi_reset", "sw_kernel_launches", "sw_profile", "sw_profile_kinds", "sw_profile_read", "sw_fp64_fma_peak",
+            "sw_epi_reset", "sw_epi_coefficients", "sw_dfr_operators", "sw_kernel_launches", "sw_profile", "sw_profile_kinds", "sw_profile_read", "sw_fp64_fma_peak",
             "sw_status_str", "sw_mlp_create", "sw_mlp_free", "sw_mlp_set_params", "sw_mlp_get_params",
             "sw_mlp_forward", "sw_mlp_gradient", "sw_mlp_train", "sw_set_controller", "sw_kiops_log",
             "sw_kiops_log_clear", "sw_diagnostics", "sw_error_norms", "sw_ens_create", "sw_ens_free",
@@ -300,6 +302,24 @@ def sw_epi_step_host(ctx, order, dt, q_host, opts=None, stream=None):
     _check("sw_epi_step_host", lib().sw_epi_step_host(ctx, int(order), float(dt), _host_ptr(q_host, n),
                                                       ctypes.byref(o), ctypes.byref(st), _stream(stream)))
     return st.as_dict()
+
+
+def sw_epi_coefficients(order):
+    """The library's EPI coefficient matrix of `order` (M x P numpy array); host only."""
+    M, P = ctypes.c_int(), ctypes.c_int()
+    A = (ctypes.c_double * 16)()
+    _check("sw_epi_coefficients", lib().sw_epi_coefficients(int(order), ctypes.byref(M), ctypes.byref(P), A))
+    return np.array(A[:M.value * P.value]).reshape(M.value, P.value)
+
+
+def sw_dfr_operators(p):
+    """The library's DFR operators of degree p: (xi, w, D_ext, l_minus, l_plus); host only."""
+    ns = int(p) + 1
+    xi, w, lm, lp = (np.zeros(ns) for _ in range(4))
+    D = np.zeros((ns, ns + 2))
+    ptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))   # noqa: E731
+    _check("sw_dfr_operators", lib().sw_dfr_operators(int(p), ptr(xi), ptr(w), ptr(D), ptr(lm), ptr(lp)))
+    return xi, w, D, lm, lp
 
 
 def sw_epi_set_history(ctx, i, q, F=None, stream=None):
