@@ -219,6 +219,25 @@ int sw_epi_coefficients(int order, int* M, int* P, double* A_host);
 int sw_dfr_operators(int p, double* xi_host, double* w_host, double* D_ext_host, double* l_minus_host,
                      double* l_plus_host);
 
+/* The node coefficients sw_init tabulates, at any points (X, Y) = (tan x^1,
+ * tan x^2) of one panel (0..5) of the grid rotated by params: out_host[k * npts
+ * + i] for k = 0..12 = g_r h^11/(2 sqrt g), g_r h^12/(2 sqrt g), g_r h^22/(2
+ * sqrt g) (App. D pressure term; Eq. 67-70), -2 Gamma^1_{01}, -2 Gamma^1_{02},
+ * -2 Gamma^2_{01}, -2 Gamma^2_{02} (Eq. 71-74, the panel frame giving the
+ * Coriolis bracket), Gamma^1_11, 2 Gamma^1_12, 2 Gamma^2_12, Gamma^2_22 (Eq.
+ * 75-80), and two topography entries (zero here: they depend on the bottom).
+ * Host only: no CUDA call, no context. */
+int sw_node_coefficients(const sw_params* params, int panel, int npts, const double* X_host,
+                         const double* Y_host, double* out_host);
+
+/* Interface k (0..11) of the cube as the library connects it: panels pa, pb,
+ * their edges (0 = x^1 = -pi/4, 1 = x^1 = +pi/4, 2 = x^2 = -pi/4, 3 = x^2 =
+ * +pi/4), rev = 1 when the along-edge coordinates run opposite, and T_host (2x2
+ * row-major) = the App. C transform (Eq. 100-135) taking contravariant
+ * components on panel pb to panel pa at the point with along-edge coordinate t
+ * on panel pa.  Any output may be NULL.  Host only. */
+int sw_interface_transform(int k, double t, int* pa, int* ea, int* pb, int* eb, int* rev, double* T_host);
+
 /* ---- Learned Krylov control (the adaptive rule stays in charge) ----------
  * A 16 -> 64 -> 64 -> 2 perceptron with GELU hidden layers, BF16 weights and
  * FP32 accumulation predicts, per phi-function call, the initial substep

@@ -2,6 +2,7 @@
 // (paper Sec. 3, App. B, App. C).  Everything here runs once in sw_init.
 #include <cmath>
 #include <cstring>
+#include <new>
 
 #include "swepi_internal.h"
 
@@ -212,6 +213,30 @@ void dfr_operators(int ns, std::vector<double>& xi, std::vector<double>& w, std:
   }
 }
 
+// Node coefficients of one point (X, Y) = (tan x^1, tan x^2) of panel p: the
+// pressure factors g_r h^ij / (2 sqrt g), -2 Gamma^i_{0j} (Eq. 71-74, with the
+// bracket sin(latitude) * delta = z-component of c + X e1 + Y e2) and the
+// spatial Christoffel symbols (Eq. 75-80); entry k goes to out[k * stride].
+// The topography entries NC_B1, NC_B2 are left alone.
+void node_coefficients(const Ctx& c, int p, double X, double Y, double* out, long long stride) {
+  const double a = c.prm.radius, gr = c.prm.gravity, om = c.prm.omega;
+  const double cz = c.frame[p][0][2], e1z = c.frame[p][1][2], e2z = c.frame[p][2][2];
+  double d2 = 1 + X * X + Y * Y;
+  Metric m = metric_at(X, Y, a);
+  out[NC_C11 * stride] = 0.5 * gr * m.h11 / m.sqrtg;
+  out[NC_C12 * stride] = 0.5 * gr * m.h12 / m.sqrtg;
+  out[NC_C22 * stride] = 0.5 * gr * m.h22 / m.sqrtg;
+  double s = cz + X * e1z + Y * e2z;
+  out[NC_K11 * stride] = -2.0 * om * X * Y * s / d2;
+  out[NC_K12 * stride] = 2.0 * om * (1 + Y * Y) * s / d2;
+  out[NC_K21 * stride] = -2.0 * om * (1 + X * X) * s / d2;
+  out[NC_K22 * stride] = 2.0 * om * X * Y * s / d2;
+  out[NC_G1A * stride] = 2.0 * X * Y * Y / d2;
+  out[NC_G1B * stride] = -2.0 * Y * (1 + Y * Y) / d2;
+  out[NC_G2A * stride] = -2.0 * X * (1 + X * X) / d2;
+  out[NC_G2B * stride] = 2.0 * X * X * Y / d2;
+}
+
 }  // namespace
 
 int build_tables(Ctx& c) {
@@ -237,36 +262,19 @@ int build_tables(Ctx& c) {
   c.dc.two_over_dx = 2.0 / c.dx;
   c.dc.gravity = c.prm.gravity;
 
-  const double a = c.prm.radius, gr = c.prm.gravity, om = c.prm.omega;
+  const double a = c.prm.radius, gr = c.prm.gravity;
 
   // node coefficients
   c.node_coef_h.assign((size_t)NC_COUNT * c.nodes, 0.0);
-  auto NCs = [&](int k, long long i) -> double& { return c.node_coef_h[(size_t)k * c.nodes + i]; };
-  for (int p = 0; p < 6; ++p) {
-    const double cz = c.frame[p][0][2], e1z = c.frame[p][1][2], e2z = c.frame[p][2][2];
+  for (int p = 0; p < 6; ++p)
     for (int e2 = 0; e2 < ne; ++e2)
       for (int e1 = 0; e1 < ne; ++e1)
         for (int k2 = 0; k2 < ns; ++k2)
           for (int k1 = 0; k1 < ns; ++k1) {
             long long i = elem_index(c, p, e2, e1) * ns * ns + k2 * ns + k1;
             double X = std::tan(line_coord(c, e1, k1)), Y = std::tan(line_coord(c, e2, k2));
-            double d2 = 1 + X * X + Y * Y;
-            Metric m = metric_at(X, Y, a);
-            NCs(NC_C11, i) = 0.5 * gr * m.h11 / m.sqrtg;
-            NCs(NC_C12, i) = 0.5 * gr * m.h12 / m.sqrtg;
-            NCs(NC_C22, i) = 0.5 * gr * m.h22 / m.sqrtg;
-            // sin(latitude) * delta: z-component of c + X e1 + Y e2 (Eq. 71-74 bracket)
-            double s = cz + X * e1z + Y * e2z;
-            NCs(NC_K11, i) = -2.0 * om * X * Y * s / d2;
-            NCs(NC_K12, i) = 2.0 * om * (1 + Y * Y) * s / d2;
-            NCs(NC_K21, i) = -2.0 * om * (1 + X * X) * s / d2;
-            NCs(NC_K22, i) = 2.0 * om * X * Y * s / d2;
-            NCs(NC_G1A, i) = 2.0 * X * Y * Y / d2;
-            NCs(NC_G1B, i) = -2.0 * Y * (1 + Y * Y) / d2;
-            NCs(NC_G2A, i) = -2.0 * X * (1 + X * X) / d2;
-            NCs(NC_G2B, i) = 2.0 * X * X * Y / d2;
+            node_coefficients(c, p, X, Y, &c.node_coef_h[(size_t)i], c.nodes);
           }
-  }
 
   // face lines: interior x1 faces, interior x2 faces, then panel interfaces
   std::vector<FaceLine> lines;
@@ -485,5 +493,38 @@ extern "C" int sw_dfr_operators(int p, double* xi, double* w, double* D_ext, dou
   }
   if (D_ext)
     for (size_t i = 0; i < D.size(); ++i) D_ext[i] = D[i];
+  return SW_OK;
+}
+
+extern "C" int sw_node_coefficients(const sw_params* prm, int panel, int npts, const double* X, const double* Y,
+                                    double* out) {
+  if (!prm || panel < 0 || panel > 5 || npts < 0 || (npts > 0 && (!X || !Y || !out))) return SW_EINVAL;
+  swepi::Ctx* c = new (std::nothrow) swepi::Ctx();
+  if (!c) return SW_ENOMEM;
+  c->prm = *prm;
+  swepi::make_frames(*c);
+  for (int k = 0; k < swepi::NC_COUNT; ++k)
+    for (int i = 0; i < npts; ++i) out[(long long)k * npts + i] = 0.0;
+  for (int i = 0; i < npts; ++i) swepi::node_coefficients(*c, panel, X[i], Y[i], out + i, npts);
+  delete c;
+  return SW_OK;
+}
+
+extern "C" int sw_interface_transform(int k, double t, int* pa, int* ea, int* pb, int* eb, int* rev, double* T) {
+  if (k < 0 || k > 11) return SW_EINVAL;
+  const swepi::Iface& f = swepi::kIfaces[k];
+  if (pa) *pa = f.pa;
+  if (ea) *ea = f.ea;
+  if (pb) *pb = f.pb;
+  if (eb) *eb = f.eb;
+  if (rev) *rev = f.rev;
+  if (T) {
+    double M[2][2];
+    swepi::appc_transform(f.pa, f.pb, std::tan(t), M);
+    T[0] = M[0][0];
+    T[1] = M[0][1];
+    T[2] = M[1][0];
+    T[3] = M[1][1];
+  }
   return SW_OK;
 }

@@ -109,6 +109,9 @@ def lib():
     L.sw_epi_set_history.argtypes = [vp, ip, vp, vp, vp]
     L.sw_epi_coefficients.argtypes = [ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), dp]
     L.sw_dfr_operators.argtypes = [ip, dp, dp, dp, dp, dp]
+    L.sw_node_coefficients.argtypes = [ctypes.POINTER(sw_params), ip, ip, dp, dp, dp]
+    ipp = ctypes.POINTER(ctypes.c_int)
+    L.sw_interface_transform.argtypes = [ip, ctypes.c_double, ipp, ipp, ipp, ipp, ipp, dp]
     L.sw_epi_reset.argtypes = [vp]
     L.sw_kernel_launches.argtypes = [vp]
     L.sw_kernel_launches.restype = ll
@@ -150,7 +153,8 @@ def lib():
 EXPORTED = ["sw_init", "sw_free", "sw_num_unknowns", "sw_grid_info", "sw_node_xyz", "sw_state_from_fields",
             "sw_set_bottom", "sw_rhs", "sw_jvp", "sw_jvp_static_scratch", "sw_linearize", "sw_jvp_linearized",
             "sw_set_jvp_mode", "sw_kiops_phi", "sw_epi_step", "sw_epi_step_host", "sw_epi_set_history",
-            "sw_epi_reset", "sw_epi_coefficients", "sw_dfr_operators", "sw_kernel_launches", "sw_profile", "sw_profile_kinds", "sw_profile_read", "sw_fp64_fma_peak",
+            "sw_epi_reset", "sw_epi_coefficients", "sw_dfr_operators", "sw_node_coefficients",
+            "sw_interface_transform", "sw_kernel_launches", "sw_profile", "sw_profile_kinds", "sw_profile_read", "sw_fp64_fma_peak",
             "sw_status_str", "sw_mlp_create", "sw_mlp_free", "sw_mlp_set_params", "sw_mlp_get_params",
             "sw_mlp_forward", "sw_mlp_gradient", "sw_mlp_train", "sw_set_controller", "sw_kiops_log",
             "sw_kiops_log_clear", "sw_diagnostics", "sw_error_norms", "sw_ens_create", "sw_ens_free",
@@ -320,6 +324,29 @@ def sw_dfr_operators(p):
     ptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))   # noqa: E731
     _check("sw_dfr_operators", lib().sw_dfr_operators(int(p), ptr(xi), ptr(w), ptr(D), ptr(lm), ptr(lp)))
     return xi, w, D, lm, lp
+
+
+def sw_node_coefficients(rotation, panel, X, Y, radius=6.37122e6, gravity=9.80616, omega=7.292e-5):
+    """The library's 13 node coefficients at points (X, Y) of a panel: [13, npts]; host only."""
+    X = np.ascontiguousarray(X, dtype=np.float64).ravel()
+    Y = np.ascontiguousarray(Y, dtype=np.float64).ravel()
+    if X.size != Y.size:
+        raise ValueError("X and Y differ in size")
+    prm = sw_params(radius, gravity, omega, rotation[0], rotation[1], rotation[2], 0)
+    out = np.zeros((13, X.size))
+    ptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))   # noqa: E731
+    _check("sw_node_coefficients", lib().sw_node_coefficients(ctypes.byref(prm), int(panel), X.size, ptr(X), ptr(Y),
+                                                              ptr(out)))
+    return out
+
+
+def sw_interface_transform(k, t):
+    """Interface k of the library: ((pa, ea, pb, eb, rev), T[2, 2] at along-edge coordinate t); host only."""
+    v = [ctypes.c_int() for _ in range(5)]
+    T = np.zeros(4)
+    _check("sw_interface_transform", lib().sw_interface_transform(
+        int(k), float(t), *[ctypes.byref(x) for x in v], T.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return tuple(x.value for x in v), T.reshape(2, 2)
 
 
 def sw_epi_set_history(ctx, i, q, F=None, stream=None):
