@@ -86,7 +86,9 @@ def dist_setup(args):
         backend = "nccl" if torch.cuda.is_available() and args.impl == "gpu" else "gloo"
         if backend == "nccl":
             torch.cuda.set_device(local)
-        dist.init_process_group(backend)
+        # rank 0 alone runs the one-rank extras while the others wait at the final barrier
+        import datetime
+        dist.init_process_group(backend, timeout=datetime.timedelta(minutes=30))
         pg = dist
     return world, rank, local, pg
 
@@ -664,7 +666,7 @@ def main():
                "roofline": roofline,
                "forms": {"timed": ("learned control + FP64 split complex-step JVP" if ctl is not None
                                    else "plain control + FP64 split complex-step JVP")}}
-        if not args.no_forms:
+        if not args.no_forms and world == 1:   # replicas (N > 1) time the step only
             from paper_2101_05617_gb300 import learned
 
             only = {x.strip() for x in args.only_forms.split(",") if x.strip()}
