@@ -67,7 +67,7 @@ def trace_rows(ns):
 
 
 def collocation_derivative_matrix(ns):
-    """Dg[k, l] = ell'_l(xi_k) on the Gauss-Legendre points alone (used for the
+    """Dg[k, l] = ell'_l(xi_k) on the Gauss-Legendre points alone (Sec. 3.1 basis; used for the
     bottom-topography gradient, which the paper does not specify)."""
     xi, _ = gauss_legendre(ns)
     return lagrange_derivatives(xi, xi)

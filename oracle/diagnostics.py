@@ -20,6 +20,7 @@ def integral(grid, psi):
 
 
 def primitives(grid, q):
+    """H = q^0 / sqrt(g) and u^i = q^i / q^0 (the state of Eq. 1-2, App. D)."""
     q = np.asarray(q).reshape((3,) + grid.x1.shape)
     H = q[0] / grid.m['sqrtg']
     u1, u2 = q[1] / q[0], q[2] / q[0]

@@ -31,6 +31,7 @@ N_SUB_STARTUP = 8
 
 
 def history_length(order):
+    """P, the number of past states q_{n-1} .. q_{n-P} the scheme of Eq. (34)-(38) uses."""
     return 0 if order == 2 else len(COEFFS[order][0])
 
 
@@ -61,6 +62,8 @@ class EPI:
         return q + self._phi(q, dt, [np.zeros_like(q), dt * F]), F
 
     def step(self, q, dt):
+        """q_{n+1} by Eq. (34)-(35) with the remainders of Eq. (33) (EPI2 substeps of
+        Eq. 25 while the history is short: the start-up of Sec. 4)."""
         q = np.asarray(q, dtype=float)
         P = history_length(self.order)
         if len(self.history) < P:

@@ -11,6 +11,8 @@ from . import geometry as geo
 
 
 def state_from_fields(grid, h, hB, V):
+    """q of Eq. (1)-(2) (q^0 = sqrt(g) H, q^i = q^0 u^i, App. D) from h, h_B and the
+    Cartesian wind at the nodes, u^i = h^{ij} (V . t_j) with Eq. (67)-(69)."""
     shp = grid.x1.shape
     h = np.asarray(h, dtype=float).reshape(shp)
     hB = np.asarray(hB, dtype=float).reshape(shp)
@@ -30,7 +32,7 @@ def state_from_fields(grid, h, hB, V):
 
 
 def wind_from_state(grid, q):
-    """Inverse map (diagnostics): Cartesian wind and H from q."""
+    """Inverse map of state_from_fields (diagnostics of Sec. 5): Cartesian wind and H from q."""
     shp = grid.x1.shape
     q = np.asarray(q).reshape((3,) + shp)
     H = q[0] / grid.m['sqrtg']

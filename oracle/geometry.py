@@ -77,7 +77,8 @@ def xy_from_lonlat(lam, phi, lam_p, phi_p, alpha_p):
 
 
 def unit_position(x1, x2, frame):
-    """Unit vector of the point (x1, x2) of a panel with frame (c, e1, e2)."""
+    """Unit vector of the point (x1, x2) of a panel with frame (c, e1, e2)
+    (Eq. 59-60 inverted: X = tan x^1, Y = tan x^2 along e1, e2 from the centre c)."""
     c, e1, e2 = frame
     X, Y = np.tan(x1), np.tan(x2)
     delta = np.sqrt(1 + X * X + Y * Y)
@@ -86,7 +87,7 @@ def unit_position(x1, x2, frame):
 
 
 def tangent_vectors(x1, x2, frame, a=RADIUS):
-    """Covariant basis d(a r)/dx^1, d(a r)/dx^2 (3-vectors) by differentiating
+    """Covariant basis d(a r)/dx^1, d(a r)/dx^2 (3-vectors; App. B, whose dot products are Eq. 64-66) by differentiating
     a (c + X e1 + Y e2)/delta with X = tan x^1, Y = tan x^2."""
     c, e1, e2 = frame
     X, Y = np.tan(x1), np.tan(x2)
@@ -162,7 +163,7 @@ INTERFACES = [
 
 
 def edge_coords(edge, t):
-    """(x^1, x^2) of the points with along-edge coordinate t on an edge."""
+    """(x^1, x^2) of the points with along-edge coordinate t on an edge (App. C)."""
     q = np.pi / 4
     t = np.asarray(t, dtype=float)
     if edge == 'E':
@@ -175,7 +176,8 @@ def edge_coords(edge, t):
 
 
 def contravariant_jacobian(x1, x2, frame_from, frame_to, a=RADIUS):
-    """d x^i_(to) / d x^j_(from) at points given in 'from' coordinates.
+    """d x^i_(to) / d x^j_(from) at points given in 'from' coordinates (the
+    contravariant transforms that App. C prints as Eq. 100-135).
 
     Plain definition: a contravariant vector A^j_(from) is the 3-vector
     V = A^j t_j(from); its components on panel 'to' are e^i_(to) . V with the

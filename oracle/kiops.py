@@ -54,7 +54,8 @@ class KiopsError(RuntimeError):
 
 def kiops(tau_out, matvec, b, tol=1e-10, m_init=10, m_min=10, m_max=128, iop=2,
           tau_init=None, max_substeps=10000, max_rejects=10000, trace=None):
-    """Return (w, stats) with w = sum_k tau_out^k phi_k(tau_out A) b_k.
+    """Return (w, stats) with w = sum_k tau_out^k phi_k(tau_out A) b_k (Eq. 29; the
+    steps listed in the module docstring).
 
     matvec(x) returns A x for a length-n vector x; b is a list [b_0, .., b_p]
     (p >= 0; p == 0 is padded with a zero b_1).  `trace`, if a list, receives one

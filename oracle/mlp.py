@@ -3,7 +3,12 @@ infrastructure only): a 16 -> 64 -> 64 -> 2 perceptron with GELU hidden
 activations, x Phi(x) with Phi the standard normal distribution function
 (scipy.special.erf as a library primitive), mean squared error on standardised
 targets, and its gradient by the chain rule written out layer by layer.
-Parameter layout: W1[64][16], b1[64], W2[64][64], b2[64], W3[2][64], b3[2]."""
+Parameter layout: W1[64][16], b1[64], W2[64][64], b2[64], W3[2][64], b3[2].
+
+The network is an extension of the method: its only counterpart in the paper is
+the phi-function solver's choice of the initial substep and Krylov size (Sec. 4,
+reference [10]), so the functions below follow no passage of the paper; they
+are the textbook definitions written out."""
 import numpy as np
 from scipy.special import erf
 
@@ -13,6 +18,8 @@ NPARAM = sum(int(np.prod(s)) for _, s in SIZES)
 
 
 def unpack(theta):
+    """Split the flat parameter vector by the layout above (the learned choice of
+    the initial KIOPS substep, Sec. 4; the network has no paper counterpart)."""
     theta = np.asarray(theta, dtype=np.float64)
     out, k = {}, 0
     for name, shape in SIZES:
@@ -23,14 +30,17 @@ def unpack(theta):
 
 
 def gelu(x):
+    """x Phi(x), Phi the standard normal distribution function."""
     return 0.5 * x * (1.0 + erf(x / np.sqrt(2.0)))
 
 
 def gelu_grad(x):
+    """d/dx of x Phi(x) = Phi(x) + x phi(x)."""
     return 0.5 * (1.0 + erf(x / np.sqrt(2.0))) + x * np.exp(-0.5 * x * x) / np.sqrt(2.0 * np.pi)
 
 
 def standardise(X, norm):
+    """(X - mean) / std with the stored input normalisation."""
     norm = np.asarray(norm, dtype=np.float64)
     return (np.asarray(X, dtype=np.float64) - norm[:NI]) / norm[NI:2 * NI]
 

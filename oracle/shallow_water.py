@@ -72,14 +72,15 @@ class Grid:
         return 3 * 6 * self.ne ** 2 * self.ns ** 2
 
     def node_xyz(self):
-        """Unit position vectors of all nodes: [3, 6, ne, ne, ns, ns]."""
+        """Unit position vectors of all nodes (App. B): [3, 6, ne, ne, ns, ns]."""
         out = np.empty((3,) + self.x1.shape)
         for p in range(6):
             out[:, p] = geo.unit_position(self.x1[p], self.x2[p], self.frames[p])
         return out
 
     def set_bottom(self, hB):
-        """Nodal h_B and its element-local collocation gradient."""
+        """Nodal h_B and its element-local collocation gradient (the bottom term of Eq. 2; reading in the
+        module docstring)."""
         self.hB = np.asarray(hB, dtype=float).reshape(self.x1.shape)
         s = 2.0 / self.dx
         self.dhB1 = s * np.einsum('kl,pefjl->pefjk', self.Dg, self.hB)    # d/dx^1 along k1
@@ -91,13 +92,14 @@ class Grid:
 
     # --------------------------------------------------------------- faces
     def face_metric_x1(self, i_face):
-        """Metric on the x^1 = const line i_face (0..ne) at all (e2, k2) points."""
+        """Metric (Eq. 67-70, evaluated at the point) on the x^1 = const line i_face (0..ne) at all (e2, k2) points."""
         x1 = -np.pi / 4 + i_face * self.dx
         X = np.tan(np.full(self.x_line.shape, x1))
         Y = np.tan(self.x_line)
         return geo.metric(X, Y, self.a)
 
     def face_metric_x2(self, i_face):
+        """Metric (Eq. 67-70, evaluated at the point) on the x^2 = const line i_face (0..ne)."""
         x2 = -np.pi / 4 + i_face * self.dx
         X = np.tan(self.x_line)
         Y = np.tan(np.full(self.x_line.shape, x2))
@@ -295,7 +297,7 @@ def rhs(grid, q):
 
 
 def rhs_real(grid, q):
-    """F(q) for a real state (the real part of the complex evaluation)."""
+    """F(q) of Eq. (1)-(2) (Sec. 3) for a real state (the real part of the complex evaluation)."""
     return np.real(rhs(grid, q))
 
 

@@ -15,6 +15,7 @@ import numpy as np
 
 
 class SemilinearParabolic:
+    """The semilinear parabolic problem of Sec. 5.1 (readings in the module docstring)."""
     def __init__(self, n=50):
         self.n = n
         self.h = 1.0 / (n + 1)
@@ -32,16 +33,20 @@ class SemilinearParabolic:
         return self.h * np.sum(u)
 
     def phi(self, t):
+        """The forcing of the semilinear problem of Sec. 5.1 (built from the discrete operators)."""
         return np.exp(t) * (self.s0 - self.L0 - self.T0)
 
     def exact(self, t):
+        """The exact solution x (1 - x) e^t of Sec. 5.1 (and t)."""
         return np.concatenate([self.s0 * np.exp(t), [t]])
 
     def rhs(self, y):
+        """Right-hand side of the semi-discrete problem (Sec. 5.1)."""
         u, t = y[:-1], y[-1]
         return np.concatenate([self._lap(u) + self._int(u) + self.phi(t), [1.0]])
 
     def jvp(self, y, v):
+        """Exact Jacobian times v (Sec. 5.1 uses the exact Jacobian)."""
         vu, vt = v[:-1], v[-1]
         t = y[-1]
         return np.concatenate([self._lap(vu) + self._int(vu) + self.phi(t) * vt, [0.0]])
@@ -74,14 +79,16 @@ class AdvectionDiffusionReaction:
         return (self.eps * lap - self.alpha * adv).ravel()
 
     def rhs(self, u):
+        """Right-hand side of the semi-discrete problem (Sec. 5.1)."""
         return self._lin(u) + self.gamma * u * (u - 0.5) * (1.0 - u)
 
     def jvp(self, u, v):
+        """Exact Jacobian times v (Sec. 5.1 uses the exact Jacobian)."""
         return self._lin(v) + self.gamma * (-3.0 * u * u + 3.0 * u - 0.5) * v
 
     def jacobian(self, u):
         """The Jacobian as a sparse matrix, assembled from the 1-D stencils
-        (for an implicit reference solver; equal to jvp)."""
+        (for an implicit reference solver as in Sec. 5.1; equal to jvp)."""
         import scipy.sparse as sps
         m, h = self.m, self.h
         e = np.ones(m)
@@ -119,14 +126,16 @@ class Burgers:
         return (P[2:] - P[:-2]) / (2.0 * self.h)
 
     def rhs(self, u):
+        """Right-hand side of the semi-discrete problem (Sec. 5.1)."""
         return self.eps * self._d2(u) - 0.5 * self._d1(u * u)
 
     def jvp(self, u, v):
+        """Exact Jacobian times v (Sec. 5.1 uses the exact Jacobian)."""
         return self.eps * self._d2(v) - self._d1(u * v)
 
     def jacobian(self, u):
-        """The Jacobian as a sparse matrix (for an implicit reference solver;
-        equal to jvp)."""
+        """The Jacobian as a sparse matrix (for an implicit reference solver as in
+        Sec. 5.1; equal to jvp)."""
         import scipy.sparse as sps
         n, h = self.n, self.h
         e = np.ones(n)
