@@ -7,8 +7,10 @@ consecutive N_e for N_s = 3..6.
 
 Not a test (it takes minutes): run as
     python -m tests.convergence_study [hours] [n_e list]
-e.g. `python -m tests.convergence_study 24 10,20`.  One spawned process per
-(N_e, N_s); uses the oracle only."""
+e.g. `python -m tests.convergence_study 24 10,20`, or for the p-refinement of
+Fig. 3a (N_e = 10, N_s = 3..8)
+    python -m tests.convergence_study [hours] p
+One spawned process per (N_e, N_s); uses the oracle only."""
 import multiprocessing as mp
 import os
 import sys
@@ -58,6 +60,11 @@ def run_jobs(jobs):
 
 def main():
     hours = float(sys.argv[1]) if len(sys.argv) > 1 else 24.0
+    if len(sys.argv) > 2 and sys.argv[2] == "p":
+        res = run_jobs([(10, ns, 6, 3600.0, hours) for ns in range(3, 9)])
+        for ne, ns, e, sec in res:
+            print(f"N_e={ne:3d} N_s={ns}  L1 {e[0]:.3e}  L2 {e[1]:.3e}  Linf {e[2]:.3e}  ({sec:.0f} s)")
+        return
     nes = [int(x) for x in sys.argv[2].split(",")] if len(sys.argv) > 2 else [5, 10]
     jobs = [(ne, ns, 6, 3600.0, hours) for ns in (3, 4, 5, 6) for ne in nes]
     res = run_jobs(jobs)
