@@ -30,7 +30,9 @@
  *
  * Errors: every int-returning call returns SW_OK (0) or a negative status;
  * no exception crosses the ABI; sw_status_str() names the status.  A context
- * is used by one host thread at a time.
+ * is used by one host thread at a time, with the device it was created on
+ * current: a call that takes a context and launches work returns SW_EINVAL,
+ * before any launch, when another device is current.
  */
 #ifndef SWEPI_H
 #define SWEPI_H
@@ -52,7 +54,10 @@ typedef struct sw_ctx* sw_ctx_t;
 
 /* Physical constants and grid rotation (App. B: panel 0 centred at longitude
  * lambda0, latitude phi0, rotated by alpha0; the other five panels follow the
- * cube, Eq. 81-95).  precision: 0 = FP64 throughout (the only value accepted). */
+ * cube, Eq. 81-95).  precision: 0 = FP64 throughout (the split FP64 JVP of
+ * sw_set_jvp_mode 1); 1 = the complex64-bulk form from the start (the Krylov
+ * JVPs' imaginary half in FP32, everything else FP64: sw_set_jvp_mode 2); other
+ * values are rejected.  sw_set_jvp_mode may change the form later. */
 typedef struct {
   double radius;   /* a, m */
   double gravity;  /* g_r, m s^-2 (Eq. 51) */
@@ -104,16 +109,27 @@ int sw_node_xyz(sw_ctx_t ctx, double* xyz_host);
 int sw_state_from_fields(sw_ctx_t ctx, const double* h_host, const double* hB_host,
                          const double* V_host, double* q_host);
 
-/* Bottom height h_B at the nodes (host array, canonical node order): the
- * topography source of Eq. (2) uses its element-local collocation gradient. */
-int sw_set_bottom(sw_ctx_t ctx, const double* hB_host);
+/* Bottom height h_B at the nodes (nodes = n/3 doubles, canonical node order):
+ * the topography source of Eq. (2) uses its element-local collocation
+ * gradient.  sw_set_bottom takes a DEVICE pointer (on the context's device;
+ * anything else is SW_EINVAL), copies it to the host and builds the
+ * topography coefficients there, as sw_set_bottom_host does from a host array.
+ * Both are initialisation calls: they synchronise the device, and the next
+ * RHS/JVP/EPI call uses the new bottom. */
+int sw_set_bottom(sw_ctx_t ctx, const double* hB_dev);
+int sw_set_bottom_host(sw_ctx_t ctx, const double* hB_host);
 
 /* F(q): the DFR right-hand side of Eq. (1)-(2) (Sec. 3, Eq. 14 per direction,
  * AUSM interface flux of App. D).  q_dev, F_dev: n doubles, may not alias. */
 int sw_rhs(sw_ctx_t ctx, const double* q_dev, double* F_dev, void* stream);
 
 /* Complex-step Jacobian-vector product, Eq. (28): Jv = Im F(q + i eps v) / eps.
- * eps > 0 (1e-30 is typical).  Jv_dev may not alias q_dev or v_dev. */
+ * The kernels carry the imaginary parts to first order (they drop the
+ * O(eps^2) cross terms), so the result is the Jacobian-vector product J(q) v
+ * itself, the eps -> 0 limit of the quotient; it equals the quotient of Eq.
+ * (28) to FP64 rounding whenever eps max|v^mu| / |q^mu| is below ~1e-8 (true
+ * for eps = 1e-30 and for the paper's eps ~ 1.5e-8 with v scaled like q).
+ * eps > 0 and finite, else SW_EINVAL.  Jv_dev may not alias q_dev or v_dev. */
 int sw_jvp(sw_ctx_t ctx, const double* q_dev, const double* v_dev, double eps,
            double* Jv_dev, void* stream);
 
@@ -126,10 +142,13 @@ int sw_jvp(sw_ctx_t ctx, const double* q_dev, const double* v_dev, double eps,
  * 16 MiB device array inside the library (held by every GPU that loads the
  * library until exit), so it serves grids with 6 n_e^2 * 12 * (p+1) <= 2^21
  * (e.g. n_e = 60, p = 5) and returns SW_ESCRATCH for larger ones.  The first
- * call on a device looks up the array's device address (once per device, for
- * the current device); make that first call before any stream capture.  All
- * calls share the array: calls that overlap on the GPU race.  Arguments and
- * results as sw_jvp. */
+ * call on a device looks up the array's device address (once per device, with
+ * that device current); make that first call before any stream capture.  The
+ * address stays cached for the process's primary context: do not use this
+ * call across a cudaDeviceReset.  With a device current other than the
+ * context's it returns SW_EINVAL before any launch.  All calls share the
+ * array: calls that overlap on the GPU race.  Arguments and results as
+ * sw_jvp. */
 int sw_jvp_static_scratch(sw_ctx_t ctx, const double* q_dev, const double* v_dev, double eps,
                           double* Jv_dev, void* stream);
 
@@ -197,10 +216,17 @@ int sw_epi_step_host(sw_ctx_t ctx, int order, double dt, double* q_host, const s
                      sw_kiops_stats* st, void* stream);
 
 /* Seed history entry i (1 = most recent) with (q_{n-i}, F(q_{n-i})) device
- * vectors (copied); F_dev NULL computes it.  i <= 4. */
+ * vectors (copied); F_dev NULL computes it.  i <= 4.  The multistep schemes of
+ * Eq. (34)-(38) read the remainders R(q_{n-i}) of Eq. (33) at the previous
+ * states; Sec. 4 (the paragraph after Eq. 38) leaves open how the starting
+ * values are obtained and computes them with EPI2 at a smaller step, which
+ * sw_epi_step does while the history is short.  This call supplies them
+ * instead (e.g. from a finer reference run, for order tests). */
 int sw_epi_set_history(sw_ctx_t ctx, int i, const double* q_dev, const double* F_dev, void* stream);
 
-/* Forget the EPI history and the KIOPS warm start. */
+/* Forget the EPI history (the previous states of Eq. 33-38) and the KIOPS
+ * warm start, so that the next sw_epi_step starts again with the EPI2 start-up
+ * of Sec. 4 (the paragraph after Eq. 38). */
 int sw_epi_reset(sw_ctx_t ctx);
 
 /* The EPI coefficient matrix of order 3..6 as sw_epi_step uses it (Eq. 30,
@@ -331,6 +357,17 @@ int sw_ens_epi_run(sw_ens_t ens, int steps, const int* orders_host, const double
                    double* const* q_dev_host, const sw_kiops_opts* opts, sw_kiops_stats* stats_host,
                    void* stream);
 int sw_ens_stats_read(sw_ens_t ens, sw_ens_stats* out);
+/* Failure-path test hook (no paper counterpart).  The batched kernel's tasks
+ * wait, bounded, for their member's previous phase; every such wait ends by
+ * construction, and the bound only turns a broken invariant into SW_ETIMEOUT
+ * instead of a hang.  This call sets that bound to limit_s seconds (0 = the
+ * default 2 s, at most 2) and adds `extra` (0 or 1) to every wait target: with
+ * extra = 1 no wait can be satisfied, so the next sw_ens_epi_run / sw_ens_tune
+ * launch completes after one bound and the call returns SW_ETIMEOUT (the
+ * members' states are then meaningless: restore them and sw_epi_reset the
+ * members).  It synchronises the device and clears an earlier give-up;
+ * sw_ens_set_wait_test(e, 0, 0) restores normal operation. */
+int sw_ens_set_wait_test(sw_ens_t ens, double limit_s, int extra);
 /* bracket every batched iteration with CUDA events on the run's stream */
 int sw_ens_profile(sw_ens_t ens, int enable);
 

@@ -15,6 +15,15 @@ using namespace swepi;
 
 namespace {
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// The context's tables and workspace live on the device sw_init ran on; a call
+// made with another device current would launch there on foreign pointers, so
+// it is refused before any launch.
+int check_device(const Ctx& c) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SW_ECUDA;
+  return dev == c.device ? SW_OK : SW_EINVAL;
+}
 }  // namespace
 
 namespace swepi {
@@ -224,7 +233,8 @@ const char* sw_status_str(int status) {
 int sw_init(int n_e, int p, const sw_params* prm, sw_ctx_t* out) {
   if (!out) return SW_EINVAL;
   *out = nullptr;
-  if (!prm || n_e < 1 || n_e > 1024 || p < 0 || p > MAX_NS - 1 || prm->precision != 0 || !(prm->radius > 0) ||
+  if (!prm || n_e < 1 || n_e > 1024 || p < 0 || p > MAX_NS - 1 || prm->precision < 0 || prm->precision > 1 ||
+      !(prm->radius > 0) ||
       !(prm->gravity > 0) || !std::isfinite(prm->omega))
     return SW_EINVAL;
   sw_ctx* c = new (std::nothrow) sw_ctx();
@@ -233,6 +243,8 @@ int sw_init(int n_e, int p, const sw_params* prm, sw_ctx_t* out) {
   c->ne = n_e;
   c->ns = p + 1;
   c->prm = *prm;
+  // precision 1: the complex64-bulk form from the start (as sw_set_jvp_mode 2)
+  c->jvp_mode = prm->precision == 1 ? 2 : 1;
   // the host tables of a very large grid can exceed host memory: no exception
   // may cross the C ABI
   int rc;
@@ -294,16 +306,41 @@ int sw_node_xyz(sw_ctx_t c, double* xyz) {
   return SW_OK;
 }
 
-int sw_set_bottom(sw_ctx_t c, const double* hB) {
+int sw_set_bottom_host(sw_ctx_t c, const double* hB) {
   if (!c || !hB) return SW_EINVAL;
   int rc = bottom_coefficients(*c, hB);
   return rc ? rc : refresh_diag_bottom(*c, hB);
 }
 
+int sw_set_bottom(sw_ctx_t c, const double* hB_dev) {
+  if (!c || !hB_dev) return SW_EINVAL;
+  int rc = check_device(*c);
+  if (rc) return rc;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, hB_dev) != cudaSuccess) {
+    cudaGetLastError();
+    return SW_EINVAL;
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return SW_EINVAL;
+  if (at.type == cudaMemoryTypeDevice && at.device != c->device) return SW_EINVAL;
+  // the topography coefficients are built by the same host routine as
+  // sw_set_bottom_host from a host copy of h_B (an initialisation call)
+  std::vector<double> h;
+  try {
+    h.resize((size_t)c->nodes);
+  } catch (const std::bad_alloc&) {
+    return SW_ENOMEM;
+  }
+  if (cudaMemcpy(h.data(), hB_dev, sizeof(double) * c->nodes, cudaMemcpyDeviceToHost) != cudaSuccess) return SW_ECUDA;
+  return sw_set_bottom_host(c, h.data());
+}
+
 int sw_diagnostics(sw_ctx_t c, const double* q, double* out, double* zeta, void* stream) {
   if (!c || !q || !out) return SW_EINVAL;
   double r[6];
-  int rc = launch_diagnostics(*c, q, nullptr, zeta, r, as_stream(stream));
+  int rc = check_device(*c);
+  if (rc) return rc;
+  rc = launch_diagnostics(*c, q, nullptr, zeta, r, as_stream(stream));
   if (rc) return rc;
   for (int k = 0; k < 4; ++k) out[k] = r[k];
   return SW_OK;
@@ -312,7 +349,9 @@ int sw_diagnostics(sw_ctx_t c, const double* q, double* out, double* zeta, void*
 int sw_error_norms(sw_ctx_t c, const double* q, const double* q_ref, double* out, void* stream) {
   if (!c || !q || !q_ref || !out) return SW_EINVAL;
   double r[6];
-  int rc = launch_diagnostics(*c, q, q_ref, nullptr, r, as_stream(stream));
+  int rc = check_device(*c);
+  if (rc) return rc;
+  rc = launch_diagnostics(*c, q, q_ref, nullptr, r, as_stream(stream));
   if (rc) return rc;
   if (!(r[2] != 0) || !(r[3] > 0) || !(r[5] > 0)) return SW_ENONFINITE;
   out[0] = r[0] / r[2];
@@ -331,11 +370,13 @@ int sw_state_from_fields(sw_ctx_t c, const double* h, const double* hB, const do
 
 int sw_rhs(sw_ctx_t c, const double* q, double* F, void* stream) {
   if (!c || !q || !F || q == F) return SW_EINVAL;
+  if (int rc = check_device(*c)) return rc;
   return launch_rhs(*c, q, F, as_stream(stream));
 }
 
 int sw_jvp(sw_ctx_t c, const double* q, const double* v, double eps, double* Jv, void* stream) {
   if (!c || !q || !v || !Jv || Jv == q || Jv == v || !(eps > 0) || !std::isfinite(eps)) return SW_EINVAL;
+  if (int rc = check_device(*c)) return rc;
   AugEpilogue ep;
   return launch_jvp(*c, q, v, eps, Jv, ep, as_stream(stream));
 }
@@ -346,9 +387,10 @@ int sw_kiops_phi(sw_ctx_t c, const double* q_lin, double dt, double tau_out, int
   for (int k = 0; k < nb; ++k)
     if (b[k] == w) return SW_EINVAL;
   if (w == q_lin) return SW_EINVAL;
+  int rc = check_device(*c);
+  if (rc) return rc;
   sw_kiops_opts o = opts ? *opts : default_opts();
   cudaStream_t s = as_stream(stream);
-  int rc;
   c->epi_order = 0;
   c->epi_stage = 0;
   if (c->jvp_mode >= 1 && (rc = launch_linearize(*c, q_lin, s))) return rc;
@@ -367,7 +409,9 @@ int sw_epi_reset(sw_ctx_t c) {
 int sw_epi_set_history(sw_ctx_t c, int i, const double* q, const double* F, void* stream) {
   if (!c || !q || i < 1 || i > MAX_HIST) return SW_EINVAL;
   cudaStream_t s = as_stream(stream);
-  int rc = ensure_epi(*c);
+  int rc = check_device(*c);
+  if (rc) return rc;
+  rc = ensure_epi(*c);
   if (rc) return rc;
   // seeding addresses entries relative to head = 0: entry i lives in slot (0 - (i-1)) mod MAX_HIST
   c->hist_head = 0;
@@ -387,6 +431,7 @@ int sw_epi_set_history(sw_ctx_t c, int i, const double* q, const double* F, void
 int sw_epi_step(sw_ctx_t c, int order, double dt, double* q, const sw_kiops_opts* opts, sw_kiops_stats* st,
                 void* stream) {
   if (!c || !q || order < 2 || order > 6 || !std::isfinite(dt) || !(dt > 0)) return SW_EINVAL;
+  if (int rc = check_device(*c)) return rc;
   TraceRange trace("EPI step");
   cudaStream_t s = as_stream(stream);
   sw_kiops_opts o = opts ? *opts : default_opts();
@@ -563,12 +608,14 @@ int sw_set_jvp_mode(sw_ctx_t c, int mode) {
 
 int sw_linearize(sw_ctx_t c, const double* q, void* stream) {
   if (!c || !q) return SW_EINVAL;
+  if (int rc = check_device(*c)) return rc;
   return launch_linearize(*c, q, as_stream(stream));
 }
 
 int sw_jvp_linearized(sw_ctx_t c, const double* v, double* Jv, void* stream) {
   if (!c || !v || !Jv || v == Jv) return SW_EINVAL;
   if (!c->linearized) return SW_EINVAL;
+  if (int rc = check_device(*c)) return rc;
   AugEpilogue ep;
   return launch_jvp_lin(*c, v, Jv, ep, as_stream(stream), c->jvp_mode == 2);
 }

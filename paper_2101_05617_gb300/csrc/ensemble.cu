@@ -109,6 +109,10 @@ struct EnsList {
 struct EnsCtl {
   unsigned int next, exited;   // task counter and exit ticket (both back to 0 when a launch ends)
   int error, where;            // a bounded wait gave up: phase | member << 4
+  // failure-path test settings (sw_ens_set_wait_test): added to every wait
+  // target (0 in normal operation) and the wait's time limit (0 = kWaitLimitNs)
+  unsigned int extra, pad;
+  unsigned long long limit_ns;
 };
 
 struct GatherSrc {
@@ -147,13 +151,15 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // After a give-up, and once any wait has given up, the task carries on with
 // whatever data is there so that the launch still completes.
 __device__ void wait_count(const unsigned int* ctr, unsigned int target, EnsCtl* ctl, int where) {
+  target += ctl->extra;
   if (ld_acquire(ctr) >= target) return;
+  const unsigned long long limit = ctl->limit_ns ? ctl->limit_ns : kWaitLimitNs;
   const unsigned long long t0 = global_ns();
   for (unsigned int it = 1;; ++it) {
     __nanosleep(128);
     if (ld_acquire(ctr) >= target) break;
     if (*(volatile int*)&ctl->error) break;
-    if (it >= kWaitMaxPolls || ((it & 255u) == 0 && global_ns() - t0 > kWaitLimitNs)) {
+    if (it >= kWaitMaxPolls || ((it & 255u) == 0 && global_ns() - t0 > limit)) {
       if (atomicCAS(&ctl->error, 0, 1) == 0) ctl->where = where;
       break;
     }
@@ -1447,6 +1453,17 @@ int sw_ens_epi_run(sw_ens_t e, int steps, const int* orders, const double* dts, 
   }
   TraceRange trace("ensemble EPI run");
   return ens_run(*e, steps, orders, dts, q_dev, o, stats, as_stream(stream));
+}
+
+int sw_ens_set_wait_test(sw_ens_t e, double limit_s, int extra) {
+  if (!e || !(limit_s >= 0.0) || limit_s > 2.0 || extra < 0 || extra > 1) return SW_EINVAL;
+  // no launch of this ensemble is in flight between calls; writing the control
+  // block also clears an earlier give-up
+  if (cudaDeviceSynchronize() != cudaSuccess) return SW_ECUDA;
+  EnsCtl ctl{};
+  ctl.extra = (unsigned int)extra;
+  ctl.limit_ns = (unsigned long long)(limit_s * 1e9);
+  return cuda_status(cudaMemcpy(e->d_ctl, &ctl, sizeof(EnsCtl), cudaMemcpyHostToDevice));
 }
 
 int sw_ens_profile(sw_ens_t e, int enable) {

@@ -94,6 +94,7 @@ def lib():
     L.sw_node_xyz.argtypes = [vp, vp]
     L.sw_state_from_fields.argtypes = [vp, vp, vp, vp, vp]
     L.sw_set_bottom.argtypes = [vp, vp]
+    L.sw_set_bottom_host.argtypes = [vp, vp]
     L.sw_rhs.argtypes = [vp, vp, vp, vp]
     L.sw_jvp.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp]
     L.sw_jvp_static_scratch.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp]
@@ -146,12 +147,13 @@ def lib():
                                  ctypes.POINTER(sw_kiops_opts), ctypes.POINTER(sw_kiops_stats), vp]
     L.sw_ens_stats_read.argtypes = [vp, ctypes.POINTER(sw_ens_stats)]
     L.sw_ens_profile.argtypes = [vp, ip]
+    L.sw_ens_set_wait_test.argtypes = [vp, ctypes.c_double, ip]
     _lib = L
     return L
 
 
 EXPORTED = ["sw_init", "sw_free", "sw_num_unknowns", "sw_grid_info", "sw_node_xyz", "sw_state_from_fields",
-            "sw_set_bottom", "sw_rhs", "sw_jvp", "sw_jvp_static_scratch", "sw_linearize", "sw_jvp_linearized",
+            "sw_set_bottom", "sw_set_bottom_host", "sw_rhs", "sw_jvp", "sw_jvp_static_scratch", "sw_linearize", "sw_jvp_linearized",
             "sw_set_jvp_mode", "sw_kiops_phi", "sw_epi_step", "sw_epi_step_host", "sw_epi_set_history",
             "sw_epi_reset", "sw_epi_coefficients", "sw_dfr_operators", "sw_node_coefficients",
             "sw_interface_transform", "sw_kernel_launches", "sw_profile", "sw_profile_kinds", "sw_profile_read", "sw_fp64_fma_peak",
@@ -159,7 +161,7 @@ EXPORTED = ["sw_init", "sw_free", "sw_num_unknowns", "sw_grid_info", "sw_node_xy
             "sw_mlp_forward", "sw_mlp_gradient", "sw_mlp_train", "sw_set_controller", "sw_kiops_log",
             "sw_kiops_log_clear", "sw_diagnostics", "sw_error_norms", "sw_ens_create", "sw_ens_free",
             "sw_ens_set_block", "sw_ens_set_tiles", "sw_ens_get_tiles", "sw_ens_set_policy", "sw_ens_tune",
-            "sw_ens_epi_run", "sw_ens_stats_read", "sw_ens_profile"]
+            "sw_ens_epi_run", "sw_ens_stats_read", "sw_ens_profile", "sw_ens_set_wait_test"]
 
 MLP_PARAMS = 5378
 MLP_NORM = 36
@@ -198,8 +200,9 @@ def make_opts(tol=1e-10, m_init=10, m_min=10, m_max=128, iop=2, tau_init=0.0):
 
 
 # ------------------------------------------------------------------ C names
-def sw_init(n_e, p, rotation=(0.0, 0.0, 0.0), radius=6.37122e6, gravity=9.80616, omega=7.292e-5):
-    prm = sw_params(radius, gravity, omega, rotation[0], rotation[1], rotation[2], 0)
+def sw_init(n_e, p, rotation=(0.0, 0.0, 0.0), radius=6.37122e6, gravity=9.80616, omega=7.292e-5, precision=0):
+    """precision 0: FP64 throughout; 1: the complex64-bulk form from the start."""
+    prm = sw_params(radius, gravity, omega, rotation[0], rotation[1], rotation[2], int(precision))
     h = ctypes.c_void_p()
     _check("sw_init", lib().sw_init(int(n_e), int(p), ctypes.byref(prm), ctypes.byref(h)))
     return h
@@ -232,9 +235,15 @@ def sw_state_from_fields(ctx, h, hB, V):
 
 
 def sw_set_bottom(ctx, hB):
+    """Bottom height at the nodes from a float64 CUDA tensor (the C call takes a device pointer)."""
+    nodes = sw_num_unknowns(ctx) // 3
+    _check("sw_set_bottom", lib().sw_set_bottom(ctx, _dev_ptr(hB, nodes)))
+
+
+def sw_set_bottom_host(ctx, hB):
     nodes = sw_num_unknowns(ctx) // 3
     hB = _host(hB, nodes)
-    _check("sw_set_bottom", lib().sw_set_bottom(ctx, hB.ctypes.data_as(ctypes.c_void_p)))
+    _check("sw_set_bottom_host", lib().sw_set_bottom_host(ctx, hB.ctypes.data_as(ctypes.c_void_p)))
 
 
 def sw_rhs(ctx, q, F, stream=None):
@@ -542,6 +551,10 @@ def sw_ens_profile(e, enable=True):
     _check("sw_ens_profile", lib().sw_ens_profile(e, int(bool(enable))))
 
 
+def sw_ens_set_wait_test(e, limit_s, extra):
+    _check("sw_ens_set_wait_test", lib().sw_ens_set_wait_test(e, float(limit_s), int(extra)))
+
+
 def sw_ens_stats_read(e):
     st = sw_ens_stats()
     _check("sw_ens_stats_read", lib().sw_ens_stats_read(e, ctypes.byref(st)))
@@ -591,6 +604,9 @@ class SWEnsemble:
     def profile(self, enable=True):
         sw_ens_profile(self.handle, enable)
 
+    def set_wait_test(self, limit_s, extra):
+        sw_ens_set_wait_test(self.handle, limit_s, extra)
+
 
 class SWContext:
     """Owns one library context (grid + workspace) on the current CUDA device."""
@@ -619,7 +635,12 @@ class SWContext:
         return sw_state_from_fields(self.handle, h, hB, V)
 
     def set_bottom(self, hB):
-        sw_set_bottom(self.handle, hB)
+        """hB: a float64 CUDA tensor (sw_set_bottom) or a host array (sw_set_bottom_host)."""
+        import torch
+        if isinstance(hB, torch.Tensor) and hB.is_cuda:
+            sw_set_bottom(self.handle, hB)
+        else:
+            sw_set_bottom_host(self.handle, np.asarray(hB))
 
     def rhs(self, q, out=None, stream=None):
         import torch

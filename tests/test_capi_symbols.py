@@ -52,8 +52,9 @@ def test_argument_checks_without_gpu():
     assert L.sw_init(0, 3, ctypes.byref(prm), ctypes.byref(h)) == EINVAL and not h.value
     assert L.sw_init(4, 8, ctypes.byref(prm), ctypes.byref(h)) == EINVAL and not h.value   # p <= 7
     assert L.sw_init(4, 3, None, ctypes.byref(h)) == EINVAL
-    bad = swepi.sw_params(6.37122e6, 9.80616, 7.292e-5, 0.0, 0.0, 0.0, 1)           # precision is set per mode
-    assert L.sw_init(4, 3, ctypes.byref(bad), ctypes.byref(h)) == EINVAL
+    for prec in (-1, 2):                                    # precision: 0 = FP64, 1 = complex64-bulk form
+        bad = swepi.sw_params(6.37122e6, 9.80616, 7.292e-5, 0.0, 0.0, 0.0, prec)
+        assert L.sw_init(4, 3, ctypes.byref(bad), ctypes.byref(h)) == EINVAL and not h.value
     x = ctypes.c_void_p(16)   # never dereferenced: every call below fails its NULL-context check first
     o = swepi.make_opts()
     st = swepi.sw_kiops_stats()
@@ -68,7 +69,7 @@ def test_argument_checks_without_gpu():
     assert L.sw_epi_set_history(None, 1, x, x, None) == EINVAL
     assert L.sw_epi_reset(None) == EINVAL
     assert L.sw_set_jvp_mode(None, 1) == EINVAL
-    assert L.sw_set_bottom(None, x) == EINVAL
+    assert L.sw_set_bottom(None, x) == EINVAL and L.sw_set_bottom_host(None, x) == EINVAL
     assert L.sw_node_xyz(None, x) == EINVAL
     assert L.sw_state_from_fields(None, x, x, x, x) == EINVAL
     assert L.sw_diagnostics(None, x, x, None, None) == EINVAL

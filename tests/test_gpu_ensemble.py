@@ -181,3 +181,33 @@ def test_ensemble_full_size_sampled():
         assert st[i]["krylov_iters"] == r["krylov_iters"]
     for y in ys:
         assert torch.isfinite(y).all()
+
+
+def test_bounded_wait_gives_up_with_timeout_status():
+    """Failure path of the batched kernel's bounded waits, with no GPU fault:
+    one extra count on every wait target (a count that no task ever provides)
+    and a 50 ms bound make each launch end by the bound, and sw_ens_epi_run
+    returns SW_ETIMEOUT; the launch completes, the context stays usable, and
+    after restoring normal operation the same ensemble reproduces the members'
+    single-context runs."""
+    from paper_2101_05617_gb300 import ensemble, swepi
+    spec = SMALL[:2]
+    members, ctxs, qs = _setup(spec)
+    ens = swepi.SWEnsemble(ctxs)
+    ens.set_wait_test(0.05, 1)
+    ys = [q.clone() for q in qs]
+    with pytest.raises(swepi.SWError) as ei:
+        ens.epi_run(1, [m.order for m in members], [m.dt for m in members], ys, tol=TOL)
+    assert ei.value.status == -5, ei.value
+    torch.cuda.synchronize()                      # the device is still answering
+    ens.set_wait_test(0.0, 0)
+    ensemble.reset(ctxs)
+    ys = [q.clone() for q in qs]
+    st = ens.epi_run(2, [m.order for m in members], [m.dt for m in members], ys, tol=TOL)
+    ens.close()
+    refs, ref_st, _ = ensemble.run_single(members, ctxs, qs, 2, tol=TOL)
+    _compare(ys, refs)
+    for a, b in zip(st, ref_st):
+        assert a["krylov_iters"] == b["krylov_iters"], (a, b)
+    with pytest.raises(swepi.SWError):
+        swepi.sw_ens_set_wait_test(swepi.sw_ens_create([c.handle for c in ctxs]), 3.0, 0)   # bound above 2 s

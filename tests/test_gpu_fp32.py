@@ -86,3 +86,32 @@ def test_fp32_window3_ne60_below_time_discretisation_error():
     e32 = _rel(q32, q64)
     etime = _rel(q64, qfine)
     assert all(a < 0.1 * b for a, b in zip(e32, etime)), (e32, etime)
+
+
+def test_precision_one_at_init_equals_mode_two():
+    """sw_params.precision = 1 selects the complex64-bulk form at sw_init: its
+    EPI trajectory (start-up and multistep steps) and statistics equal those of
+    a precision-0 context switched by sw_set_jvp_mode(2), bit for bit."""
+    from paper_2101_05617_gb300 import synth
+    from paper_2101_05617_gb300.swepi import SWContext
+    wl = synth.WORKLOADS["small_ne4_p3"]
+    f = synth.make_fields("small_ne4_p3", 4)
+    a = SWContext(wl.ne, wl.p, f.rotation, precision=1)
+    b = SWContext(wl.ne, wl.p, f.rotation)
+    b.set_jvp_mode(2)
+    h, hB, V = f.evaluate(a.node_xyz())
+    q0 = a.state_from_fields(h, hB, V)
+    b.state_from_fields(h, hB, V)
+    qa = torch.tensor(q0, device="cuda")
+    qb = qa.clone()
+    for _ in range(6):
+        sa = a.epi_step(5, wl.dt, qa, tol=wl.tol)
+        sb = b.epi_step(5, wl.dt, qb, tol=wl.tol)
+        assert sa == sb, (sa, sb)
+    assert torch.equal(qa, qb)
+    c = SWContext(wl.ne, wl.p, f.rotation)          # precision 0 differs (the FP64 path)
+    c.state_from_fields(h, hB, V)
+    qc = torch.tensor(q0, device="cuda")
+    for _ in range(6):
+        c.epi_step(5, wl.dt, qc, tol=wl.tol)
+    assert not torch.equal(qa, qc)

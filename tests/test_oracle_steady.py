@@ -15,6 +15,10 @@ including the twelve panel edges with their App. C transforms, takes part.
 What the discretisation must give: a tendency and an EPI trajectory drift that
 vanish under h-refinement at roughly the DFR order (Table 1).
 """
+import multiprocessing as mp
+import os
+import time
+
 import numpy as np
 import pytest
 
@@ -35,6 +39,43 @@ def _steady(ne, ns, rot, omega=geo.OMEGA):
     V = U0 * np.stack([-y, x, np.zeros_like(z)])
     h = H0 - (g.a * geo.OMEGA * U0 + 0.5 * U0 ** 2) * z ** 2 / geo.GRAVITY
     return g, fields.state_from_fields(g, h, np.zeros_like(h), V)
+
+
+def _run_convergence_job(args):
+    """One (N_e, N_s, order, dt, hours) run of the oracle's whole method on the
+    steady flow: EPI with KIOPS tolerance 1e-10 from the exact state, then the
+    error norms of Eq. 39-41 of H against that (time-independent) state."""
+    ne, ns, order, dt, hours = args
+    from oracle import diagnostics as od
+    g, q = _steady(ne, ns, ROTATIONS[0])
+    it = oepi.EPI(lambda x: sw.rhs_real(g, x.reshape(q.shape)).reshape(-1),
+                  lambda x, v: sw.jvp(g, x.reshape(q.shape), v.reshape(q.shape)).reshape(-1), order, tol=1e-10)
+    y = q.reshape(-1).copy()
+    t0 = time.time()
+    for _ in range(int(round(hours * 3600.0 / dt))):
+        y = it.step(y, dt)
+    H = y.reshape(q.shape)[0] / g.m['sqrtg']
+    HT = q[0] / g.m['sqrtg']
+    return ne, ns, [float(e) for e in od.error_norms(g, H, HT)], time.time() - t0
+
+
+_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+def _run_convergence_jobs(jobs):
+    """The jobs in spawned processes, one BLAS thread each (the children inherit
+    the environment at spawn)."""
+    saved = {k: os.environ.get(k) for k in _THREAD_VARS}
+    os.environ.update({k: "1" for k in _THREAD_VARS})
+    try:
+        with mp.get_context("spawn").Pool(min(len(jobs), mp.cpu_count())) as pool:
+            return pool.map(_run_convergence_job, jobs, chunksize=1)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
 
 
 def _residual(g, q):
@@ -97,9 +138,8 @@ def test_spatial_orders_follow_table_1():
     the paper's jump of about 2 from N_s = 4 to N_s = 5 (odd N_s - 1 gains one
     order over the even one below it), and N_s = 6 above 5.  The same runs
     with N_e 10 -> 20 over a day give 3.49 / 3.63 / 5.40 / 5.69 (L1)."""
-    from tests.convergence_study import run_jobs
     table = golden_dfr_orders()
-    res = run_jobs([(ne, ns, 6, 3600.0, 6.0) for ns in (3, 4, 5, 6) for ne in (5, 10)])
+    res = _run_convergence_jobs([(ne, ns, 6, 3600.0, 6.0) for ns in (3, 4, 5, 6) for ne in (5, 10)])
     err = {(ne, ns): np.array(e) for ne, ns, e, _ in res}
     order = {ns: np.log(err[(5, ns)] / err[(10, ns)]) / np.log(2.0) for ns in (3, 4, 5, 6)}
     for ns in (3, 4, 5):

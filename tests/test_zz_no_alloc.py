@@ -2,7 +2,9 @@
 memory while running (their memory manager owns the device memory, or they run
 where cudaMalloc is not allowed or its implicit synchronisation cannot be
 afforded).  It keeps its interface-flux scratch in a fixed array inside the
-library; these tests call it through the C ABI and check it against sw_jvp.
+library; these tests call it through the C ABI and check it against the oracle's
+complex-step JVP (Eq. 28) and against sw_jvp, and that its calls leave the
+device's free memory unchanged.
 
 This file is collected last on purpose: if it fails, a run that stops at the
 first failure has already run every other test."""
@@ -11,6 +13,7 @@ import ctypes
 import numpy as np
 import pytest
 
+from oracle import shallow_water as osw
 from tests.gpu_common import oracle_case, scaled_direction, scaled_err_per_var, term_scale
 
 torch = pytest.importorskip("torch")
@@ -26,7 +29,7 @@ def _raw_call(lib, ctx, q, v, eps, out):
 
 
 @pytest.mark.parametrize("ne,ns,seed", [(4, 4, 0), (6, 6, 3)])
-def test_static_scratch_matches_sw_jvp_two_calls(ne, ns, seed):
+def test_static_scratch_matches_oracle_two_calls(ne, ns, seed):
     from paper_2101_05617_gb300 import swepi
     _, g, q, hB = oracle_case(ne, ns, seed=seed)
     ctx = swepi.SWContext(g.ne, g.ns - 1, g.rotation)
@@ -35,15 +38,38 @@ def test_static_scratch_matches_sw_jvp_two_calls(ne, ns, seed):
     for call, vseed in enumerate((seed + 1, seed + 2)):       # two calls in a row reuse the array
         v = scaled_direction(q, vseed)
         vd = torch.tensor(v.reshape(-1), device="cuda")
-        ref = ctx.jvp(qd, vd, 1e-30)
+        ref = osw.jvp(g, q, v, 1e-30)
         out = torch.full_like(qd, float("nan"))
         rc = _raw_call(lib, ctx.handle, qd, vd, 1e-30, out)
         assert rc == 0, swepi.sw_status_str(rc)
         torch.cuda.synchronize()
-        a, b = out.cpu().numpy(), ref.cpu().numpy()
+        a = out.cpu().numpy()
         assert np.all(np.isfinite(a)), f"call {call}: unwritten entries"
-        err = scaled_err_per_var(a, b, term_scale(g, q, v))
+        err = scaled_err_per_var(a, ref, term_scale(g, q, v))
         assert max(err) < TOL_JVP, (call, err)
+        err2 = scaled_err_per_var(a, ctx.jvp(qd, vd, 1e-30).cpu().numpy(), term_scale(g, q, v))
+        assert max(err2) < TOL_JVP, (call, err2)
+
+
+def test_static_scratch_allocates_nothing():
+    """After a first call (the one-time address lookup), further calls leave the
+    device's free memory as it was: the library makes no cudaMalloc of its own,
+    which torch's allocator statistics would not show."""
+    from paper_2101_05617_gb300 import swepi
+    _, g, q, _ = oracle_case(5, 5, seed=2)
+    ctx = swepi.SWContext(g.ne, g.ns - 1, g.rotation)
+    lib = swepi.lib()
+    qd = torch.tensor(q.reshape(-1), device="cuda")
+    vd = torch.tensor(scaled_direction(q, 11).reshape(-1), device="cuda")
+    out = torch.empty_like(qd)
+    assert _raw_call(lib, ctx.handle, qd, vd, 1e-30, out) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        assert _raw_call(lib, ctx.handle, qd, vd, 1e-30, out) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
 
 
 def test_static_scratch_rejects_oversized_grid():
