@@ -204,10 +204,10 @@ def test_bounded_wait_gives_up_with_timeout_status():
     ensemble.reset(ctxs)
     ys = [q.clone() for q in qs]
     st = ens.epi_run(2, [m.order for m in members], [m.dt for m in members], ys, tol=TOL)
+    with pytest.raises(swepi.SWError):
+        ens.set_wait_test(3.0, 0)                 # bounds above the default 2 s are refused
     ens.close()
     refs, ref_st, _ = ensemble.run_single(members, ctxs, qs, 2, tol=TOL)
     _compare(ys, refs)
     for a, b in zip(st, ref_st):
         assert a["krylov_iters"] == b["krylov_iters"], (a, b)
-    with pytest.raises(swepi.SWError):
-        swepi.sw_ens_set_wait_test(swepi.sw_ens_create([c.handle for c in ctxs]), 3.0, 0)   # bound above 2 s
