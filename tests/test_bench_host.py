@@ -95,3 +95,40 @@ def test_reference_arm_runs_on_cpu():
     assert out.returncode == 0, out.stderr
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["e2e"]["h2d_bytes_per_step"] == 0
+    assert line["projected"] is True and "PROJECTED" in line["cpu_baseline"]["sample"]
+
+
+def test_oracle_step_projection_arithmetic():
+    """The projected oracle step: Krylov iterations x their cost + one expm per
+    substep attempt + one combination per accepted substep + P remainder JVPs +
+    one RHS."""
+    sys.path.insert(0, ROOT)
+    import bench
+    s = {"t_iter": 0.5, "t_expm": 0.1, "t_combine_128": 0.2, "t_jvp": 0.4, "t_rhs": 0.3}
+    assert abs(bench.project_oracle_step(s, 100, 5, 3, 3) - (50.0 + 0.5 + 0.6 + 1.2 + 0.3)) < 1e-12
+
+
+def test_oracle_full_step_runs_on_cpu():
+    """--oracle-full-step: one complete oracle EPI step (measured, with its own
+    KIOPS counts) on the small workload."""
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-full-step", "--workload",
+                          "small_ne4_p3"], capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr
+    r = json.loads(out.stdout.strip().splitlines()[-1])["oracle_full_step"]
+    assert r["finite"] and r["krylov_iters"] > 0 and r["attempts"] >= r["substeps"] >= 1 and r["seconds"] > 0
+
+
+def test_headline_keys():
+    """The compact comparison at the end of the line reads the n_e = 60 form."""
+    sys.path.insert(0, ROOT)
+    import bench
+    out = {"value": 10.0, "e2e": {"value": 9.5}, "forms": {"complex64_bulk_ne60_p5": {
+        "steps": 48, "time_discretisation_err_rel_l2": [1e-5, 2e-4, 1e-4],
+        "fp64": {"steps_per_s": 9.0},
+        "complex64_bulk_window3": {"steps_per_s": 20.0, "speedup_vs_fp64": 20 / 9, "err_vs_fp64_rel_l2": [1e-7, 5e-7, 2e-7],
+                                   "finite": True},
+        "complex64_bulk_window3_learned": {"error": "SWError: non-finite value"}}}}
+    h = bench.headline(out)
+    assert h["fp64_steps_per_s"] == 10.0 and h["time_disc_err"] == 2e-4 and h["steps"] == 48
+    assert h["plain_c64"]["err_vs_fp64"] == 5e-7 and h["plain_c64"]["finite"]
+    assert "non-finite" in h["learned_c64"]["error"]
