@@ -141,14 +141,16 @@ struct VolShape {
 // set -- the window dot products of the incomplete orthogonalisation (two or
 // three vectors; see AugEpilogue).
 // SCALED: the caller has already multiplied res by scale.  W3: compiled for
-// the window of three (dotC may be set); W3 = false drops that code.
-template <int THREADS, bool SCALED = false, bool W3 = false>
+// the window of three (dotC may be set); W3 = false drops that code.  B64:
+// the b-column terms are added here in FP64; false: the caller has added them
+// already (the FP32 kernels of the complex64-bulk form, from ep.b32).
+template <int THREADS, bool SCALED = false, bool W3 = false, bool B64 = true>
 __device__ __forceinline__ void volume_epilogue(const AugEpilogue& ep, bool active, long long idx, long long N,
                                                 const double res[3], double* __restrict__ out, unsigned int blk,
                                                 unsigned int nblk) {
   // the tail coefficients nu * y_l, once per block
   __shared__ double coef[MAX_NB];
-  if (threadIdx.x < MAX_NB) {
+  if (B64 && threadIdx.x < MAX_NB) {
     const int l = threadIdx.x;
     coef[l] = (l < ep.p && ep.b[l]) ? ep.nu * ep.tail_in[l] : 0.0;
   }
@@ -160,7 +162,7 @@ __device__ __forceinline__ void volume_epilogue(const AugEpilogue& ep, bool acti
       double o = SCALED ? res[mu] : ep.scale * res[mu];
 #pragma unroll
       for (int l = 0; l < MAX_NB; ++l)
-        if (l < ep.p && ep.b[l]) o = fma(coef[l], ep.b[l][idx + mu * N], o);
+        if (B64 && l < ep.p && ep.b[l]) o = fma(coef[l], ep.b[l][idx + mu * N], o);
       out[idx + mu * N] = o;
       if (ep.dotB) {
         db = fma(o, ep.dotB[idx + mu * N], db);

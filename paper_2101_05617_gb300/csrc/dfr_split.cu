@@ -225,6 +225,9 @@ int launch_linearize(Ctx& c, const double* q, cudaStream_t s) {
 int launch_jvp_lin(Ctx& c, const double* v, double* out, const AugEpilogue& ep, cudaStream_t s, bool fp32) {
   if (!c.linearized) return SW_EINVAL;
   if (fp32 && !c.d_lin_node32) return SW_EINVAL;
+  // the FP32 kernels take the b-column terms from their FP32 copies only
+  for (int l = 0; fp32 && l < ep.p && l < MAX_NB; ++l)
+    if (ep.b[l] && !ep.b32[l]) return SW_EINVAL;
   switch (c.ns) {
     case 1: return tangent_any<1>(c, v, out, ep, fp32, s);
     case 2: return tangent_any<2>(c, v, out, ep, fp32, s);

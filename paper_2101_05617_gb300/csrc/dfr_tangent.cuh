@@ -13,8 +13,50 @@ namespace swepi {
 // ---------------------------------------------------------------- tangent
 // The imaginary half in arithmetic type T: double (the FP64 path) or float
 // (the complex64-bulk form: tables rounded from the FP64 linearisation, FP32
-// accumulation).  Krylov vectors in and out stay FP64; the epilogue (augmented
-// operator and orthogonalisation dots) is FP64 in both.
+// accumulation).  Krylov vectors in and out stay FP64; the orthogonalisation
+// dots of the epilogue are FP64 in both.
+//
+// Conversions between the FP64 Krylov vectors and the FP32 arithmetic of the
+// complex64-bulk form are done on the IEEE-754 bit fields with integer
+// operations, so that none of them occupies the FP64 pipe (on this GPU a
+// fraction of the FP32 rate).  binary64 -> binary32 truncates the significand
+// (rounding toward zero: relative error below 2^-23, against 2^-24 for
+// round-to-nearest) and maps magnitudes below the binary32 normal range to
+// signed zero, above it to infinity, NaN to NaN; binary32 -> binary64 is exact
+// for normal numbers, zero, infinities and NaN (binary32 subnormals become
+// zero).
+__device__ __forceinline__ float f64_to_f32_bits(double x) {
+  const unsigned int hi = (unsigned int)__double2hiint(x), lo = (unsigned int)__double2loint(x);
+  const unsigned int sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 896;                  // binary32 biased exponent
+  const unsigned int mant = ((hi & 0xfffffu) << 3) | (lo >> 29);   // top 23 significand bits
+  unsigned int r = sign | ((unsigned int)e << 23) | mant;
+  r = (e <= 0) ? sign : r;
+  r = (e >= 255) ? (sign | 0x7f800000u) : r;
+  const bool nan = ((hi & 0x7ff00000u) == 0x7ff00000u) && (((hi & 0xfffffu) | lo) != 0u);
+  return __uint_as_float(nan ? 0x7fc00000u : r);
+}
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int sign = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  unsigned int hi = sign | ((e + 896u) << 20) | (m >> 3);
+  unsigned int lo = m << 29;
+  hi = (e == 0u) ? sign : hi;
+  lo = (e == 0u) ? 0u : lo;
+  hi = (e == 255u) ? (sign | 0x7ff00000u | (m >> 3) | (m ? 0x80000u : 0u)) : hi;
+  return __hiloint2double((int)hi, (int)lo);
+}
+template <typename T>
+__device__ __forceinline__ T from_f64(double x) {
+  if constexpr (sizeof(T) == 4) return f64_to_f32_bits(x);
+  else return x;
+}
+template <typename T>
+__device__ __forceinline__ double to_f64(T x) {
+  if constexpr (sizeof(T) == 4) return f32_to_f64_bits(x);
+  else return x;
+}
+
 template <typename T, int NS>
 __device__ __forceinline__ void trace_tan(const double* __restrict__ v, long long nodes, int elem, int edge, int i,
                                           const DfrConst& dc, T out[3]) {
@@ -26,7 +68,7 @@ __device__ __forceinline__ void trace_tan(const double* __restrict__ v, long lon
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
       const long long idx = base + ((edge <= 1) ? (i * NS + k) : (k * NS + i)) + var * nodes;
-      acc = fma(T(w[k]), T(__ldg(v + idx)), acc);
+      acc = fma(from_f64<T>(w[k]), from_f64<T>(__ldg(v + idx)), acc);
     }
     out[var] = acc;
   }
@@ -68,8 +110,9 @@ __device__ __forceinline__ void face_tangent_body(const TanFaceArgs<T>& a, const
     f[mu] = s;
   }
   const double* fc = a.fc + t;
-  const T sig = T(fc[FC_SIG * P]);
-  const T M00 = T(fc[FC_M00 * P]), M01 = T(fc[FC_M01 * P]), M10 = T(fc[FC_M10 * P]), M11 = T(fc[FC_M11 * P]);
+  const T sig = from_f64<T>(fc[FC_SIG * P]);
+  const T M00 = from_f64<T>(fc[FC_M00 * P]), M01 = from_f64<T>(fc[FC_M01 * P]);
+  const T M10 = from_f64<T>(fc[FC_M10 * P]), M11 = from_f64<T>(fc[FC_M11 * P]);
   T* fo = a.fb + ((long long)L.owner * 4 + L.owner_edge) * 3 * NS + i;
   fo[0] = f[0];
   fo[NS] = f[1];
@@ -115,7 +158,7 @@ __device__ __forceinline__ void volume_tangent_body(const TanVolArgs<T>& a, cons
   // multiply-adds started from scale * source
   const double dscale = -dc.two_over_dx * a.ep.scale;
   for (int t = threadIdx.x; t < NS * (NS + 2); t += BLOCK)
-    sD[t / (NS + 2)][t % (NS + 2)] = T(dscale * dc.D[t / (NS + 2)][t % (NS + 2)]);
+    sD[t / (NS + 2)][t % (NS + 2)] = from_f64<T>(dscale * dc.D[t / (NS + 2)][t % (NS + 2)]);
   const int le = threadIdx.x / NN, node = threadIdx.x % NN;
   const long long elem = (long long)blk * EPB + le;
   const bool active = threadIdx.x < EPB * NN && elem < a.nelem;
@@ -129,7 +172,8 @@ __device__ __forceinline__ void volume_tangent_body(const TanVolArgs<T>& a, cons
   T S1 = T(0), S2 = T(0);
   const long long N = a.nodes;
   if (active) {
-    const T v0 = T(__ldg(a.v + idx)), v1 = T(__ldg(a.v + idx + N)), v2 = T(__ldg(a.v + idx + 2 * N));
+    const T v0 = from_f64<T>(__ldg(a.v + idx)), v1 = from_f64<T>(__ldg(a.v + idx + N));
+    const T v2 = from_f64<T>(__ldg(a.v + idx + 2 * N));
     const T* ln = a.ln + idx;
     const T u1 = ln[LN_U1 * N], u2 = ln[LN_U2 * N];
     const T F11 = fma(T(2) * u1, v1, ln[LN_A11 * N] * v0);
@@ -147,6 +191,15 @@ __device__ __forceinline__ void volume_tangent_body(const TanVolArgs<T>& a, cons
   __syncthreads();
   const T src[3] = {T(0), S1, S2};
   double res[3] = {0.0, 0.0, 0.0};
+  // complex64-bulk form: the b-column terms of the augmented operator in FP32
+  // from nu * b_l rounded to FP32 (coefficients y_l of the tail, once per block)
+  constexpr bool F32 = sizeof(T) == 4;
+  __shared__ float coef32[MAX_NB];
+  if (F32 && threadIdx.x < MAX_NB) {
+    const int l = threadIdx.x;
+    coef32[l] = (l < a.ep.p && a.ep.b32[l]) ? f64_to_f32_bits(a.ep.tail_in[l]) : 0.f;
+  }
+  if (F32) __syncthreads();
   if (active) {
     // this thread's rows of the derivative matrix, from shared memory into registers
     // (a per-thread row index into the constant bank would serialise the warp)
@@ -156,7 +209,7 @@ __device__ __forceinline__ void volume_tangent_body(const TanVolArgs<T>& a, cons
       Da[n] = sD[k1][n];
       Db[n] = sD[k2][n];
     }
-    const T sc = T(a.ep.scale);
+    const T sc = from_f64<T>(a.ep.scale);
 #pragma unroll
     for (int mu = 0; mu < 3; ++mu) {
       T acc = (mu == 0) ? T(0) : sc * src[mu];
@@ -168,10 +221,15 @@ __device__ __forceinline__ void volume_tangent_body(const TanVolArgs<T>& a, cons
       acc = fma(Db[NS + 1], sB[le][3][mu][k1], acc);
 #pragma unroll
       for (int l = 0; l < NS; ++l) acc = fma(Db[l + 1], sF[le][1][mu][l * NS + k1], acc);
-      res[mu] = double(acc);
+      if (F32) {
+#pragma unroll
+        for (int l = 0; l < MAX_NB; ++l)
+          if (l < a.ep.p && a.ep.b32[l]) acc = fma(T(coef32[l]), T(__ldg(a.ep.b32[l] + idx + mu * N)), acc);
+      }
+      res[mu] = to_f64<T>(acc);
     }
   }
-  volume_epilogue<BLOCK, true, W3>(a.ep, active, idx, N, res, a.out, blk, nblk);
+  volume_epilogue<BLOCK, true, W3, !F32>(a.ep, active, idx, N, res, a.out, blk, nblk);
 }
 
 }  // namespace swepi

@@ -481,6 +481,9 @@ struct Member {
 struct Ens {
   int device = 0;
   int count = 0;
+  // a run that ended with an error (e.g. a wait that gave up) can leave the
+  // members' phase counters part-way: the next run clears them first
+  bool dyn_stale = false;
   std::vector<Member> mem;
   std::vector<EnsDesc> hdesc;
   std::vector<EnsDyn> hdyn;
@@ -1289,6 +1292,15 @@ using namespace swepi;
 namespace {
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// zero every member's phase counters and tickets (no launch in flight)
+int reset_dyn(sw_ens* e) {
+  if (cudaDeviceSynchronize() != cudaSuccess) return SW_ECUDA;
+  if (cudaMemset(e->d_dyn, 0, sizeof(EnsDyn) * e->count) != cudaSuccess) return SW_ECUDA;
+  e->hdyn.assign(e->count, EnsDyn{});
+  e->dyn_stale = false;
+  return SW_OK;
+}
+
 void ens_release(sw_ens* e) {
   for (int i = 0; i < 3; ++i) {
     if (e->gexec[i]) cudaGraphExecDestroy(e->gexec[i]);
@@ -1437,7 +1449,11 @@ int sw_ens_tune(sw_ens_t e, double* const* q_dev, int iters, int* block, void* s
   if (!e || !q_dev) return SW_EINVAL;
   for (int m = 0; m < e->count; ++m)
     if (!q_dev[m]) return SW_EINVAL;
-  return ens_tune(*e, q_dev, iters, as_stream(stream), block);
+  int rc = e->dyn_stale ? reset_dyn(e) : SW_OK;
+  if (rc) return rc;
+  rc = ens_tune(*e, q_dev, iters, as_stream(stream), block);
+  if (rc) e->dyn_stale = true;
+  return rc;
 }
 
 int sw_ens_epi_run(sw_ens_t e, int steps, const int* orders, const double* dts, double* const* q_dev,
@@ -1452,7 +1468,11 @@ int sw_ens_epi_run(sw_ens_t e, int steps, const int* orders, const double* dts, 
     if (c.jvp_mode != 1 || c.controller) return SW_EINVAL;
   }
   TraceRange trace("ensemble EPI run");
-  return ens_run(*e, steps, orders, dts, q_dev, o, stats, as_stream(stream));
+  int rc = e->dyn_stale ? reset_dyn(e) : SW_OK;
+  if (rc) return rc;
+  rc = ens_run(*e, steps, orders, dts, q_dev, o, stats, as_stream(stream));
+  if (rc) e->dyn_stale = true;
+  return rc;
 }
 
 int sw_ens_set_wait_test(sw_ens_t e, double limit_s, int extra) {
@@ -1463,7 +1483,8 @@ int sw_ens_set_wait_test(sw_ens_t e, double limit_s, int extra) {
   EnsCtl ctl{};
   ctl.extra = (unsigned int)extra;
   ctl.limit_ns = (unsigned long long)(limit_s * 1e9);
-  return cuda_status(cudaMemcpy(e->d_ctl, &ctl, sizeof(EnsCtl), cudaMemcpyHostToDevice));
+  if (cudaMemcpy(e->d_ctl, &ctl, sizeof(EnsCtl), cudaMemcpyHostToDevice) != cudaSuccess) return SW_ECUDA;
+  return reset_dyn(e);
 }
 
 int sw_ens_profile(sw_ens_t e, int enable) {

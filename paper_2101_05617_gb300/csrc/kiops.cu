@@ -139,6 +139,23 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
   ep.p = p;
   for (int l = 0; l < p; ++l) ep.b[l] = bk[p - l];
   ep.skip = c.d_flags;
+  if (use_lin && c.jvp_mode == 2) {
+    // complex64-bulk form: the operator's b-column terms in FP32, from nu * b_l
+    // rounded once per call (the FP32 volume kernels read these instead)
+    if (c.b32_cap < p) {
+      if (c.d_b32) cudaFree(c.d_b32);
+      c.d_b32 = nullptr;
+      c.b32_cap = 0;
+      if (cudaMalloc(&c.d_b32, sizeof(float) * (size_t)p * n) != cudaSuccess) return SW_ENOMEM;
+      c.b32_cap = p;
+    }
+    for (int l = 0; l < p; ++l) {
+      if (!ep.b[l]) continue;
+      float* dst = c.d_b32 + (long long)l * n;
+      if ((rc = launch_to_float_scaled(c, ep.b[l], dst, n, nu, s))) return rc;
+      ep.b32[l] = dst;
+    }
+  }
 
   const double tau_end = tau_out;
   double tau = (o.tau_init > 0) ? std::min(o.tau_init, tau_end) : tau_end;

@@ -104,6 +104,12 @@ __global__ void lincomb_kernel(double* __restrict__ out, long long n, int k, Lin
   }
 }
 
+__global__ void to_float_scaled_kernel(const double* __restrict__ src, float* __restrict__ dst, long long n,
+                                       double scale) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (float)(scale * src[i]);
+}
+
 // w = beta sum_{k<j} F[k][0] V_k (first n entries), beta = scal[0]
 __global__ void combine_kernel(double* __restrict__ X, const double* __restrict__ V, long long ldv, long long n, int j,
                                const double* __restrict__ F, int ldh, const double* scal) {
@@ -354,6 +360,12 @@ int launch_lincomb(Ctx& c, double* out, long long n, int k, const double* const*
   Lin L{};
   for (int j = 0; j < k; ++j) { L.x[j] = xs[j]; L.c[j] = coef[j]; }
   lincomb_kernel<<<blocks_for(n, 256), 256, 0, s>>>(out, n, k, L);
+  c.launches++;
+  return cuda_status(cudaGetLastError());
+}
+
+int launch_to_float_scaled(Ctx& c, const double* src, float* dst, long long n, double scale, cudaStream_t s) {
+  to_float_scaled_kernel<<<blocks_for(n, 256), 256, 0, s>>>(src, dst, n, scale);
   c.launches++;
   return cuda_status(cudaGetLastError());
 }

@@ -134,6 +134,8 @@ struct Ctx {
   double* d_lin_face = nullptr;     // [18][nfacepts]
   float* d_lin_node32 = nullptr;    // FP32 copies (complex64-bulk form)
   float* d_lin_face32 = nullptr;
+  float* d_b32 = nullptr;           // FP32 copies of nu * b_l of the current phi-function call [MAX_NB][n]
+  int b32_cap = 0;                  // vectors allocated in d_b32
   // KIOPS call log and learned control
   Mlp* controller = nullptr;      // not owned
   int epi_order = 0;              // EPI order of the current call (0: direct sw_kiops_phi)
@@ -209,6 +211,10 @@ struct AugEpilogue {
   double nu = 0.0;
   int p = 0;
   const double* b[MAX_NB] = {};
+  // complex64-bulk form: FP32 copies of nu * b[l] (same l); the FP32 volume
+  // kernels add the b-column terms in FP32 from these (the FP64 b[l] are then
+  // not read by them)
+  const float* b32[MAX_NB] = {};
   const double* tail_in = nullptr;  // p doubles (device)
   double* tail_out = nullptr;       // p doubles (device): (tail_in[1..p-1], 0)
   const int* skip = nullptr;        // if non-null and *skip != 0 the kernels return
@@ -259,6 +265,8 @@ int launch_scale_inv(Ctx& c, double* y, const double* x, const double* s_dev, lo
 int launch_expm_prep(Ctx& c, int j, double tau, double tau_happy, cudaStream_t s);
 int launch_expm_eval(Ctx& c, int N, double norm1, int* squarings, cudaStream_t s);
 int launch_combine(Ctx& c, int j, long long n, cudaStream_t s);
+// dst = (float)(scale * src), n entries (the complex64-bulk form's b-column copies)
+int launch_to_float_scaled(Ctx& c, const double* src, float* dst, long long n, double scale, cudaStream_t s);
 // fused incomplete orthogonalisation (window two or three) after an epilogue
 // with dots: z -= h0 V_C + h1 V_A + h2 V_B and ||z|| -> *hsub (happy flag below
 // tol), then V_next = z / *hsub, V_next . V_B -> *c_out and, with V_A given,
