@@ -134,6 +134,10 @@ struct VolShape {
 };
 
 
+template <int THREADS, bool W3>
+__device__ __forceinline__ void epilogue_finish(const AugEpilogue& ep, double da, double db, double dcc,
+                                                unsigned int blk, unsigned int nblk);
+
 // Epilogue of the volume kernels (all threads of the block call it; blk/nblk:
 // this block's index and the number of blocks working on the same vector):
 // out = scale * res + nu * sum_l y_l b_{p-l} (the augmented operator of the
@@ -171,6 +175,17 @@ __device__ __forceinline__ void volume_epilogue(const AugEpilogue& ep, bool acti
       }
     }
   }
+  epilogue_finish<THREADS, W3>(ep, da, db, dcc, blk, nblk);
+}
+
+// Second half of the volume epilogue (all threads of the block call it, with
+// their partial window dots da = z . V_{j-1}, db = z . V_j, dcc = z . V_{j-2}
+// over their nodes): the shift of the augmented tail, the tail's share of the
+// dots, the block sums and -- in the last block to finish -- the modified
+// Gram-Schmidt coefficients.
+template <int THREADS, bool W3>
+__device__ __forceinline__ void epilogue_finish(const AugEpilogue& ep, double da, double db, double dcc,
+                                                unsigned int blk, unsigned int nblk) {
   if (ep.tail_out && blk == 0 && threadIdx.x < ep.p)
     ep.tail_out[threadIdx.x] = (threadIdx.x + 1 < ep.p) ? ep.tail_in[threadIdx.x + 1] : 0.0;
   if (!ep.dotB) return;   // uniform over the grid

@@ -112,6 +112,8 @@ __global__ void __launch_bounds__(128) lin_face_kernel(LinFaceArgs a, DfrConst d
 // single-grid kernels around the shared bodies (dfr_tangent.cuh)
 template <typename T, int NS>
 __global__ void __launch_bounds__(128) face_tangent_kernel(TanFaceArgs<T> a, DfrConst dc) {
+  pdl_wait();
+  pdl_trigger();
   if (a.skip && *a.skip) return;
   face_tangent_body<T, NS>(a, dc, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
@@ -119,6 +121,8 @@ __global__ void __launch_bounds__(128) face_tangent_kernel(TanFaceArgs<T> a, Dfr
 // W3: with the orthogonalisation window of three in the epilogue
 template <typename T, int NS, bool W3>
 __global__ void __launch_bounds__(VolShape<NS>::THREADS) volume_tangent_kernel(TanVolArgs<T> a, DfrConst dc) {
+  pdl_wait();
+  pdl_trigger();
   if (a.ep.skip && *a.ep.skip) return;
   __shared__ VolSmem<T, NS, VolShape<NS>::EPB> sm;
   volume_tangent_body<T, NS, VolShape<NS>::EPB, VolShape<NS>::THREADS, W3>(a, dc, blockIdx.x, gridDim.x, sm);
@@ -149,17 +153,28 @@ int tangent_ns(Ctx& c, const double* v, double* out, const AugEpilogue& ep, cons
     cudaEventRecord(e0, s);
   }
   TanFaceArgs<T> fa{v, c.nodes, c.d_lines, c.d_face_coef, lf, c.nfacepts, fb, ep.skip};
-  face_tangent_kernel<T, NS><<<(unsigned)((c.nfacepts + 127) / 128), 128, 0, s>>>(fa, c.dc);
+  if (launch_pdl(face_tangent_kernel<T, NS>, dim3((unsigned)((c.nfacepts + 127) / 128)), dim3(128), s, fa, c.dc) !=
+      cudaSuccess)
+    return SW_ECUDA;
   if (pf || pv) {
     e1 = prof_event(c);
     cudaEventRecord(e1, s);
   }
   TanVolArgs<T> va{v, c.nodes, c.nelem, ln, fb, out, ep};
   const long long vblocks = (c.nelem + VolShape<NS>::EPB - 1) / VolShape<NS>::EPB;
-  if (ep.dotC)
-    volume_tangent_kernel<T, NS, true><<<(unsigned)vblocks, VolShape<NS>::THREADS, 0, s>>>(va, c.dc);
-  else
-    volume_tangent_kernel<T, NS, false><<<(unsigned)vblocks, VolShape<NS>::THREADS, 0, s>>>(va, c.dc);
+  int rt = 1;
+  if (sizeof(T) == 4) {   // complex64-bulk form: element tiles staged by bulk copies where aligned
+    rt = launch_volume_tile_f32<NS>(c, v, out, ep, s);
+    if (rt < 0) return rt;
+    if (rt == SW_OK) c.launches--;   // counted below
+  }
+  if (rt != SW_OK) {
+    const cudaError_t ev = ep.dotC ? launch_pdl(volume_tangent_kernel<T, NS, true>, dim3((unsigned)vblocks),
+                                                 dim3(VolShape<NS>::THREADS), s, va, c.dc)
+                                   : launch_pdl(volume_tangent_kernel<T, NS, false>, dim3((unsigned)vblocks),
+                                                dim3(VolShape<NS>::THREADS), s, va, c.dc);
+    if (ev != cudaSuccess) return SW_ECUDA;
+  }
   if (pv) {
     e2 = prof_event(c);
     cudaEventRecord(e2, s);

@@ -1,0 +1,289 @@
+// Imaginary half of the split complex-step JVP (Eq. 28) in the complex64-bulk
+// form, with each element tile staged in shared memory by bulk asynchronous
+// copies (the Hopper/Blackwell copy engine: cp.async.bulk completing on an
+// mbarrier).
+//
+// Per block, one thread issues the one-dimensional copies of everything the
+// tile's nodes read -- the Krylov vector v (FP64), the FP32 linearisation
+// coefficients, the FP32 interface fluxes of the tile's elements (written by
+// the face kernel), the FP32 b-column copies of the augmented operator and the
+// FP64 orthogonalisation window vectors -- so that all of a tile's HBM traffic
+// is in flight at once; the threads then compute from shared memory exactly
+// what volume_tangent_body computes (pointwise imaginary fluxes and sources,
+// the DFR sweeps of Eq. 12-14, the augmented operator, the window dots of the
+// incomplete orthogonalisation) and share its epilogue.
+//
+// The copies need 16-byte aligned addresses and sizes: a tile holds EPB
+// elements with EPB (p+1)^2 a multiple of four, and the launcher falls back to
+// the register-and-cache kernel (dfr_split.cu) when the grid or a pointer does
+// not satisfy this.  The wait on the mbarrier is bounded: after ~2 s the block
+// sets the context's flag (reported as SW_ETIMEOUT by the phi-function solver),
+// waits once more with the same bound for its own copies, takes part in the
+// epilogue's reduction with zero contributions and returns.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "dfr_tangent.cuh"
+#include "swepi_internal.h"
+
+namespace swepi {
+
+namespace {
+
+constexpr int KMAXB = 4;     // b-column vectors staged per tile (EPI orders up to 6 use p <= 4)
+
+constexpr int tile_epb(int nn) {
+  int e = (256 / nn) > 0 ? (256 / nn) : 1;
+  while (e > 1 && (e * nn) % 4 != 0) --e;
+  return e;
+}
+
+template <int NS>
+struct TileShape {
+  static constexpr int NN = NS * NS;
+  static constexpr int EPB = tile_epb(NN);
+  static constexpr int TN = EPB * NN;   // nodes (threads) per tile
+};
+
+constexpr size_t up16(size_t b) { return (b + 15) / 16 * 16; }
+
+// byte offsets of the regions of the dynamic shared memory of one tile
+template <int NS>
+struct TileLayout {
+  static constexpr int TN = TileShape<NS>::TN, EPB = TileShape<NS>::EPB, NN = NS * NS;
+  static constexpr size_t v = 0;                                            // double [3][TN]
+  static constexpr size_t dots = v + up16(sizeof(double) * 3 * TN);         // double [3 (C, A, B)][3][TN]
+  static constexpr size_t ln = dots + up16(sizeof(double) * 9 * TN);        // float [LN_COUNT][TN]
+  static constexpr size_t b32 = ln + up16(sizeof(float) * LN_COUNT * TN);   // float [KMAXB][3][TN]
+  static constexpr size_t fb = b32 + up16(sizeof(float) * KMAXB * 3 * TN);  // float [EPB][4][3][NS]
+  static constexpr size_t flux = fb + up16(sizeof(float) * EPB * 12 * NS);  // float [EPB][2][3][NN]
+  static constexpr size_t dmat = flux + up16(sizeof(float) * EPB * 6 * NN); // float [NS][NS + 3]
+  static constexpr size_t mbar = dmat + up16(sizeof(float) * NS * (NS + 3));
+  static constexpr size_t bytes = mbar + 16;
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(mbar))
+               : "memory");
+}
+
+// wait for phase 0 of the tile's mbarrier; false after ~2 s (or 2^26 polls)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar) {
+  const unsigned m = smem_addr(mbar);
+  const unsigned long long t0 = now_ns();
+  for (unsigned it = 0; it < (1u << 26); ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(m)
+        : "memory");
+    if (done) return true;
+    if ((it & 255u) == 255u && now_ns() - t0 > 2000000000ull) return false;
+  }
+  return false;
+}
+
+template <int NS, bool W3>
+__global__ void __launch_bounds__(TileShape<NS>::TN, 3) volume_tangent_tile_f32_kernel(TanVolArgs<float> a,
+                                                                                      DfrConst dc, int* err) {
+  using L = TileLayout<NS>;
+  constexpr int NN = NS * NS, EPB = TileShape<NS>::EPB, TN = TileShape<NS>::TN;
+  extern __shared__ __align__(16) unsigned char sm[];
+  double* sv = reinterpret_cast<double*>(sm + L::v);
+  double* sdot = reinterpret_cast<double*>(sm + L::dots);
+  float* sln = reinterpret_cast<float*>(sm + L::ln);
+  float* sb32 = reinterpret_cast<float*>(sm + L::b32);
+  float* sfb = reinterpret_cast<float*>(sm + L::fb);
+  float (*sF)[2][3][NN] = reinterpret_cast<float (*)[2][3][NN]>(sm + L::flux);
+  float (*sD)[NS + 3] = reinterpret_cast<float (*)[NS + 3]>(sm + L::dmat);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + L::mbar);
+
+  pdl_wait();
+  pdl_trigger();
+  const AugEpilogue& ep = a.ep;
+  if (ep.skip && *ep.skip) return;
+  const unsigned blk = blockIdx.x, nblk = gridDim.x;
+  const long long N = a.nodes;
+  const long long tile0 = (long long)blk * TN;
+  const long long left = N - tile0;
+  const int tn = left < TN ? (int)left : TN;                  // nodes of this tile
+  const int ne = tn / NN;                                      // elements of this tile
+  const bool dA = ep.dotA != nullptr, dB = ep.dotB != nullptr, dC = W3 && ep.dotC != nullptr;
+
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned bd = (unsigned)(sizeof(double) * tn), bf = (unsigned)(sizeof(float) * tn);
+    unsigned tx = 3 * bd + LN_COUNT * bf + (unsigned)(sizeof(float) * ne * 12 * NS);
+    const double* dsrc[3] = {W3 ? ep.dotC : nullptr, ep.dotA, ep.dotB};
+    for (int k = 0; k < 3; ++k)
+      if (dsrc[k] && (k > 0 || dC)) tx += 3 * bd;
+    for (int l = 0; l < ep.p && l < KMAXB; ++l)
+      if (ep.b32[l]) tx += 3 * bf;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(tx)
+                 : "memory");
+    for (int var = 0; var < 3; ++var) bulk_g2s(sv + var * TN, a.v + tile0 + var * N, bd, mbar);
+    for (int k = 0; k < 3; ++k) {
+      if (!dsrc[k] || (k == 0 && !dC)) continue;
+      for (int var = 0; var < 3; ++var)
+        bulk_g2s(sdot + (k * 3 + var) * TN, dsrc[k] + tile0 + var * N, bd, mbar);
+    }
+    for (int c = 0; c < LN_COUNT; ++c) bulk_g2s(sln + c * TN, a.ln + tile0 + c * N, bf, mbar);
+    for (int l = 0; l < ep.p && l < KMAXB; ++l) {
+      if (!ep.b32[l]) continue;
+      for (int var = 0; var < 3; ++var)
+        bulk_g2s(sb32 + (l * 3 + var) * TN, ep.b32[l] + tile0 + var * N, bf, mbar);
+    }
+    bulk_g2s(sfb, a.fb + (long long)blk * EPB * 12 * NS, (unsigned)(sizeof(float) * ne * 12 * NS), mbar);
+  }
+  // while the copies are in flight: the pre-scaled derivative matrix and the
+  // tail coefficients of the b-column terms
+  const double dscale = -dc.two_over_dx * ep.scale;
+  for (int t = threadIdx.x; t < NS * (NS + 2); t += TN)
+    sD[t / (NS + 2)][t % (NS + 2)] = f64_to_f32_bits(dscale * dc.D[t / (NS + 2)][t % (NS + 2)]);
+  __shared__ float coef32[KMAXB];
+  if (threadIdx.x < KMAXB) {
+    const int l = threadIdx.x;
+    coef32[l] = (l < ep.p && ep.b32[l]) ? f64_to_f32_bits(ep.tail_in[l]) : 0.f;
+  }
+  bool ok = mbar_wait_bounded(mbar);
+  if (!ok) {
+    atomicExch(err, 1);
+    mbar_wait_bounded(mbar);   // do not leave with this block's copies still landing
+  }
+  ok = __syncthreads_and(ok);
+  const int t = threadIdx.x;
+  const bool active = ok && t < tn;
+  const int le = t / NN, node = t % NN, k2 = node / NS, k1 = node % NS;
+  float S1 = 0.f, S2 = 0.f;
+  if (active) {
+    const float v0 = f64_to_f32_bits(sv[t]), v1 = f64_to_f32_bits(sv[TN + t]), v2 = f64_to_f32_bits(sv[2 * TN + t]);
+    const float u1 = sln[LN_U1 * TN + t], u2 = sln[LN_U2 * TN + t];
+    const float F11 = fmaf(2.f * u1, v1, sln[LN_A11 * TN + t] * v0);
+    const float F12 = fmaf(u2, v1, fmaf(u1, v2, sln[LN_A12 * TN + t] * v0));
+    const float F22 = fmaf(2.f * u2, v2, sln[LN_A22 * TN + t] * v0);
+    S1 = fmaf(sln[LN_S11 * TN + t], v1, fmaf(sln[LN_S12 * TN + t], v2, sln[LN_S10 * TN + t] * v0));
+    S2 = fmaf(sln[LN_S21 * TN + t], v1, fmaf(sln[LN_S22 * TN + t], v2, sln[LN_S20 * TN + t] * v0));
+    sF[le][0][0][node] = v1;
+    sF[le][0][1][node] = F11;
+    sF[le][0][2][node] = F12;
+    sF[le][1][0][node] = v2;
+    sF[le][1][1][node] = F12;
+    sF[le][1][2][node] = F22;
+  }
+  __syncthreads();
+  double da = 0.0, db = 0.0, dcc = 0.0;
+  if (active) {
+    float Da[NS + 2], Db[NS + 2];
+#pragma unroll
+    for (int n = 0; n < NS + 2; ++n) {
+      Da[n] = sD[k1][n];
+      Db[n] = sD[k2][n];
+    }
+    const float sc = f64_to_f32_bits(ep.scale);
+    const float src[3] = {0.f, S1, S2};
+    const float* fbe = sfb + le * 12 * NS;   // [edge][mu][k] of this element
+    const long long idx = tile0 + t;
+#pragma unroll
+    for (int mu = 0; mu < 3; ++mu) {
+      float acc = (mu == 0) ? 0.f : sc * src[mu];
+      acc = fmaf(Da[0], fbe[(0 * 3 + mu) * NS + k2], acc);
+      acc = fmaf(Da[NS + 1], fbe[(1 * 3 + mu) * NS + k2], acc);
+#pragma unroll
+      for (int l = 0; l < NS; ++l) acc = fmaf(Da[l + 1], sF[le][0][mu][k2 * NS + l], acc);
+      acc = fmaf(Db[0], fbe[(2 * 3 + mu) * NS + k1], acc);
+      acc = fmaf(Db[NS + 1], fbe[(3 * 3 + mu) * NS + k1], acc);
+#pragma unroll
+      for (int l = 0; l < NS; ++l) acc = fmaf(Db[l + 1], sF[le][1][mu][l * NS + k1], acc);
+#pragma unroll
+      for (int l = 0; l < KMAXB; ++l)
+        if (l < ep.p && ep.b32[l]) acc = fmaf(coef32[l], sb32[(l * 3 + mu) * TN + t], acc);
+      const double o = f32_to_f64_bits(acc);
+      a.out[idx + mu * N] = o;
+      if (dB) {
+        db = fma(o, sdot[(2 * 3 + mu) * TN + t], db);
+        if (dA) da = fma(o, sdot[(1 * 3 + mu) * TN + t], da);
+        if (dC) dcc = fma(o, sdot[(0 * 3 + mu) * TN + t], dcc);
+      }
+    }
+  }
+  epilogue_finish<TN, W3>(ep, da, db, dcc, blk, nblk);
+}
+
+template <int NS>
+bool tile_eligible(const Ctx& c, const double* v, const double* out, const AugEpilogue& ep) {
+  auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  if (c.nodes % 4 != 0 || ep.p > KMAXB || !al(v) || !al(c.d_lin_node32) || !al(c.d_fb)) return false;
+  if ((ep.dotA && !al(ep.dotA)) || (ep.dotB && !al(ep.dotB)) || (ep.dotC && !al(ep.dotC))) return false;
+  for (int l = 0; l < ep.p && l < MAX_NB; ++l) {
+    if (ep.b[l] && !ep.b32[l]) return false;
+    if (ep.b32[l] && !al(ep.b32[l])) return false;
+  }
+  (void)out;
+  return true;
+}
+
+template <int NS, bool W3>
+int launch_tile(Ctx& c, const double* v, double* out, const AugEpilogue& ep, cudaStream_t s) {
+  using L = TileLayout<NS>;
+  static bool configured = false;
+  auto kernel = volume_tangent_tile_f32_kernel<NS, W3>;
+  if (!configured) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes) != cudaSuccess)
+      return SW_ECUDA;
+    configured = true;
+  }
+  TanVolArgs<float> va{v, c.nodes, c.nelem, c.d_lin_node32, reinterpret_cast<const float*>(c.d_fb), out, ep};
+  const long long tiles = (c.nodes + TileShape<NS>::TN - 1) / TileShape<NS>::TN;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)tiles);
+  cfg.blockDim = dim3(TileShape<NS>::TN);
+  cfg.dynamicSmemBytes = L::bytes;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int* err = c.d_flags + 3;
+  if (cudaLaunchKernelEx(&cfg, kernel, va, c.dc, err) != cudaSuccess) return SW_ECUDA;
+  c.launches++;
+  return SW_OK;
+}
+
+}  // namespace
+
+// returns SW_OK after launching, 1 when the grid or a pointer is not eligible
+// (the caller then launches the register-and-cache kernel)
+template <int NS>
+int launch_volume_tile_f32(Ctx& c, const double* v, double* out, const AugEpilogue& ep, cudaStream_t s) {
+  if (!tile_eligible<NS>(c, v, out, ep)) return 1;
+  return ep.dotC ? launch_tile<NS, true>(c, v, out, ep, s) : launch_tile<NS, false>(c, v, out, ep, s);
+}
+
+template int launch_volume_tile_f32<1>(Ctx&, const double*, double*, const AugEpilogue&, cudaStream_t);
+template int launch_volume_tile_f32<2>(Ctx&, const double*, double*, const AugEpilogue&, cudaStream_t);
+template int launch_volume_tile_f32<3>(Ctx&, const double*, double*, const AugEpilogue&, cudaStream_t);
+template int launch_volume_tile_f32<4>(Ctx&, const double*, double*, const AugEpilogue&, cudaStream_t);
+template int launch_volume_tile_f32<5>(Ctx&, const double*, double*, const AugEpilogue&, cudaStream_t);
+template int launch_volume_tile_f32<6>(Ctx&, const double*, double*, const AugEpilogue&, cudaStream_t);
+template int launch_volume_tile_f32<7>(Ctx&, const double*, double*, const AugEpilogue&, cudaStream_t);
+template int launch_volume_tile_f32<8>(Ctx&, const double*, double*, const AugEpilogue&, cudaStream_t);
+
+}  // namespace swepi

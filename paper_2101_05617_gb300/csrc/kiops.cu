@@ -48,6 +48,8 @@ int read_back(Ctx& c, cudaStream_t s) {
   return SW_OK;
 }
 const int* pinned_flags(const Ctx& c) { return reinterpret_cast<const int*>(c.h_pinned + 32); }
+// flags[3]: a bounded wait of a staged volume kernel gave up (dfr_tile.cu)
+bool wait_gave_up(const Ctx& c) { return pinned_flags(c)[3] != 0; }
 
 void free_ptr(double*& p) {
   if (p) cudaFree(p);
@@ -109,6 +111,7 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
       return SW_ECUDA;
     }
   }
+  if (cudaMemsetAsync(c.d_flags + 3, 0, sizeof(int), s) != cudaSuccess) return SW_ECUDA;
   // X = [b_0; 0 .. 0 mu]
   if (bk[0]) {
     if (cudaMemcpyAsync(c.d_X, bk[0], sizeof(double) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return SW_ECUDA;
@@ -239,6 +242,7 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
       if ((rc = launch_expm_eval(c, Ne, c.h_pinned[S_STAT + 5], nullptr, s))) return rc;
     }
     if ((rc = read_back(c, s))) return rc;
+    if (wait_gave_up(c)) return SW_ETIMEOUT;
     const int* fl = pinned_flags(c);
     const bool happy = fl[0] != 0;
     if ((rc = K.decide(happy, happy ? fl[1] : m_cur, c.h_pinned[S_BETA], c.h_pinned[S_STAT + 4],

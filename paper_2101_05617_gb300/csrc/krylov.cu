@@ -154,6 +154,8 @@ __global__ void __launch_bounds__(RED_THREADS) update_norm_kernel(double* __rest
                                                                   unsigned int* ticket, double* hsub, double tol,
                                                                   int* happy, int happy_value,
                                                                   const double* __restrict__ VC, const double* h0p) {
+  pdl_wait();
+  pdl_trigger();
   if (happy[0]) return;
   const double h1 = VA ? *h1p : 0.0, h2 = *h2p, h0 = VC ? *h0p : 0.0;
   const double acc = mgs_update_range(z, VA, VB, h1, h2, (long long)blockIdx.x * blockDim.x + threadIdx.x, n,
@@ -188,6 +190,8 @@ __global__ void __launch_bounds__(RED_THREADS) scale_dot_kernel(double* __restri
                                                                 const double* hsub, long long n, double* partials,
                                                                 unsigned int* ticket, double* c_out, const int* happy,
                                                                 const double* __restrict__ VA, double* c2_out) {
+  pdl_wait();
+  pdl_trigger();
   if (happy[0]) return;
   const double r = 1.0 / *hsub;
   double acc2 = 0.0;
@@ -317,9 +321,9 @@ int launch_update_norm(Ctx& c, double* z, const double* VA, const double* VB, co
     e1 = prof_event(c);
     cudaEventRecord(e0, s);
   }
-  update_norm_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(z, VA, VB, h1, h2, N, c.d_partials,
-                                                       (unsigned int*)(c.d_flags + 8), hsub, tol, c.d_flags,
-                                                       happy_value, VC, h0);
+  if (launch_pdl(update_norm_kernel, dim3(RED_BLOCKS), dim3(RED_THREADS), s, z, VA, VB, h1, h2, N, c.d_partials,
+                 (unsigned int*)(c.d_flags + 8), hsub, tol, c.d_flags, happy_value, VC, h0) != cudaSuccess)
+    return SW_ECUDA;
   if (prof_on(c, PK_ORTH)) {
     cudaEventRecord(e1, s);
     prof_record(c, PK_ORTH, e0, e1);
@@ -336,8 +340,9 @@ int launch_scale_dot(Ctx& c, double* z, const double* VB, const double* hsub, lo
     e1 = prof_event(c);
     cudaEventRecord(e0, s);
   }
-  scale_dot_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(z, VB, hsub, N, c.d_partials, (unsigned int*)(c.d_flags + 8),
-                                                     c_out, c.d_flags, VA, c2_out);
+  if (launch_pdl(scale_dot_kernel, dim3(RED_BLOCKS), dim3(RED_THREADS), s, z, VB, hsub, N, c.d_partials,
+                 (unsigned int*)(c.d_flags + 8), c_out, c.d_flags, VA, c2_out) != cudaSuccess)
+    return SW_ECUDA;
   if (prof_on(c, PK_ORTH)) {
     cudaEventRecord(e1, s);
     prof_record(c, PK_ORTH, e0, e1);

@@ -245,6 +245,12 @@ int launch_jvp(Ctx& c, const double* q, const double* v, double eps, double* out
 int launch_linearize(Ctx& c, const double* q, cudaStream_t s);
 // fp32: the imaginary half in FP32 (complex64-bulk form; needs a mode-2 linearisation)
 int launch_jvp_lin(Ctx& c, const double* v, double* out, const AugEpilogue& ep, cudaStream_t s, bool fp32);
+// the FP32 tangent volume kernel with bulk-copy staging of each element tile
+// (dfr_tile.cu): SW_OK when launched, 1 when the grid or a pointer does not
+// meet its 16-byte alignment (the caller then launches volume_tangent_kernel);
+// a tile wait that gave up sets d_flags[3]
+template <int NS>
+int launch_volume_tile_f32(Ctx& c, const double* v, double* out, const AugEpilogue& ep, cudaStream_t s);
 // the JVP with a caller-supplied interface-flux buffer (nelem * 12 * ns doubles)
 int launch_jvp_fb(Ctx& c, const double* q, const double* v, double eps, double* out, double* fb,
                   cudaStream_t s);
@@ -288,6 +294,33 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
 int ensure_krylov(Ctx& c, int m_max);
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? SW_OK : SW_ECUDA; }
+
+// Programmatic dependent launch for the kernels of one Krylov iteration (face
+// and volume tangent kernels, the two orthogonalisation passes): a kernel
+// launched by launch_pdl can be scheduled while its predecessor on the stream
+// is still running, so the launch latency between consecutive kernels is
+// hidden.  Each such kernel calls pdl_wait() before its first global memory
+// access of any kind (which returns once the predecessor has completed and its
+// writes are visible) and pdl_trigger() to let its own successor be scheduled.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+#endif
 
 }  // namespace swepi
 

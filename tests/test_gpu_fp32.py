@@ -115,3 +115,28 @@ def test_precision_one_at_init_equals_mode_two():
     for _ in range(6):
         c.epi_step(5, wl.dt, qc, tol=wl.tol)
     assert not torch.equal(qa, qc)
+
+
+@pytest.mark.parametrize("ne,ns,seed", [(4, 6, 0), (4, 7, 2), (6, 3, 1)])
+def test_fp32_staged_tile_kernel_equals_register_kernel(ne, ns, seed):
+    """The complex64-bulk volume kernel stages each element tile in shared memory
+    by bulk asynchronous copies when every address is 16-byte aligned, and
+    otherwise runs the register-and-cache kernel; both perform the same FP32
+    operations in the same order, so a direction vector given 8 bytes off
+    alignment (the fallback) must give the same product bit for bit, and both
+    match the oracle within the FP32 bound."""
+    _, g, q, _ = oracle_case(ne, ns, seed=seed)
+    ctx = _ctx(g, 2)
+    qd = torch.tensor(q.reshape(-1), device="cuda")
+    ctx.linearize(qd)
+    v = scaled_direction(q, seed + 500).reshape(-1)
+    buf = torch.zeros(v.size + 2, dtype=torch.float64, device="cuda")
+    aligned = torch.tensor(v, device="cuda")
+    shifted = buf[1:v.size + 1]
+    shifted.copy_(aligned)
+    assert aligned.data_ptr() % 16 == 0 and shifted.data_ptr() % 16 == 8
+    a = ctx.jvp_linearized(aligned)
+    b = ctx.jvp_linearized(shifted)
+    assert torch.equal(a, b)
+    err = scaled_err_per_var(a.cpu().numpy(), osw.jvp(g, q, v.reshape(q.shape)), term_scale(g, q, v.reshape(q.shape)))
+    assert max(err) < TOL_JVP32, err
