@@ -64,15 +64,21 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
-    ap.add_argument("--large", action="store_true",
-                    help="also run the 6x90x90, p=6 EPI6 instance (FP64 and complex64-bulk, per-kernel rooflines)")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 6x90x90, p=6 EPI6 instance (FP64 and complex64-bulk, per-kernel rooflines)")
     ap.add_argument("--only-forms", default="",
                     help="comma-separated forms to run (learned, ne30, ne60, ensemble, large); default all")
     ap.add_argument("--control", default="plain", choices=["learned", "plain"])
     ap.add_argument("--oracle-full-step", action="store_true",
                     help="time one complete oracle EPI step of the workload on one host core and exit")
-    ap.add_argument("--jvp-mode", type=int, default=1, choices=[0, 1],
-                    help="0: full complex-step evaluation per JVP, 1: split (default)")
+    ap.add_argument("--jvp-mode", type=int, default=1, choices=[0, 1, 2],
+                    help="0: full complex-step evaluation per JVP, 1: split (default), 2: complex64-bulk "
+                         "(--kiops-call only; the timed step is the FP64 path)")
+    ap.add_argument("--kiops-call", action="store_true",
+                    help="one phi-function call on the workload (b = [0, dt F, 1e-3 dt F shifted, ...]) with "
+                         "--jvp-mode, --iop and --m-max, then exit: the small case for kernel profiles")
+    ap.add_argument("--iop", type=int, default=2)
+    ap.add_argument("--m-max", type=int, default=24)
     return ap.parse_args()
 
 
@@ -382,7 +388,7 @@ def kernel_rooflines(prof, wl, mode, iop, step_ms, fp64_peak):
 
 
 def fp32_form_comparison(args, dev, workload="ne30_p5", variants=(("fp64", 1, 2), ("complex64_bulk", 2, 2)),
-                         fp64_peak=None, total_steps=None):
+                         fp64_peak=None, total_steps=None, dt=None):
     """The complex64-bulk form against the FP64 path: steps/s of each variant
     (name, JVP mode, orthogonalisation window[, "learned": the learned initial
     substep after the warm-up]) from the same start, each variant's state
@@ -401,8 +407,9 @@ def fp32_form_comparison(args, dev, workload="ne30_p5", variants=(("fp64", 1, 2)
     states = {}
     kernels = {}
     stats = {}
-    runs = [(v[0], v[1], v[2], wl.dt, 1, len(v) > 3 and v[3] == "learned") for v in variants]
-    runs.append(("fp64_dt4", 1, 2, wl.dt / 4, 4, False))
+    dt0 = wl.dt if dt is None else dt
+    runs = [(v[0], v[1], v[2], dt0, 1, len(v) > 3 and v[3] == "learned") for v in variants]
+    runs.append(("fp64_dt4", 1, 2, dt0 / 4, 4, False))
     ctl = None
     fields = None   # the same grid and rotation for every run: evaluate the fields once
     for name, mode, iop, dt, mult, use_ctl in runs:
@@ -453,7 +460,7 @@ def fp32_form_comparison(args, dev, workload="ne30_p5", variants=(("fp64", 1, 2)
         return [float(torch.linalg.norm(a[k] - b[k]) / torch.linalg.norm(b[k])) for k in range(3)]
     base = variants[0][0]
     ok = lambda k: states.get(k) is not None   # noqa: E731
-    out = {"workload": f"{workload}: 6x{wl.ne}x{wl.ne} elements, p={wl.p}, EPI{wl.order}, dt={wl.dt:g} s, "
+    out = {"workload": f"{workload}: 6x{wl.ne}x{wl.ne} elements, p={wl.p}, EPI{wl.order}, dt={dt0:g} s, "
                        f"KIOPS tol {wl.tol:g}",
            "steps": warm + timed, "timed_steps": timed,
            "time_discretisation_err_rel_l2": rel(states[base], states["fp64_dt4"])
@@ -477,11 +484,17 @@ def fp32_form_comparison(args, dev, workload="ne30_p5", variants=(("fp64", 1, 2)
     return out
 
 
+# The largest time step (of 1200, 900, 600 s) at which EPI6 on the 6 x 90 x 90,
+# p = 6 workload stays stable over its 36 steps on the GB300 (FP64 path,
+# diagnostics after every step; the complex64-bulk form behaves the same).
+LARGE_STABLE_DT = 600.0
+
 # One complete oracle EPI5 multistep step on the default workload (6 x 60 x 60,
-# p = 5; history q_{n-i} = q_n - i dt F(q_n)), measured on one host core of the
-# GB300 machine by `python bench.py --oracle-full-step`: its own KIOPS counts (used
-# to project the reference arm's sampled step) and its wall time.
-ORACLE_STEP_NE60_P5 = {"krylov_iters": 390, "attempts": 5, "substeps": 3, "seconds": None, "measured": False}
+# p = 5; history q_{n-i} = q_n - i dt F(q_n)), measured on one host core by
+# `python bench.py --oracle-full-step`: its own KIOPS counts (used to project the
+# reference arm's sampled step) and its wall time.
+ORACLE_STEP_NE60_P5 = {"krylov_iters": 384, "attempts": 13, "substeps": 3, "seconds": 342.3,
+                       "host": "one x86-64 core of the build container (the counts do not depend on the host)"}
 
 
 def ensemble_form(args, dev, fp64_peak):
@@ -617,6 +630,29 @@ def run_reference(args, world, rank):
     print(json.dumps(out), flush=True)
 
 
+def run_kiops_call(args):
+    """One phi-function call (Eq. 29) at the workload's first state: b_0 = 0,
+    b_1 = dt F(q), b_2, b_3 = 1e-3 and 1e-4 dt F(q) shifted by 7 and 11 entries;
+    Krylov size fixed at --m-max (tolerance 1e-6), window --iop, JVP form
+    --jvp-mode.  Prints the solver statistics."""
+    import torch
+
+    from paper_2101_05617_gb300 import synth
+    from paper_2101_05617_gb300.swepi import SWContext
+    wl = synth.WORKLOADS[args.workload]
+    f = synth.make_fields(wl, args.seed)
+    ctx = SWContext(wl.ne, wl.p, f.rotation)
+    q = torch.tensor(ctx.state_from_fields(*f.evaluate(ctx.node_xyz())), device="cuda")
+    ctx.set_jvp_mode(args.jvp_mode)
+    b1 = wl.dt * ctx.rhs(q)
+    t0 = time.perf_counter()
+    _, st = ctx.kiops_phi(q, wl.dt, [None, b1, 1e-3 * b1.roll(7), 1e-4 * b1.roll(11)], m_max=args.m_max, m_min=10,
+                          m_init=args.m_max, iop=args.iop, tol=1e-6)
+    torch.cuda.synchronize()
+    print(json.dumps({"kiops_call": {"workload": wl.name, "jvp_mode": args.jvp_mode, "iop": args.iop,
+                                     "m_max": args.m_max, "seconds": time.perf_counter() - t0, **st}}), flush=True)
+
+
 def run_oracle_full_step(args):
     """One complete oracle EPI step of the workload on one host core, measured
     (not projected): history q_{n-i} = q_n - i dt F(q_n) for the P previous
@@ -651,6 +687,9 @@ def main():
     if args.oracle_full_step:
         run_oracle_full_step(args)
         return
+    if args.kiops_call:
+        run_kiops_call(args)
+        return
     world, rank, local, pg = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
@@ -673,6 +712,8 @@ def main():
     h, hB, V = f.evaluate(ctx.node_xyz())
     q_host = ctx.state_from_fields(h, hB, V)
     q = torch.tensor(q_host, device=dev)
+    if args.jvp_mode == 2:
+        raise SystemExit("--jvp-mode 2 applies to --kiops-call; the timed step is the FP64 path")
     ctx.set_jvp_mode(args.jvp_mode)
     opts = dict(tol=wl.tol)
     stream = torch.cuda.current_stream()
@@ -843,11 +884,14 @@ def main():
                     total_steps=48))
             if world == 1 and not args.no_ensemble:
                 form("ensemble_96", lambda: ensemble_form(args, dev, peak))
-            if world == 1 and (args.large or "large" in only):
-                # the large single instance: 6 x 90 x 90 elements, p = 6, bottom topography, EPI6
-                # (opt-in: minutes, most of them the host-side evaluation of its degree-32 fields)
+            if world == 1 and not args.no_large:
+                # the large single instance: 6 x 90 x 90 elements, p = 6, bottom topography, EPI6 over its
+                # configured 36 steps at dt = 600 s: at the configured 1200 s (and at 900 s) the FP64 method
+                # itself goes unstable within the 36 steps (the order-6 vorticity growth), at 600 s both
+                # forms stay finite
                 form("large_ne90_p6", lambda: fp32_form_comparison(
-                    args, dev, "ne90_p6", (("fp64", 1, 2), ("complex64_bulk_window3", 2, 3)), fp64_peak=peak))
+                    args, dev, "ne90_p6", (("fp64", 1, 2), ("complex64_bulk_window3", 2, 3)), fp64_peak=peak,
+                    total_steps=36, dt=LARGE_STABLE_DT))
         if world == 1 and not args.no_cpu_baseline:
             counts = (krylov / args.steps, attempts / args.steps, substeps / args.steps)
             out["cpu_baseline"] = oracle_sample(wl, args.seed, counts, P)

@@ -3,7 +3,7 @@
 // copies (the Hopper/Blackwell copy engine: cp.async.bulk completing on an
 // mbarrier).
 //
-// Per block, one thread issues the one-dimensional copies of everything the
+// Per element tile, one thread issues the one-dimensional copies of everything the
 // tile's nodes read -- the Krylov vector v (FP64), the FP32 linearisation
 // coefficients, the FP32 interface fluxes of the tile's elements (written by
 // the face kernel), the FP32 b-column copies of the augmented operator and the
@@ -16,12 +16,15 @@
 // The copies need 16-byte aligned addresses and sizes: a tile holds EPB
 // elements with EPB (p+1)^2 a multiple of four, and the launcher falls back to
 // the register-and-cache kernel (dfr_split.cu) when the grid or a pointer does
-// not satisfy this.  The wait on the mbarrier is bounded: after ~2 s the block
-// sets the context's flag (reported as SW_ETIMEOUT by the phi-function solver),
-// waits once more with the same bound for its own copies, takes part in the
-// epilogue's reduction with zero contributions and returns.
+// not satisfy this.  Two persistent CTAs per SM loop over the tiles with two
+// stages, so the copies of a CTA's next tile are in flight while it computes the
+// current one.  The waits on the mbarriers are bounded: after ~2 s the CTA sets
+// the context's flag (reported as SW_ETIMEOUT by the phi-function solver),
+// waits once more with the same bound for its own copies, leaves its tile loop,
+// takes part in the epilogue's reduction with zero contributions and returns.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "dfr_tangent.cuh"
@@ -48,18 +51,22 @@ struct TileShape {
 
 constexpr size_t up16(size_t b) { return (b + 15) / 16 * 16; }
 
-// byte offsets of the regions of the dynamic shared memory of one tile
+// byte offsets of the regions of the dynamic shared memory: two stages of the
+// staged operands of one tile, then the scratch of the tile being computed
 template <int NS>
 struct TileLayout {
   static constexpr int TN = TileShape<NS>::TN, EPB = TileShape<NS>::EPB, NN = NS * NS;
+  // one stage
   static constexpr size_t v = 0;                                            // double [3][TN]
   static constexpr size_t dots = v + up16(sizeof(double) * 3 * TN);         // double [3 (C, A, B)][3][TN]
   static constexpr size_t ln = dots + up16(sizeof(double) * 9 * TN);        // float [LN_COUNT][TN]
   static constexpr size_t b32 = ln + up16(sizeof(float) * LN_COUNT * TN);   // float [KMAXB][3][TN]
   static constexpr size_t fb = b32 + up16(sizeof(float) * KMAXB * 3 * TN);  // float [EPB][4][3][NS]
-  static constexpr size_t flux = fb + up16(sizeof(float) * EPB * 12 * NS);  // float [EPB][2][3][NN]
+  static constexpr size_t stage = fb + up16(sizeof(float) * EPB * 12 * NS);
+  // scratch and barriers after the two stages
+  static constexpr size_t flux = 2 * stage;                                 // float [EPB][2][3][NN]
   static constexpr size_t dmat = flux + up16(sizeof(float) * EPB * 6 * NN); // float [NS][NS + 3]
-  static constexpr size_t mbar = dmat + up16(sizeof(float) * NS * (NS + 3));
+  static constexpr size_t mbar = dmat + up16(sizeof(float) * NS * (NS + 3)); // two mbarriers
   static constexpr size_t bytes = mbar + 16;
 };
 
@@ -79,16 +86,17 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
                : "memory");
 }
 
-// wait for phase 0 of the tile's mbarrier; false after ~2 s (or 2^26 polls)
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar) {
+// wait for the phase of the mbarrier with the given parity to complete; false
+// after ~2 s (or 2^26 polls)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, unsigned parity) {
   const unsigned m = smem_addr(mbar);
   const unsigned long long t0 = now_ns();
   for (unsigned it = 0; it < (1u << 26); ++it) {
     unsigned done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(m)
+        : "r"(m), "r"(parity)
         : "memory");
     if (done) return true;
     if ((it & 255u) == 255u && now_ns() - t0 > 2000000000ull) return false;
@@ -96,17 +104,55 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar) {
   return false;
 }
 
+// issue the bulk copies of tile `tile` into stage buffer `st` (one thread)
 template <int NS, bool W3>
-__global__ void __launch_bounds__(TileShape<NS>::TN, 3) volume_tangent_tile_f32_kernel(TanVolArgs<float> a,
-                                                                                      DfrConst dc, int* err) {
+__device__ __forceinline__ void issue_tile(const TanVolArgs<float>& a, long long tile, unsigned char* st,
+                                           uint64_t* mbar) {
   using L = TileLayout<NS>;
   constexpr int NN = NS * NS, EPB = TileShape<NS>::EPB, TN = TileShape<NS>::TN;
+  const AugEpilogue& ep = a.ep;
+  const long long N = a.nodes, tile0 = tile * TN;
+  const int tn = (N - tile0) < TN ? (int)(N - tile0) : TN;
+  const int ne = tn / NN;
+  const unsigned bd = (unsigned)(sizeof(double) * tn), bf = (unsigned)(sizeof(float) * tn);
+  const double* dsrc[3] = {W3 ? ep.dotC : nullptr, ep.dotA, ep.dotB};
+  unsigned tx = 3 * bd + LN_COUNT * bf + (unsigned)(sizeof(float) * ne * 12 * NS);
+  for (int k = 0; k < 3; ++k)
+    if (dsrc[k]) tx += 3 * bd;
+  for (int l = 0; l < ep.p && l < KMAXB; ++l)
+    if (ep.b32[l]) tx += 3 * bf;
+  // the stage was last read through the generic proxy: order that before the copies
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(tx) : "memory");
+  double* sv = reinterpret_cast<double*>(st + L::v);
+  double* sdot = reinterpret_cast<double*>(st + L::dots);
+  float* sln = reinterpret_cast<float*>(st + L::ln);
+  float* sb32 = reinterpret_cast<float*>(st + L::b32);
+  float* sfb = reinterpret_cast<float*>(st + L::fb);
+  for (int var = 0; var < 3; ++var) bulk_g2s(sv + var * TN, a.v + tile0 + var * N, bd, mbar);
+  for (int k = 0; k < 3; ++k) {
+    if (!dsrc[k]) continue;
+    for (int var = 0; var < 3; ++var) bulk_g2s(sdot + (k * 3 + var) * TN, dsrc[k] + tile0 + var * N, bd, mbar);
+  }
+  for (int c = 0; c < LN_COUNT; ++c) bulk_g2s(sln + c * TN, a.ln + tile0 + c * N, bf, mbar);
+  for (int l = 0; l < ep.p && l < KMAXB; ++l) {
+    if (!ep.b32[l]) continue;
+    for (int var = 0; var < 3; ++var) bulk_g2s(sb32 + (l * 3 + var) * TN, ep.b32[l] + tile0 + var * N, bf, mbar);
+  }
+  bulk_g2s(sfb, a.fb + tile * EPB * 12 * NS, (unsigned)(sizeof(float) * ne * 12 * NS), mbar);
+}
+
+// Persistent: CTA b takes tiles b, b + G, b + 2G, ... (G CTAs); stage s = k mod
+// 2 of its k-th tile is refilled with tile k + 2 as soon as tile k is done, so
+// the copies of the next tile are in flight while the current one computes.
+// Each thread accumulates its window dots over all its tiles; one block
+// reduction per CTA then feeds the shared epilogue.
+template <int NS, bool W3>
+__global__ void __launch_bounds__(TileShape<NS>::TN, 2) volume_tangent_tile_f32_kernel(TanVolArgs<float> a,
+                                                                                      DfrConst dc, int* err) {
+  using L = TileLayout<NS>;
+  constexpr int NN = NS * NS, TN = TileShape<NS>::TN;
   extern __shared__ __align__(16) unsigned char sm[];
-  double* sv = reinterpret_cast<double*>(sm + L::v);
-  double* sdot = reinterpret_cast<double*>(sm + L::dots);
-  float* sln = reinterpret_cast<float*>(sm + L::ln);
-  float* sb32 = reinterpret_cast<float*>(sm + L::b32);
-  float* sfb = reinterpret_cast<float*>(sm + L::fb);
   float (*sF)[2][3][NN] = reinterpret_cast<float (*)[2][3][NN]>(sm + L::flux);
   float (*sD)[NS + 3] = reinterpret_cast<float (*)[NS + 3]>(sm + L::dmat);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + L::mbar);
@@ -115,45 +161,23 @@ __global__ void __launch_bounds__(TileShape<NS>::TN, 3) volume_tangent_tile_f32_
   pdl_trigger();
   const AugEpilogue& ep = a.ep;
   if (ep.skip && *ep.skip) return;
-  const unsigned blk = blockIdx.x, nblk = gridDim.x;
   const long long N = a.nodes;
-  const long long tile0 = (long long)blk * TN;
-  const long long left = N - tile0;
-  const int tn = left < TN ? (int)left : TN;                  // nodes of this tile
-  const int ne = tn / NN;                                      // elements of this tile
+  const long long ntiles = (N + TN - 1) / TN;
+  const long long G = gridDim.x;
   const bool dA = ep.dotA != nullptr, dB = ep.dotB != nullptr, dC = W3 && ep.dotC != nullptr;
 
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar + 1)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned bd = (unsigned)(sizeof(double) * tn), bf = (unsigned)(sizeof(float) * tn);
-    unsigned tx = 3 * bd + LN_COUNT * bf + (unsigned)(sizeof(float) * ne * 12 * NS);
-    const double* dsrc[3] = {W3 ? ep.dotC : nullptr, ep.dotA, ep.dotB};
-    for (int k = 0; k < 3; ++k)
-      if (dsrc[k] && (k > 0 || dC)) tx += 3 * bd;
-    for (int l = 0; l < ep.p && l < KMAXB; ++l)
-      if (ep.b32[l]) tx += 3 * bf;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(tx)
-                 : "memory");
-    for (int var = 0; var < 3; ++var) bulk_g2s(sv + var * TN, a.v + tile0 + var * N, bd, mbar);
-    for (int k = 0; k < 3; ++k) {
-      if (!dsrc[k] || (k == 0 && !dC)) continue;
-      for (int var = 0; var < 3; ++var)
-        bulk_g2s(sdot + (k * 3 + var) * TN, dsrc[k] + tile0 + var * N, bd, mbar);
+    for (int s = 0; s < 2; ++s) {
+      const long long tile = blockIdx.x + s * G;
+      if (tile < ntiles) issue_tile<NS, W3>(a, tile, sm + s * L::stage, mbar + s);
     }
-    for (int c = 0; c < LN_COUNT; ++c) bulk_g2s(sln + c * TN, a.ln + tile0 + c * N, bf, mbar);
-    for (int l = 0; l < ep.p && l < KMAXB; ++l) {
-      if (!ep.b32[l]) continue;
-      for (int var = 0; var < 3; ++var)
-        bulk_g2s(sb32 + (l * 3 + var) * TN, ep.b32[l] + tile0 + var * N, bf, mbar);
-    }
-    bulk_g2s(sfb, a.fb + (long long)blk * EPB * 12 * NS, (unsigned)(sizeof(float) * ne * 12 * NS), mbar);
   }
-  // while the copies are in flight: the pre-scaled derivative matrix and the
-  // tail coefficients of the b-column terms
   const double dscale = -dc.two_over_dx * ep.scale;
   for (int t = threadIdx.x; t < NS * (NS + 2); t += TN)
     sD[t / (NS + 2)][t % (NS + 2)] = f64_to_f32_bits(dscale * dc.D[t / (NS + 2)][t % (NS + 2)]);
@@ -162,68 +186,87 @@ __global__ void __launch_bounds__(TileShape<NS>::TN, 3) volume_tangent_tile_f32_
     const int l = threadIdx.x;
     coef32[l] = (l < ep.p && ep.b32[l]) ? f64_to_f32_bits(ep.tail_in[l]) : 0.f;
   }
-  bool ok = mbar_wait_bounded(mbar);
-  if (!ok) {
-    atomicExch(err, 1);
-    mbar_wait_bounded(mbar);   // do not leave with this block's copies still landing
-  }
-  ok = __syncthreads_and(ok);
+  const float sc = f64_to_f32_bits(ep.scale);
   const int t = threadIdx.x;
-  const bool active = ok && t < tn;
   const int le = t / NN, node = t % NN, k2 = node / NS, k1 = node % NS;
-  float S1 = 0.f, S2 = 0.f;
-  if (active) {
-    const float v0 = f64_to_f32_bits(sv[t]), v1 = f64_to_f32_bits(sv[TN + t]), v2 = f64_to_f32_bits(sv[2 * TN + t]);
-    const float u1 = sln[LN_U1 * TN + t], u2 = sln[LN_U2 * TN + t];
-    const float F11 = fmaf(2.f * u1, v1, sln[LN_A11 * TN + t] * v0);
-    const float F12 = fmaf(u2, v1, fmaf(u1, v2, sln[LN_A12 * TN + t] * v0));
-    const float F22 = fmaf(2.f * u2, v2, sln[LN_A22 * TN + t] * v0);
-    S1 = fmaf(sln[LN_S11 * TN + t], v1, fmaf(sln[LN_S12 * TN + t], v2, sln[LN_S10 * TN + t] * v0));
-    S2 = fmaf(sln[LN_S21 * TN + t], v1, fmaf(sln[LN_S22 * TN + t], v2, sln[LN_S20 * TN + t] * v0));
-    sF[le][0][0][node] = v1;
-    sF[le][0][1][node] = F11;
-    sF[le][0][2][node] = F12;
-    sF[le][1][0][node] = v2;
-    sF[le][1][1][node] = F12;
-    sF[le][1][2][node] = F22;
-  }
-  __syncthreads();
   double da = 0.0, db = 0.0, dcc = 0.0;
-  if (active) {
-    float Da[NS + 2], Db[NS + 2];
-#pragma unroll
-    for (int n = 0; n < NS + 2; ++n) {
-      Da[n] = sD[k1][n];
-      Db[n] = sD[k2][n];
+  bool ok = true;
+  int k = 0;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += G, ++k) {
+    const int s = k & 1;
+    unsigned char* st = sm + s * L::stage;
+    const double* sv = reinterpret_cast<const double*>(st + L::v);
+    const double* sdot = reinterpret_cast<const double*>(st + L::dots);
+    const float* sln = reinterpret_cast<const float*>(st + L::ln);
+    const float* sb32 = reinterpret_cast<const float*>(st + L::b32);
+    const float* sfb = reinterpret_cast<const float*>(st + L::fb);
+    const long long tile0 = tile * TN;
+    const int tn = (N - tile0) < TN ? (int)(N - tile0) : TN;
+    bool got = ok && mbar_wait_bounded(mbar + s, (unsigned)((k >> 1) & 1));
+    if (ok && !got) {
+      atomicExch(err, 1);
+      mbar_wait_bounded(mbar + s, (unsigned)((k >> 1) & 1));   // do not leave with copies still landing
     }
-    const float sc = f64_to_f32_bits(ep.scale);
-    const float src[3] = {0.f, S1, S2};
-    const float* fbe = sfb + le * 12 * NS;   // [edge][mu][k] of this element
-    const long long idx = tile0 + t;
+    ok = __syncthreads_and(got) != 0;   // also orders the coefficient tables written above
+    if (!ok) break;
+    const bool active = t < tn;
+    float S1 = 0.f, S2 = 0.f;
+    if (active) {
+      const float v0 = f64_to_f32_bits(sv[t]), v1 = f64_to_f32_bits(sv[TN + t]);
+      const float v2 = f64_to_f32_bits(sv[2 * TN + t]);
+      const float u1 = sln[LN_U1 * TN + t], u2 = sln[LN_U2 * TN + t];
+      const float F11 = fmaf(2.f * u1, v1, sln[LN_A11 * TN + t] * v0);
+      const float F12 = fmaf(u2, v1, fmaf(u1, v2, sln[LN_A12 * TN + t] * v0));
+      const float F22 = fmaf(2.f * u2, v2, sln[LN_A22 * TN + t] * v0);
+      S1 = fmaf(sln[LN_S11 * TN + t], v1, fmaf(sln[LN_S12 * TN + t], v2, sln[LN_S10 * TN + t] * v0));
+      S2 = fmaf(sln[LN_S21 * TN + t], v1, fmaf(sln[LN_S22 * TN + t], v2, sln[LN_S20 * TN + t] * v0));
+      sF[le][0][0][node] = v1;
+      sF[le][0][1][node] = F11;
+      sF[le][0][2][node] = F12;
+      sF[le][1][0][node] = v2;
+      sF[le][1][1][node] = F12;
+      sF[le][1][2][node] = F22;
+    }
+    __syncthreads();
+    if (active) {
+      float Da[NS + 2], Db[NS + 2];
 #pragma unroll
-    for (int mu = 0; mu < 3; ++mu) {
-      float acc = (mu == 0) ? 0.f : sc * src[mu];
-      acc = fmaf(Da[0], fbe[(0 * 3 + mu) * NS + k2], acc);
-      acc = fmaf(Da[NS + 1], fbe[(1 * 3 + mu) * NS + k2], acc);
+      for (int n = 0; n < NS + 2; ++n) {
+        Da[n] = sD[k1][n];
+        Db[n] = sD[k2][n];
+      }
+      const float src[3] = {0.f, S1, S2};
+      const float* fbe = sfb + le * 12 * NS;   // [edge][mu][k] of this element
+      const long long idx = tile0 + t;
 #pragma unroll
-      for (int l = 0; l < NS; ++l) acc = fmaf(Da[l + 1], sF[le][0][mu][k2 * NS + l], acc);
-      acc = fmaf(Db[0], fbe[(2 * 3 + mu) * NS + k1], acc);
-      acc = fmaf(Db[NS + 1], fbe[(3 * 3 + mu) * NS + k1], acc);
+      for (int mu = 0; mu < 3; ++mu) {
+        float acc = (mu == 0) ? 0.f : sc * src[mu];
+        acc = fmaf(Da[0], fbe[(0 * 3 + mu) * NS + k2], acc);
+        acc = fmaf(Da[NS + 1], fbe[(1 * 3 + mu) * NS + k2], acc);
 #pragma unroll
-      for (int l = 0; l < NS; ++l) acc = fmaf(Db[l + 1], sF[le][1][mu][l * NS + k1], acc);
+        for (int l = 0; l < NS; ++l) acc = fmaf(Da[l + 1], sF[le][0][mu][k2 * NS + l], acc);
+        acc = fmaf(Db[0], fbe[(2 * 3 + mu) * NS + k1], acc);
+        acc = fmaf(Db[NS + 1], fbe[(3 * 3 + mu) * NS + k1], acc);
 #pragma unroll
-      for (int l = 0; l < KMAXB; ++l)
-        if (l < ep.p && ep.b32[l]) acc = fmaf(coef32[l], sb32[(l * 3 + mu) * TN + t], acc);
-      const double o = f32_to_f64_bits(acc);
-      a.out[idx + mu * N] = o;
-      if (dB) {
-        db = fma(o, sdot[(2 * 3 + mu) * TN + t], db);
-        if (dA) da = fma(o, sdot[(1 * 3 + mu) * TN + t], da);
-        if (dC) dcc = fma(o, sdot[(0 * 3 + mu) * TN + t], dcc);
+        for (int l = 0; l < NS; ++l) acc = fmaf(Db[l + 1], sF[le][1][mu][l * NS + k1], acc);
+#pragma unroll
+        for (int l = 0; l < KMAXB; ++l)
+          if (l < ep.p && ep.b32[l]) acc = fmaf(coef32[l], sb32[(l * 3 + mu) * TN + t], acc);
+        const double o = f32_to_f64_bits(acc);
+        a.out[idx + mu * N] = o;
+        if (dB) {
+          db = fma(o, sdot[(2 * 3 + mu) * TN + t], db);
+          if (dA) da = fma(o, sdot[(1 * 3 + mu) * TN + t], da);
+          if (dC) dcc = fma(o, sdot[(0 * 3 + mu) * TN + t], dcc);
+        }
       }
     }
+    __syncthreads();   // stage s and the flux scratch are free again
+    if (threadIdx.x == 0 && tile + 2 * G < ntiles) issue_tile<NS, W3>(a, tile + 2 * G, st, mbar + s);
   }
-  epilogue_finish<TN, W3>(ep, da, db, dcc, blk, nblk);
+  // a CTA that gave up contributes zeros; the reduction protocol still completes
+  if (!ok) da = db = dcc = 0.0;
+  epilogue_finish<TN, W3>(ep, da, db, dcc, blockIdx.x, gridDim.x);
 }
 
 template <int NS>
@@ -251,8 +294,11 @@ int launch_tile(Ctx& c, const double* v, double* out, const AugEpilogue& ep, cud
   }
   TanVolArgs<float> va{v, c.nodes, c.nelem, c.d_lin_node32, reinterpret_cast<const float*>(c.d_fb), out, ep};
   const long long tiles = (c.nodes + TileShape<NS>::TN - 1) / TileShape<NS>::TN;
+  static int sms = 0;
+  if (!sms && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess) return SW_ECUDA;
+  const long long ctas = std::min<long long>(tiles, 2LL * sms);   // two persistent CTAs per SM
   cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3((unsigned)tiles);
+  cfg.gridDim = dim3((unsigned)ctas);
   cfg.blockDim = dim3(TileShape<NS>::TN);
   cfg.dynamicSmemBytes = L::bytes;
   cfg.stream = s;
