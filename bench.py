@@ -338,18 +338,34 @@ def ortho_roofline(prof_all, wl):
             "peak_source": src}
 
 
+def volume_bytes_per_node(ns, mode, iop, p):
+    """Bytes one volume-kernel launch of a Krylov iteration must move per node:
+    read v and write Jv (3 + 3 doubles), read the iop orthogonalisation window
+    vectors (3 iop doubles), the p b-column vectors of the augmented operator (3 p
+    entries: FP64, or their FP32 copies in the complex64-bulk form), the 11
+    split-JVP coefficients (FP64, or FP32 in the complex64-bulk form) and the
+    interface fluxes of the element's four edges (12 N_s values per element =
+    12 / N_s per node, FP64 or FP32)."""
+    w = 8 if mode == 1 else 4
+    return 24 + 24 + 24 * iop + 3 * p * w + 11 * w + 12.0 / ns * w
+
+
+def orth_bytes_per_unknown(iop):
+    """The two vector passes of the fused window-iop orthogonalisation per unknown
+    of the augmented vector: (read z and the iop window vectors, write z) + (read
+    z and iop - 1 window vectors for the dots, write V_{j+1}) = 8 (2 iop + 3) B."""
+    return 8.0 * (2 * iop + 3)
+
+
 def kernel_rooflines(prof, wl, mode, iop, step_ms, fp64_peak):
     """Per-kernel figures of one EPI step with every kernel family bracketed by
     events.  FP64 kernels: algorithmic flops (flops_per_jvp, 6 more per node for
     the third dot of window 3) against the measured FP64 peak.  HBM: the
-    algorithmic vector bytes against the measured copy bandwidth; the volume
-    kernel reads v, the 4 augmented-operator vectors and the iop dot operands and
-    writes Jv (24 (6 + iop) B per node), plus its 11 split-JVP coefficients per
-    node (8 B each in FP64, 4 B in the complex64-bulk form); the two vector passes
-    move (read z and the iop basis vectors, write z) + (read z and iop - 1 basis
-    vectors, write V_{j+1}) = 8 (4 iop + 3) B per unknown of the augmented vector."""
+    algorithmic bytes (volume_bytes_per_node, orth_bytes_per_unknown) against
+    the measured copy bandwidth."""
     hbm, _ = hbm_peak_gbs()
     nodes = 6 * wl.ne * wl.ne * wl.ns * wl.ns
+    p = {2: 1, 3: 2, 4: 3, 5: 4, 6: 4}[wl.order]
     fv, ff = flops_per_jvp(wl.ne, wl.ns)
     fv += 6 * nodes * (iop - 2)
     out = {}
@@ -359,7 +375,7 @@ def kernel_rooflines(prof, wl, mode, iop, step_ms, fp64_peak):
         return k["ms"] / k["count"] * 1e-3 if k["count"] else None
     tv, tf, to = avg("volume_jvp"), avg("face_jvp"), avg("orthogonalisation")
     if tv:
-        vbytes = nodes * (24 * (6 + iop) + 11 * (8 if mode == 1 else 4))
+        vbytes = nodes * volume_bytes_per_node(wl.ns, mode, iop, p)
         v = {"avg_us": tv * 1e6, "launches": prof["volume_jvp"]["count"], "flops": fv,
              "bytes": vbytes, "gbs": vbytes / tv / 1e9, "hbm_frac": vbytes / tv / 1e9 / hbm}
         if mode == 1:
@@ -376,7 +392,7 @@ def kernel_rooflines(prof, wl, mode, iop, step_ms, fp64_peak):
         out["face"] = f
     if to:
         t = 2.0 * to   # one update-and-norm plus one scale-and-dot pass per Krylov iteration
-        obytes = 8.0 * (4 * iop + 3) * (wl.n_unknowns + 4)
+        obytes = orth_bytes_per_unknown(iop) * (wl.n_unknowns + 4)
         out["orthogonalisation"] = {"avg_us_per_iteration": t * 1e6, "bytes_per_iteration": obytes,
                                     "gbs": obytes / t / 1e9, "hbm_frac": obytes / t / 1e9 / hbm}
     if prof["expm"]["count"]:

@@ -57,9 +57,10 @@ def test_flop_counts():
 
 def test_kernel_rooflines_arithmetic():
     """Per-kernel figures of a profiled EPI step: algorithmic flops and bytes per
-    launch (the volume kernel's vectors 24 (6 + window) B/node plus its 11
-    coefficients, the vector passes 8 (4 window + 3) B per unknown), divided by
-    the average event time, against the given peaks."""
+    launch (the volume kernel: v and Jv, the window vectors, 4 b-columns, 11
+    coefficients and the face fluxes per node, FP32 copies of the tables in the
+    complex64-bulk form; the vector passes 8 (2 window + 3) B per unknown),
+    divided by the average event time, against the given peaks."""
     sys.path.insert(0, ROOT)
     import bench
     from paper_2101_05617_gb300 import synth
@@ -71,10 +72,10 @@ def test_kernel_rooflines_arithmetic():
     prof["orthogonalisation"] = {"ms": 1.0, "count": 20}  # two passes per iteration: 0.1 ms per iteration
     for mode, iop, coef in ((1, 2, 8), (1, 3, 8), (2, 3, 4)):
         r = bench.kernel_rooflines(prof, wl, mode, iop, 10.0, 1.25)
-        vb = nodes * (24 * (6 + iop) + 11 * coef)
+        vb = nodes * (48 + 24 * iop + 12 * coef + 11 * coef + 2 * coef)     # EPI5: 4 b-columns; N_s = 6
         assert r["volume"]["bytes"] == vb
         assert abs(r["volume"]["gbs"] - vb / 2e-4 / 1e9) < 1e-9 * r["volume"]["gbs"]
-        ob = 8.0 * (4 * iop + 3) * (wl.n_unknowns + 4)
+        ob = 8.0 * (2 * iop + 3) * (wl.n_unknowns + 4)
         assert r["orthogonalisation"]["bytes_per_iteration"] == ob
         assert abs(r["orthogonalisation"]["gbs"] - ob / 1e-4 / 1e9) < 1e-9 * ob
         fv = bench.flops_per_jvp(60, 6)[0] + 6 * nodes * (iop - 2)
