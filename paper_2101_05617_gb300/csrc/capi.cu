@@ -274,6 +274,7 @@ void sw_free(sw_ctx_t c) {
   if (c->d_lin_node32) cudaFree(c->d_lin_node32);
   if (c->d_lin_face32) cudaFree(c->d_lin_face32);
   if (c->d_b32) cudaFree(c->d_b32);
+  if (c->d_V32) cudaFree(c->d_V32);
   for (double* p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i < MAX_HIST; ++i) {

@@ -152,7 +152,8 @@ int tangent_ns(Ctx& c, const double* v, double* out, const AugEpilogue& ep, cons
     e0 = prof_event(c);
     cudaEventRecord(e0, s);
   }
-  TanFaceArgs<T> fa{v, c.nodes, c.d_lines, c.d_face_coef, lf, c.nfacepts, fb, ep.skip};
+  TanFaceArgs<T> fa{v, sizeof(T) == 4 ? ep.v32 : nullptr, c.nodes, c.d_lines, c.d_face_coef, lf, c.nfacepts, fb,
+                    ep.skip};
   if (launch_pdl(face_tangent_kernel<T, NS>, dim3((unsigned)((c.nfacepts + 127) / 128)), dim3(128), s, fa, c.dc) !=
       cudaSuccess)
     return SW_ECUDA;

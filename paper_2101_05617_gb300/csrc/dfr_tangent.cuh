@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include "convert.cuh"
 #include "dfr_device.cuh"
 #include "swepi_internal.h"
 
@@ -16,55 +17,9 @@ namespace swepi {
 // accumulation).  Krylov vectors in and out stay FP64; the orthogonalisation
 // dots of the epilogue are FP64 in both.
 //
-// Conversions between the FP64 Krylov vectors and the FP32 arithmetic of the
-// complex64-bulk form are done on the IEEE-754 bit fields with integer
-// operations, so that none of them occupies the FP64 pipe (on this GPU a
-// fraction of the FP32 rate).  binary64 -> binary32 rounds the significand to
-// nearest, ties to even (an unbiased rounding matters: a systematic one, as
-// truncation, scales every Krylov matvec the same way, and the stiff
-// exponential amplifies that), carries into the exponent as the packed
-// integer increments, maps magnitudes below the binary32 normal range to
-// signed zero and above it to infinity, and NaN to NaN; binary32 -> binary64
-// is exact for normal numbers, zero, infinities and NaN (binary32 subnormals
-// become zero).
-__device__ __forceinline__ float f64_to_f32_bits(double x) {
-  const unsigned int hi = (unsigned int)__double2hiint(x), lo = (unsigned int)__double2loint(x);
-  const unsigned int sign = hi & 0x80000000u;
-  const int e = (int)((hi >> 20) & 0x7ffu) - 896;                  // binary32 biased exponent
-  const unsigned int mant = ((hi & 0xfffffu) << 3) | (lo >> 29);   // top 23 significand bits
-  unsigned int r = ((unsigned int)e << 23) | mant;
-  const unsigned int round = (lo >> 28) & 1u, sticky = (lo & 0x0fffffffu) != 0u;
-  r += round & (sticky | (r & 1u));                                // nearest, ties to even
-  r |= sign;
-  r = (e <= 0) ? sign : r;
-  r = (e >= 255 || (r & 0x7f800000u) == 0x7f800000u) ? (sign | 0x7f800000u) : r;
-  const bool nan = ((hi & 0x7ff00000u) == 0x7ff00000u) && (((hi & 0xfffffu) | lo) != 0u);
-  return __uint_as_float(nan ? 0x7fc00000u : r);
-}
-__device__ __forceinline__ double f32_to_f64_bits(float f) {
-  const unsigned int u = __float_as_uint(f);
-  const unsigned int sign = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
-  unsigned int hi = sign | ((e + 896u) << 20) | (m >> 3);
-  unsigned int lo = m << 29;
-  hi = (e == 0u) ? sign : hi;
-  lo = (e == 0u) ? 0u : lo;
-  hi = (e == 255u) ? (sign | 0x7ff00000u | (m >> 3) | (m ? 0x80000u : 0u)) : hi;
-  return __hiloint2double((int)hi, (int)lo);
-}
-template <typename T>
-__device__ __forceinline__ T from_f64(double x) {
-  if constexpr (sizeof(T) == 4) return f64_to_f32_bits(x);
-  else return x;
-}
-template <typename T>
-__device__ __forceinline__ double to_f64(T x) {
-  if constexpr (sizeof(T) == 4) return f32_to_f64_bits(x);
-  else return x;
-}
-
 template <typename T, int NS>
-__device__ __forceinline__ void trace_tan(const double* __restrict__ v, long long nodes, int elem, int edge, int i,
-                                          const DfrConst& dc, T out[3]) {
+__device__ __forceinline__ void trace_tan(const double* __restrict__ v, const float* __restrict__ v32, long long nodes,
+                                          int elem, int edge, int i, const DfrConst& dc, T out[3]) {
   const long long base = (long long)elem * NS * NS;
   const double* w = (edge == 0 || edge == 2) ? dc.lm : dc.lp;
 #pragma unroll
@@ -73,7 +28,10 @@ __device__ __forceinline__ void trace_tan(const double* __restrict__ v, long lon
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
       const long long idx = base + ((edge <= 1) ? (i * NS + k) : (k * NS + i)) + var * nodes;
-      acc = fma(from_f64<T>(w[k]), from_f64<T>(__ldg(v + idx)), acc);
+      T x;
+      if constexpr (sizeof(T) == 4) x = v32 ? __ldg(v32 + idx) : from_f64<T>(__ldg(v + idx));
+      else x = __ldg(v + idx);
+      acc = fma(from_f64<T>(w[k]), x, acc);
     }
     out[var] = acc;
   }
@@ -82,6 +40,7 @@ __device__ __forceinline__ void trace_tan(const double* __restrict__ v, long lon
 template <typename T>
 struct TanFaceArgs {
   const double* v;
+  const float* v32;   // FP32 copy of v (complex64-bulk form), or null
   long long nodes;
   const FaceLine* lines;
   const double* fc;
@@ -99,8 +58,8 @@ __device__ __forceinline__ void face_tangent_body(const TanFaceArgs<T>& a, const
   const FaceLine L = a.lines[line];
   const int in = L.reversed ? NS - 1 - i : i;
   T vo[3], vn[3];
-  trace_tan<T, NS>(a.v, a.nodes, L.owner, L.owner_edge, i, dc, vo);
-  trace_tan<T, NS>(a.v, a.nodes, L.nbr, L.nbr_edge, in, dc, vn);
+  trace_tan<T, NS>(a.v, a.v32, a.nodes, L.owner, L.owner_edge, i, dc, vo);
+  trace_tan<T, NS>(a.v, a.v32, a.nodes, L.nbr, L.nbr_edge, in, dc, vn);
   const long long P = a.nfacepts;
   const T* lf = a.lf + t;
   T f[3];

@@ -4,7 +4,8 @@
 // mbarrier).
 //
 // Per element tile, one thread issues the one-dimensional copies of everything the
-// tile's nodes read -- the Krylov vector v (FP64), the FP32 linearisation
+// tile's nodes read -- the Krylov vector v (its FP32 copy when the solver keeps
+// one, else FP64), the FP32 linearisation
 // coefficients, the FP32 interface fluxes of the tile's elements (written by
 // the face kernel), the FP32 b-column copies of the augmented operator and the
 // FP64 orthogonalisation window vectors -- so that all of a tile's HBM traffic
@@ -116,7 +117,7 @@ __device__ __forceinline__ void issue_tile(const TanVolArgs<float>& a, long long
   const int ne = tn / NN;
   const unsigned bd = (unsigned)(sizeof(double) * tn), bf = (unsigned)(sizeof(float) * tn);
   const double* dsrc[3] = {W3 ? ep.dotC : nullptr, ep.dotA, ep.dotB};
-  unsigned tx = 3 * bd + LN_COUNT * bf + (unsigned)(sizeof(float) * ne * 12 * NS);
+  unsigned tx = 3 * (ep.v32 ? bf : bd) + LN_COUNT * bf + (unsigned)(sizeof(float) * ne * 12 * NS);
   for (int k = 0; k < 3; ++k)
     if (dsrc[k]) tx += 3 * bd;
   for (int l = 0; l < ep.p && l < KMAXB; ++l)
@@ -129,7 +130,12 @@ __device__ __forceinline__ void issue_tile(const TanVolArgs<float>& a, long long
   float* sln = reinterpret_cast<float*>(st + L::ln);
   float* sb32 = reinterpret_cast<float*>(st + L::b32);
   float* sfb = reinterpret_cast<float*>(st + L::fb);
-  for (int var = 0; var < 3; ++var) bulk_g2s(sv + var * TN, a.v + tile0 + var * N, bd, mbar);
+  if (ep.v32) {   // v from its FP32 copy: [3][TN] floats in the same region
+    float* svf = reinterpret_cast<float*>(st + L::v);
+    for (int var = 0; var < 3; ++var) bulk_g2s(svf + var * TN, ep.v32 + tile0 + var * N, bf, mbar);
+  } else {
+    for (int var = 0; var < 3; ++var) bulk_g2s(sv + var * TN, a.v + tile0 + var * N, bd, mbar);
+  }
   for (int k = 0; k < 3; ++k) {
     if (!dsrc[k]) continue;
     for (int var = 0; var < 3; ++var) bulk_g2s(sdot + (k * 3 + var) * TN, dsrc[k] + tile0 + var * N, bd, mbar);
@@ -165,6 +171,7 @@ __global__ void __launch_bounds__(TileShape<NS>::TN, 2) volume_tangent_tile_f32_
   const long long ntiles = (N + TN - 1) / TN;
   const long long G = gridDim.x;
   const bool dA = ep.dotA != nullptr, dB = ep.dotB != nullptr, dC = W3 && ep.dotC != nullptr;
+  const bool f32v = ep.v32 != nullptr;
 
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)) : "memory");
@@ -196,6 +203,7 @@ __global__ void __launch_bounds__(TileShape<NS>::TN, 2) volume_tangent_tile_f32_
     const int s = k & 1;
     unsigned char* st = sm + s * L::stage;
     const double* sv = reinterpret_cast<const double*>(st + L::v);
+    const float* svf = reinterpret_cast<const float*>(st + L::v);
     const double* sdot = reinterpret_cast<const double*>(st + L::dots);
     const float* sln = reinterpret_cast<const float*>(st + L::ln);
     const float* sb32 = reinterpret_cast<const float*>(st + L::b32);
@@ -212,8 +220,16 @@ __global__ void __launch_bounds__(TileShape<NS>::TN, 2) volume_tangent_tile_f32_
     const bool active = t < tn;
     float S1 = 0.f, S2 = 0.f;
     if (active) {
-      const float v0 = f64_to_f32_bits(sv[t]), v1 = f64_to_f32_bits(sv[TN + t]);
-      const float v2 = f64_to_f32_bits(sv[2 * TN + t]);
+      float v0, v1, v2;
+      if (f32v) {
+        v0 = svf[t];
+        v1 = svf[TN + t];
+        v2 = svf[2 * TN + t];
+      } else {
+        v0 = f64_to_f32_bits(sv[t]);
+        v1 = f64_to_f32_bits(sv[TN + t]);
+        v2 = f64_to_f32_bits(sv[2 * TN + t]);
+      }
       const float u1 = sln[LN_U1 * TN + t], u2 = sln[LN_U2 * TN + t];
       const float F11 = fmaf(2.f * u1, v1, sln[LN_A11 * TN + t] * v0);
       const float F12 = fmaf(u2, v1, fmaf(u1, v2, sln[LN_A12 * TN + t] * v0));
@@ -273,6 +289,7 @@ template <int NS>
 bool tile_eligible(const Ctx& c, const double* v, const double* out, const AugEpilogue& ep) {
   auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
   if (c.nodes % 4 != 0 || ep.p > KMAXB || !al(v) || !al(c.d_lin_node32) || !al(c.d_fb)) return false;
+  if (ep.v32 && !al(ep.v32)) return false;
   if ((ep.dotA && !al(ep.dotA)) || (ep.dotB && !al(ep.dotB)) || (ep.dotC && !al(ep.dotC))) return false;
   for (int l = 0; l < ep.p && l < MAX_NB; ++l) {
     if (ep.b[l] && !ep.b32[l]) return false;

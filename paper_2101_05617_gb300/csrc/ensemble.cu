@@ -201,7 +201,7 @@ __device__ __forceinline__ AugEpilogue iter_epilogue(const EnsDesc& d, int j) {
 
 template <int NS, int BLOCK>
 __device__ __forceinline__ void face_range(const EnsDesc& d, int j, long long t0, long long t1) {
-  TanFaceArgs<double> fa{d.V + (long long)j * d.ldv, d.nodes, d.lines, d.fc, d.lf, d.nfacepts, d.fb, nullptr};
+  TanFaceArgs<double> fa{d.V + (long long)j * d.ldv, nullptr, d.nodes, d.lines, d.fc, d.lf, d.nfacepts, d.fb, nullptr};
   for (long long t = t0 + threadIdx.x; t < t1; t += BLOCK) face_tangent_body<double, NS>(fa, d.dc, t);
 }
 

@@ -182,6 +182,16 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
   K.start(tau_end, o.tol, beta0, o, tau, m);
   double* V = c.d_V;
   const long long ldv = c.ldv;
+  // complex64-bulk form with a fused window: an FP32 copy of the basis, written
+  // by the scale pass with each new vector, feeds the FP32 kernels
+  const bool use32 = use_lin && c.jvp_mode == 2 && (o.iop == 2 || o.iop == 3);
+  if (use32 && c.v32_cap < c.vcap) {
+    if (c.d_V32) cudaFree(c.d_V32);
+    c.d_V32 = nullptr;
+    c.v32_cap = 0;
+    if (cudaMalloc(&c.d_V32, sizeof(float) * (size_t)c.vcap * ldv) != cudaSuccess) return SW_ENOMEM;
+    c.v32_cap = c.vcap;
+  }
 
   while (!K.done()) {
     TraceRange attempt("substep attempt");
@@ -189,6 +199,7 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
     if (j == 0) {
       if ((rc = launch_norm2(c, c.d_X, N, c.d_scal + S_BETA, 0.0, nullptr, 0, nullptr, s))) return rc;
       if ((rc = launch_scale_inv(c, V, c.d_X, c.d_scal + S_BETA, N, nullptr, s))) return rc;
+      if (use32 && (rc = launch_to_float(c, V, c.d_V32, N, s))) return rc;
       if (cudaMemsetAsync(c.d_flags, 0, sizeof(int) * 2, s) != cudaSuccess) return SW_ECUDA;
       if (cudaMemsetAsync(c.d_H, 0, sizeof(double) * c.ldh * c.ldh, s) != cudaSuccess) return SW_ECUDA;
     }
@@ -214,16 +225,20 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
         ep.dpart = c.d_vpart;
         ep.dticket = (unsigned int*)(c.d_flags + 9);
         ep.n = n;
+        ep.v32 = use32 ? c.d_V32 + it * ldv : nullptr;
         rc = use_lin ? launch_jvp_lin(c, Vi, Vn, ep, s, c.jvp_mode == 2) : launch_jvp(c, q_lin, Vi, kEpsJvp, Vn, ep, s);
         if (rc) return rc;
         double* hs = c.d_H + (long long)(it + 1) * c.ldh + it;
         if ((rc = launch_update_norm(c, Vn, ep.dotA, Vi, hA, hB, N, hs, o.tol, it + 1, s, ep.dotC, hC))) return rc;
         // V_{j+1} . V_{j-1} is needed by the window of three two iterations later
         const double* Vprev = (o.iop == 3 && it >= 1) ? V + (it - 1) * ldv : nullptr;
-        if ((rc = launch_scale_dot(c, Vn, Vi, hs, N, c.d_cdot + it + 1, s, Vprev, c.d_cdot2 + it + 1))) return rc;
+        if ((rc = launch_scale_dot(c, Vn, Vi, hs, N, c.d_cdot + it + 1, s, Vprev, c.d_cdot2 + it + 1,
+                                   use32 ? c.d_V32 + (it + 1) * ldv : nullptr)))
+          return rc;
         continue;
       }
       ep.dotA = ep.dotB = ep.dotC = nullptr;
+      ep.v32 = nullptr;
       rc = use_lin ? launch_jvp_lin(c, Vi, Vn, ep, s, c.jvp_mode == 2) : launch_jvp(c, q_lin, Vi, kEpsJvp, Vn, ep, s);
       if (rc) return rc;
       for (int i = std::max(0, it - o.iop + 1); i <= it; ++i) {

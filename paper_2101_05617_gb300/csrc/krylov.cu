@@ -189,14 +189,15 @@ __global__ void __launch_bounds__(RED_THREADS) update_norm_kernel(double* __rest
 __global__ void __launch_bounds__(RED_THREADS) scale_dot_kernel(double* __restrict__ z, const double* __restrict__ VB,
                                                                 const double* hsub, long long n, double* partials,
                                                                 unsigned int* ticket, double* c_out, const int* happy,
-                                                                const double* __restrict__ VA, double* c2_out) {
+                                                                const double* __restrict__ VA, double* c2_out,
+                                                                float* __restrict__ z32) {
   pdl_wait();
   pdl_trigger();
   if (happy[0]) return;
   const double r = 1.0 / *hsub;
   double acc2 = 0.0;
   const double acc = scale_dot_range(z, VB, r, (long long)blockIdx.x * blockDim.x + threadIdx.x, n,
-                                     (long long)gridDim.x * blockDim.x, VA, &acc2);
+                                     (long long)gridDim.x * blockDim.x, VA, &acc2, z32);
   const double b = block_sum(acc);
   const double b2 = VA ? block_sum(acc2) : 0.0;   // uniform condition
   __shared__ bool last;
@@ -333,7 +334,7 @@ int launch_update_norm(Ctx& c, double* z, const double* VA, const double* VB, co
 }
 
 int launch_scale_dot(Ctx& c, double* z, const double* VB, const double* hsub, long long N, double* c_out,
-                     cudaStream_t s, const double* VA, double* c2_out) {
+                     cudaStream_t s, const double* VA, double* c2_out, float* z32) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (prof_on(c, PK_ORTH)) {
     e0 = prof_event(c);
@@ -341,7 +342,7 @@ int launch_scale_dot(Ctx& c, double* z, const double* VB, const double* hsub, lo
     cudaEventRecord(e0, s);
   }
   if (launch_pdl(scale_dot_kernel, dim3(RED_BLOCKS), dim3(RED_THREADS), s, z, VB, hsub, N, c.d_partials,
-                 (unsigned int*)(c.d_flags + 8), c_out, c.d_flags, VA, c2_out) != cudaSuccess)
+                 (unsigned int*)(c.d_flags + 8), c_out, c.d_flags, VA, c2_out, z32) != cudaSuccess)
     return SW_ECUDA;
   if (prof_on(c, PK_ORTH)) {
     cudaEventRecord(e1, s);
@@ -365,6 +366,17 @@ int launch_lincomb(Ctx& c, double* out, long long n, int k, const double* const*
   Lin L{};
   for (int j = 0; j < k; ++j) { L.x[j] = xs[j]; L.c[j] = coef[j]; }
   lincomb_kernel<<<blocks_for(n, 256), 256, 0, s>>>(out, n, k, L);
+  c.launches++;
+  return cuda_status(cudaGetLastError());
+}
+
+__global__ void to_float_rn_kernel(const double* __restrict__ src, float* __restrict__ dst, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = f64_to_f32_bits(src[i]);
+}
+
+int launch_to_float(Ctx& c, const double* src, float* dst, long long n, cudaStream_t s) {
+  to_float_rn_kernel<<<blocks_for(n, 256), 256, 0, s>>>(src, dst, n);
   c.launches++;
   return cuda_status(cudaGetLastError());
 }

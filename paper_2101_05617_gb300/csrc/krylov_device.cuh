@@ -7,6 +7,8 @@
 
 #include <cmath>
 
+#include "convert.cuh"
+
 namespace swepi {
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -72,10 +74,12 @@ __device__ __forceinline__ double mgs_update_range(double* __restrict__ z, const
 }
 
 //   z *= r; returns the thread's sum of z_i VB_i, and with VA also the sum of
-//   z_i VA_i in *za
+//   z_i VA_i in *za; with z32, also the FP32 copy of the scaled z (rounded to
+//   nearest) for the complex64-bulk form's kernels
 __device__ __forceinline__ double scale_dot_range(double* __restrict__ z, const double* __restrict__ VB, double r,
                                                   long long i, long long i1, long long stride,
-                                                  const double* __restrict__ VA = nullptr, double* za = nullptr) {
+                                                  const double* __restrict__ VA = nullptr, double* za = nullptr,
+                                                  float* __restrict__ z32 = nullptr) {
   if (VA) {
     double acc = 0.0, acc2 = 0.0;
     for (; i + 3 * stride < i1; i += 4 * stride) {
@@ -90,6 +94,7 @@ __device__ __forceinline__ double scale_dot_range(double* __restrict__ z, const 
       for (int k = 0; k < 4; ++k) {
         v[k] *= r;
         z[i + k * stride] = v[k];
+        if (z32) z32[i + k * stride] = f64_to_f32_bits(v[k]);
         acc = fma(v[k], b[k], acc);
         acc2 = fma(v[k], a[k], acc2);
       }
@@ -97,6 +102,7 @@ __device__ __forceinline__ double scale_dot_range(double* __restrict__ z, const 
     for (; i < i1; i += stride) {
       const double v = __ldcg(z + i) * r;
       z[i] = v;
+      if (z32) z32[i] = f64_to_f32_bits(v);
       acc = fma(v, VB[i], acc);
       acc2 = fma(v, VA[i], acc2);
     }
@@ -115,12 +121,14 @@ __device__ __forceinline__ double scale_dot_range(double* __restrict__ z, const 
     for (int k = 0; k < 4; ++k) {
       v[k] *= r;
       z[i + k * stride] = v[k];
+      if (z32) z32[i + k * stride] = f64_to_f32_bits(v[k]);
       acc = fma(v[k], b[k], acc);
     }
   }
   for (; i < i1; i += stride) {
     const double v = __ldcg(z + i) * r;
     z[i] = v;
+    if (z32) z32[i] = f64_to_f32_bits(v);
     acc = fma(v, VB[i], acc);
   }
   return acc;

@@ -134,6 +134,8 @@ struct Ctx {
   double* d_lin_face = nullptr;     // [18][nfacepts]
   float* d_lin_node32 = nullptr;    // FP32 copies (complex64-bulk form)
   float* d_lin_face32 = nullptr;
+  float* d_V32 = nullptr;           // FP32 copy of the Krylov basis [vcap][ldv] (complex64-bulk form)
+  int v32_cap = 0;                  // rows allocated in d_V32
   float* d_b32 = nullptr;           // FP32 copies of nu * b_l of the current phi-function call [MAX_NB][n]
   int b32_cap = 0;                  // vectors allocated in d_b32
   // KIOPS call log and learned control
@@ -215,6 +217,9 @@ struct AugEpilogue {
   // kernels add the b-column terms in FP32 from these (the FP64 b[l] are then
   // not read by them)
   const float* b32[MAX_NB] = {};
+  // complex64-bulk form: FP32 copy of the product's input vector v (first n
+  // entries; rounded to nearest), read by the FP32 kernels instead of v
+  const float* v32 = nullptr;
   const double* tail_in = nullptr;  // p doubles (device)
   double* tail_out = nullptr;       // p doubles (device): (tail_in[1..p-1], 0)
   const int* skip = nullptr;        // if non-null and *skip != 0 the kernels return
@@ -281,7 +286,9 @@ int launch_update_norm(Ctx& c, double* z, const double* VA, const double* VB, co
                        long long N, double* hsub, double tol, int happy_value, cudaStream_t s,
                        const double* VC = nullptr, const double* h0 = nullptr);
 int launch_scale_dot(Ctx& c, double* z, const double* VB, const double* hsub, long long N, double* c_out,
-                     cudaStream_t s, const double* VA = nullptr, double* c2_out = nullptr);
+                     cudaStream_t s, const double* VA = nullptr, double* c2_out = nullptr, float* z32 = nullptr);
+// dst = src rounded to FP32 (n entries)
+int launch_to_float(Ctx& c, const double* src, float* dst, long long n, cudaStream_t s);
 double fp64_fma_peak_tflops();
 int launch_set_tail(Ctx& c, double* x, long long n, int p, const double* vals, cudaStream_t s);
 int launch_lincomb(Ctx& c, double* out, long long n, int k, const double* const* xs,
