@@ -223,11 +223,14 @@ int launch_linearize(Ctx& c, const double* q, cudaStream_t s) {
     // complex64-bulk form: FP32 copies of the coefficient tables
     if (!c.d_lin_node32 && cudaMalloc(&c.d_lin_node32, sizeof(float) * LN_COUNT * c.nodes) != cudaSuccess)
       return SW_ENOMEM;
-    if (!c.d_lin_face32 && cudaMalloc(&c.d_lin_face32, sizeof(float) * 18 * c.nfacepts) != cudaSuccess)
+    if (!c.d_lin_face32 && cudaMalloc(&c.d_lin_face32, sizeof(float) * 23 * c.nfacepts) != cudaSuccess)
       return SW_ENOMEM;
     to_float_kernel<<<1024, 256, 0, s>>>(c.d_lin_node, c.d_lin_node32, (long long)LN_COUNT * c.nodes);
     to_float_kernel<<<1024, 256, 0, s>>>(c.d_lin_face, c.d_lin_face32, 18LL * c.nfacepts);
-    c.launches += 2;
+    // M00, M01, M10, M11, sigma (consecutive rows of the face table) after the map rows
+    to_float_kernel<<<1024, 256, 0, s>>>(c.d_face_coef + (long long)FC_M00 * c.nfacepts,
+                                         c.d_lin_face32 + 18LL * c.nfacepts, 5LL * c.nfacepts);
+    c.launches += 3;
     rc = cuda_status(cudaGetLastError());
   }
   if (pl) {

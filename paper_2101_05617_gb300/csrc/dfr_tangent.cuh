@@ -22,16 +22,19 @@ __device__ __forceinline__ void trace_tan(const double* __restrict__ v, const fl
                                           int elem, int edge, int i, const DfrConst& dc, T out[3]) {
   const long long base = (long long)elem * NS * NS;
   const double* w = (edge == 0 || edge == 2) ? dc.lm : dc.lp;
+  const float* w32 = (edge == 0 || edge == 2) ? dc.lm32 : dc.lp32;
 #pragma unroll
   for (int var = 0; var < 3; ++var) {
     T acc = T(0);
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
       const long long idx = base + ((edge <= 1) ? (i * NS + k) : (k * NS + i)) + var * nodes;
-      T x;
-      if constexpr (sizeof(T) == 4) x = v32 ? __ldg(v32 + idx) : from_f64<T>(__ldg(v + idx));
-      else x = __ldg(v + idx);
-      acc = fma(from_f64<T>(w[k]), x, acc);
+      if constexpr (sizeof(T) == 4) {
+        const float x = v32 ? __ldg(v32 + idx) : f64_to_f32_bits(__ldg(v + idx));
+        acc = fmaf(w32[k], x, acc);
+      } else {
+        acc = fma(w[k], __ldg(v + idx), acc);
+      }
     }
     out[var] = acc;
   }
@@ -73,10 +76,21 @@ __device__ __forceinline__ void face_tangent_body(const TanFaceArgs<T>& a, const
     s = fma(lf[(9 + mu * 3 + 2) * P], vn[2], s);
     f[mu] = s;
   }
-  const double* fc = a.fc + t;
-  const T sig = from_f64<T>(fc[FC_SIG * P]);
-  const T M00 = from_f64<T>(fc[FC_M00 * P]), M01 = from_f64<T>(fc[FC_M01 * P]);
-  const T M10 = from_f64<T>(fc[FC_M10 * P]), M11 = from_f64<T>(fc[FC_M11 * P]);
+  T sig, M00, M01, M10, M11;
+  if constexpr (sizeof(T) == 4) {   // FP32 copies of the hand-back coefficients after the 18 map rows
+    M00 = lf[18 * P];
+    M01 = lf[19 * P];
+    M10 = lf[20 * P];
+    M11 = lf[21 * P];
+    sig = lf[22 * P];
+  } else {
+    const double* fc = a.fc + t;
+    sig = fc[FC_SIG * P];
+    M00 = fc[FC_M00 * P];
+    M01 = fc[FC_M01 * P];
+    M10 = fc[FC_M10 * P];
+    M11 = fc[FC_M11 * P];
+  }
   T* fo = a.fb + ((long long)L.owner * 4 + L.owner_edge) * 3 * NS + i;
   fo[0] = f[0];
   fo[NS] = f[1];

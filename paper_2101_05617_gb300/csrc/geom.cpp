@@ -255,6 +255,8 @@ int build_tables(Ctx& c) {
   for (int k = 0; k < ns; ++k) {
     c.dc.lm[k] = lm[k];
     c.dc.lp[k] = lp[k];
+    c.dc.lm32[k] = (float)lm[k];
+    c.dc.lp32[k] = (float)lp[k];
   }
   c.Dg = (ns == 1) ? std::vector<double>(1, 0.0) : bary_diff(c.xi);
   for (int k = 0; k < ns; ++k)

@@ -73,6 +73,7 @@ struct DfrConst {
   double D[MAX_NS][MAX_NS + 2];   // l~'_n(xi_k), Eq. (12)-(13)
   double Dg[MAX_NS][MAX_NS];      // l'_l(xi_k) on the solution points (collocation derivative)
   double lm[MAX_NS], lp[MAX_NS];  // l_k(-1), l_k(+1), Eq. (8)
+  float lm32[MAX_NS], lp32[MAX_NS];  // the same rounded to FP32 (complex64-bulk form)
   double two_over_dx;             // Eq. (6)
   double gravity;
 };
@@ -133,7 +134,7 @@ struct Ctx {
   double* d_lin_node = nullptr;     // [LN_COUNT][nodes]
   double* d_lin_face = nullptr;     // [18][nfacepts]
   float* d_lin_node32 = nullptr;    // FP32 copies (complex64-bulk form)
-  float* d_lin_face32 = nullptr;
+  float* d_lin_face32 = nullptr;    // [23][nfacepts]: the 18 flux-map rows, then M00, M01, M10, M11, sigma
   float* d_V32 = nullptr;           // FP32 copy of the Krylov basis [vcap][ldv] (complex64-bulk form)
   int v32_cap = 0;                  // rows allocated in d_V32
   float* d_b32 = nullptr;           // FP32 copies of nu * b_l of the current phi-function call [MAX_NB][n]
