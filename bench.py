@@ -424,16 +424,19 @@ def fp32_form_comparison(args, dev, workload="ne30_p5", variants=(("fp64", 1, 2)
     kernels = {}
     stats = {}
     dt0 = wl.dt if dt is None else dt
-    runs = [(v[0], v[1], v[2], dt0, 1, len(v) > 3 and v[3] == "learned") for v in variants]
-    runs.append(("fp64_dt4", 1, 2, dt0 / 4, 4, False))
+    runs = [(v[0], v[1], v[2], dt0, 1, v[3] if len(v) > 3 else "") for v in variants]
+    runs.append(("fp64_dt4", 1, 2, dt0 / 4, 4, ""))
     ctl = None
     fields = None   # the same grid and rotation for every run: evaluate the fields once
-    for name, mode, iop, dt, mult, use_ctl in runs:
+    for name, mode, iop, dt, mult, extra in runs:
+        use_ctl = extra == "learned"
         ctx = swepi.SWContext(wl.ne, wl.p, f.rotation)
         if fields is None:
             fields = f.evaluate(ctx.node_xyz())
         q = torch.tensor(ctx.state_from_fields(*fields), device=dev)
         ctx.set_jvp_mode(mode)
+        if extra == "device":   # the phi-function solver's controller on the device (one CUDA graph per call)
+            ctx.set_kiops_driver(1)
         try:
             for _ in range(warm * mult):
                 ctx.epi_step(wl.order, dt, q, tol=wl.tol, iop=iop)
@@ -484,7 +487,8 @@ def fp32_form_comparison(args, dev, workload="ne30_p5", variants=(("fp64", 1, 2)
     for v in variants:
         name, mode, iop = v[0], v[1], v[2]
         out[name] = {"jvp": "FP64" if mode == 1 else "complex64 bulk (FP32 imaginary half)", "window": iop,
-                     "control": v[3] if len(v) > 3 else "plain"}
+                     "control": "learned" if len(v) > 3 and v[3] == "learned" else "plain",
+                     "controller_on": "device" if len(v) > 3 and v[3] == "device" else "host"}
         if not ok(name):
             out[name]["error"] = res[name]
             continue
@@ -896,8 +900,10 @@ def main():
                 # the configured 48 EPI5 steps of this grid (4 untimed, 44 timed) from the same start
                 form("complex64_bulk_ne60_p5", lambda: fp32_form_comparison(
                     args, dev, "ne60_p5", (("fp64", 1, 2), ("fp64_window3", 1, 3), ("complex64_bulk_window3", 2, 3),
-                                           ("complex64_bulk_window3_learned", 2, 3, "learned")), fp64_peak=peak,
-                    total_steps=48))
+                                           ("complex64_bulk_window3_learned", 2, 3, "learned"),
+                                           ("fp64_device_controller", 1, 2, "device"),
+                                           ("complex64_bulk_window3_device_controller", 2, 3, "device")),
+                    fp64_peak=peak, total_steps=48))
             if world == 1 and not args.no_ensemble:
                 form("ensemble_96", lambda: ensemble_form(args, dev, peak))
             if world == 1 and not args.no_large:

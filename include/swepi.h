@@ -185,6 +185,20 @@ int sw_jvp_linearized(sw_ctx_t ctx, const double* v_dev, double* Jv_dev, void* s
  * linearisation. */
 int sw_set_jvp_mode(sw_ctx_t ctx, int mode);
 
+/* Where the phi-function solver's adaptive controller runs (Eq. 29 and the
+ * KIOPS reading: accept/reject, the next substep tau and Krylov size m):
+ * 0 = on the host (default), which reads a few device scalars after each
+ * substep attempt; 1 = on the device: the whole call is one CUDA graph whose
+ * conditional loops (attempts, Krylov iterations, squarings of the small
+ * exponential) are steered by device kernels running the same controller, and
+ * the host synchronises once, when the call returns.  The device controller
+ * applies to the split JVP (modes 1 and 2) with windows 2 and 3 and the plain
+ * rule while profiling is off; other calls use the host controller.  It caps a
+ * call at 2000 substep attempts (SW_EKRYLOV).  The graph is built on the first
+ * call and again when the window, the number of phi-vectors, the form or the
+ * Krylov workspace changes. */
+int sw_set_kiops_driver(sw_ctx_t ctx, int driver);
+
 /* w = sum_{k=0}^{nb-1} tau_out^k phi_k(tau_out dt J(q_lin)) b_k (Eq. 29), J by
  * the complex-step product above.  b_dev_host: host array of nb device
  * pointers (1 <= nb <= 8); a NULL entry means a zero vector.  w_dev: n

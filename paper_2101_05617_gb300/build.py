@@ -14,7 +14,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libswepi.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
-SOURCES = ["geom.cpp", "dfr.cu", "krylov.cu", "kiops.cu", "capi.cu", "noalloc.cu", "dfr_split.cu", "dfr_tile.cu", "mlp.cu", "diag.cu", "ensemble.cu"]
+SOURCES = ["geom.cpp", "dfr.cu", "krylov.cu", "kiops.cu", "kiops_graph.cu", "capi.cu", "noalloc.cu", "dfr_split.cu", "dfr_tile.cu", "mlp.cu", "diag.cu", "ensemble.cu"]
 
 
 def nvcc():

@@ -267,6 +267,7 @@ int sw_init(int n_e, int p, const sw_params* prm, sw_ctx_t* out) {
 
 void sw_free(sw_ctx_t c) {
   if (!c) return;
+  kiops_graph_free(*c);
   double* ptrs[] = {c->d_node_coef, c->d_face_coef, c->d_fb, c->d_V, c->d_X, c->d_H, c->d_F, c->d_expm_ws,
                     c->d_partials, c->d_scal, c->d_Fn, c->d_tmp, c->d_tmp2, c->d_lin_node, c->d_lin_face,
                     c->d_vpart, c->d_cdot, c->d_cdot2, c->d_diag_tab, c->d_diag_part, c->d_diag_out, c->d_qhost};
@@ -598,6 +599,12 @@ int sw_kiops_log(sw_ctx_t c, float* out, int max_records) {
 int sw_kiops_log_clear(sw_ctx_t c) {
   if (!c) return SW_EINVAL;
   c->kiops_log.clear();
+  return SW_OK;
+}
+
+int sw_set_kiops_driver(sw_ctx_t c, int driver) {
+  if (!c || driver < 0 || driver > 1) return SW_EINVAL;
+  c->kiops_driver = driver;
   return SW_OK;
 }
 

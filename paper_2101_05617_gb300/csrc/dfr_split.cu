@@ -27,6 +27,7 @@
 
 #include "dfr_device.cuh"
 #include "dfr_tangent.cuh"
+#include "kiops_dev.h"
 #include "swepi_internal.h"
 
 namespace swepi {
@@ -128,6 +129,35 @@ __global__ void __launch_bounds__(VolShape<NS>::THREADS) volume_tangent_kernel(T
   volume_tangent_body<T, NS, VolShape<NS>::EPB, VolShape<NS>::THREADS, W3>(a, dc, blockIdx.x, gridDim.x, sm);
 }
 
+// the same kernels for the device-driven solver: the Krylov iteration index and
+// the augmented operator come from its device state
+template <typename T, int NS>
+__global__ void __launch_bounds__(128) face_tangent_dev_kernel(const KDev* __restrict__ kd, KFix f,
+                                                               TanFaceArgs<T> a, DfrConst dc) {
+  if (*a.skip) return;
+  const long long it = kd->it;
+  a.v = f.V + it * f.ldv;
+  a.v32 = (sizeof(T) == 4 && f.V32) ? f.V32 + it * f.ldv : nullptr;
+  face_tangent_body<T, NS>(a, dc, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+template <typename T, int NS, bool W3>
+__global__ void __launch_bounds__(VolShape<NS>::THREADS) volume_tangent_dev_kernel(const KDev* __restrict__ kd, KFix f,
+                                                                                   TanVolArgs<T> a0, DfrConst dc) {
+  __shared__ TanVolArgs<T> a;
+  if (threadIdx.x == 0) {
+    a = a0;
+    const int it = kd->it;
+    a.v = f.V + (long long)it * f.ldv;
+    a.out = f.V + (long long)(it + 1) * f.ldv;
+    iter_epilogue_dev(a.ep, *kd, f, it, W3, sizeof(T) == 4);
+  }
+  __syncthreads();
+  if (*a.ep.skip) return;
+  __shared__ VolSmem<T, NS, VolShape<NS>::EPB> sm;
+  volume_tangent_body<T, NS, VolShape<NS>::EPB, VolShape<NS>::THREADS, W3>(a, dc, blockIdx.x, gridDim.x, sm);
+}
+
 __global__ void to_float_kernel(const double* __restrict__ src, float* __restrict__ dst, long long n) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     dst[i] = (float)src[i];
@@ -193,7 +223,50 @@ int tangent_any(Ctx& c, const double* v, double* out, const AugEpilogue& ep, boo
   return tangent_ns<double, NS>(c, v, out, ep, c.d_lin_node, c.d_lin_face, c.d_fb, s);
 }
 
+template <typename T, int NS>
+int capture_iter_ns(Ctx& c, KDev* kd, const KFix& f, bool w3, int p, cudaStream_t s) {
+  const bool fp32 = sizeof(T) == 4;
+  const T* lf = fp32 ? reinterpret_cast<const T*>(c.d_lin_face32) : reinterpret_cast<const T*>(c.d_lin_face);
+  const T* ln = fp32 ? reinterpret_cast<const T*>(c.d_lin_node32) : reinterpret_cast<const T*>(c.d_lin_node);
+  T* fb = reinterpret_cast<T*>(c.d_fb);
+  TanFaceArgs<T> fa{nullptr, nullptr, c.nodes, c.d_lines, c.d_face_coef, lf, c.nfacepts, fb, c.d_flags};
+  face_tangent_dev_kernel<T, NS><<<(unsigned)((c.nfacepts + 127) / 128), 128, 0, s>>>(kd, f, fa, c.dc);
+  c.launches++;
+  if (cudaGetLastError() != cudaSuccess) return SW_ECUDA;
+  if (fp32 && p <= kTileMaxB) {   // the staged kernel where the buffers allow it
+    const int rt = capture_volume_tile_dev<NS>(c, kd, f, w3, s);
+    if (rt <= 0) return rt;
+  }
+  TanVolArgs<T> va{nullptr, c.nodes, c.nelem, ln, fb, nullptr, AugEpilogue{}};
+  const long long vblocks = (c.nelem + VolShape<NS>::EPB - 1) / VolShape<NS>::EPB;
+  if (w3)
+    volume_tangent_dev_kernel<T, NS, true><<<(unsigned)vblocks, VolShape<NS>::THREADS, 0, s>>>(kd, f, va, c.dc);
+  else
+    volume_tangent_dev_kernel<T, NS, false><<<(unsigned)vblocks, VolShape<NS>::THREADS, 0, s>>>(kd, f, va, c.dc);
+  c.launches++;
+  return cuda_status(cudaGetLastError());
+}
+
+template <int NS>
+int capture_iter_any(Ctx& c, KDev* kd, const KFix& f, bool fp32, bool w3, int p, cudaStream_t s) {
+  return fp32 ? capture_iter_ns<float, NS>(c, kd, f, w3, p, s) : capture_iter_ns<double, NS>(c, kd, f, w3, p, s);
+}
+
 }  // namespace
+
+int capture_iter_jvp(Ctx& c, KDev* kd, const KFix& f, bool fp32, bool w3, int p, cudaStream_t s) {
+  switch (c.ns) {
+    case 1: return capture_iter_any<1>(c, kd, f, fp32, w3, p, s);
+    case 2: return capture_iter_any<2>(c, kd, f, fp32, w3, p, s);
+    case 3: return capture_iter_any<3>(c, kd, f, fp32, w3, p, s);
+    case 4: return capture_iter_any<4>(c, kd, f, fp32, w3, p, s);
+    case 5: return capture_iter_any<5>(c, kd, f, fp32, w3, p, s);
+    case 6: return capture_iter_any<6>(c, kd, f, fp32, w3, p, s);
+    case 7: return capture_iter_any<7>(c, kd, f, fp32, w3, p, s);
+    case 8: return capture_iter_any<8>(c, kd, f, fp32, w3, p, s);
+    default: return SW_EINVAL;
+  }
+}
 
 int launch_linearize(Ctx& c, const double* q, cudaStream_t s) {
   if (!c.d_lin_node && cudaMalloc(&c.d_lin_node, sizeof(double) * LN_COUNT * c.nodes) != cudaSuccess)

@@ -29,13 +29,14 @@
 #include <cstdint>
 
 #include "dfr_tangent.cuh"
+#include "kiops_dev.h"
 #include "swepi_internal.h"
 
 namespace swepi {
 
 namespace {
 
-constexpr int KMAXB = 4;     // b-column vectors staged per tile (EPI orders up to 6 use p <= 4)
+constexpr int KMAXB = kTileMaxB;   // b-column vectors staged per tile (EPI orders up to 6 use p <= 4)
 
 constexpr int tile_epb(int nn) {
   int e = (256 / nn) > 0 ? (256 / nn) : 1;
@@ -154,17 +155,14 @@ __device__ __forceinline__ void issue_tile(const TanVolArgs<float>& a, long long
 // Each thread accumulates its window dots over all its tiles; one block
 // reduction per CTA then feeds the shared epilogue.
 template <int NS, bool W3>
-__global__ void __launch_bounds__(TileShape<NS>::TN, 2) volume_tangent_tile_f32_kernel(TanVolArgs<float> a,
-                                                                                      DfrConst dc, int* err) {
+__device__ __forceinline__ void tile_body(const TanVolArgs<float>& a, const DfrConst& dc, int* err,
+                                          unsigned char* sm) {
   using L = TileLayout<NS>;
   constexpr int NN = NS * NS, TN = TileShape<NS>::TN;
-  extern __shared__ __align__(16) unsigned char sm[];
   float (*sF)[2][3][NN] = reinterpret_cast<float (*)[2][3][NN]>(sm + L::flux);
   float (*sD)[NS + 3] = reinterpret_cast<float (*)[NS + 3]>(sm + L::dmat);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + L::mbar);
 
-  pdl_wait();
-  pdl_trigger();
   const AugEpilogue& ep = a.ep;
   if (ep.skip && *ep.skip) return;
   const long long N = a.nodes;
@@ -285,6 +283,54 @@ __global__ void __launch_bounds__(TileShape<NS>::TN, 2) volume_tangent_tile_f32_
   epilogue_finish<TN, W3>(ep, da, db, dcc, blockIdx.x, gridDim.x);
 }
 
+template <int NS, bool W3>
+__global__ void __launch_bounds__(TileShape<NS>::TN, 2) volume_tangent_tile_f32_kernel(TanVolArgs<float> a,
+                                                                                      DfrConst dc, int* err) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  pdl_wait();
+  pdl_trigger();
+  tile_body<NS, W3>(a, dc, err, sm);
+}
+
+// the same for the device-driven solver: the iteration index and the augmented
+// operator come from its device state
+template <int NS, bool W3>
+__global__ void __launch_bounds__(TileShape<NS>::TN, 2) volume_tangent_tile_dev_kernel(const KDev* __restrict__ kd,
+                                                                                     KFix f, TanVolArgs<float> a0,
+                                                                                     DfrConst dc, int* err) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ TanVolArgs<float> a;
+  if (threadIdx.x == 0) {
+    a = a0;
+    const int it = kd->it;
+    a.v = f.V + (long long)it * f.ldv;
+    a.out = f.V + (long long)(it + 1) * f.ldv;
+    iter_epilogue_dev(a.ep, *kd, f, it, W3, true);
+  }
+  __syncthreads();
+  tile_body<NS, W3>(a, dc, err, sm);
+}
+
+template <int NS, bool W3, bool DEV>
+int set_tile_smem() {
+  static bool configured = false;
+  if (configured) return SW_OK;
+  const cudaError_t e =
+      DEV ? cudaFuncSetAttribute(volume_tangent_tile_dev_kernel<NS, W3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)TileLayout<NS>::bytes)
+          : cudaFuncSetAttribute(volume_tangent_tile_f32_kernel<NS, W3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)TileLayout<NS>::bytes);
+  if (e != cudaSuccess) return SW_ECUDA;
+  configured = true;
+  return SW_OK;
+}
+
+int persistent_ctas(const Ctx& c, long long tiles) {
+  static int sms = 0;
+  if (!sms && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess) return -1;
+  return (int)std::min<long long>(tiles, 2LL * sms);   // two persistent CTAs per SM
+}
+
 template <int NS>
 bool tile_eligible(const Ctx& c, const double* v, const double* out, const AugEpilogue& ep) {
   auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
@@ -302,18 +348,12 @@ bool tile_eligible(const Ctx& c, const double* v, const double* out, const AugEp
 template <int NS, bool W3>
 int launch_tile(Ctx& c, const double* v, double* out, const AugEpilogue& ep, cudaStream_t s) {
   using L = TileLayout<NS>;
-  static bool configured = false;
   auto kernel = volume_tangent_tile_f32_kernel<NS, W3>;
-  if (!configured) {
-    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes) != cudaSuccess)
-      return SW_ECUDA;
-    configured = true;
-  }
+  if (int rc = set_tile_smem<NS, W3, false>()) return rc;
   TanVolArgs<float> va{v, c.nodes, c.nelem, c.d_lin_node32, reinterpret_cast<const float*>(c.d_fb), out, ep};
   const long long tiles = (c.nodes + TileShape<NS>::TN - 1) / TileShape<NS>::TN;
-  static int sms = 0;
-  if (!sms && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess) return SW_ECUDA;
-  const long long ctas = std::min<long long>(tiles, 2LL * sms);   // two persistent CTAs per SM
+  const int ctas = persistent_ctas(c, tiles);
+  if (ctas < 0) return SW_ECUDA;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)ctas);
   cfg.blockDim = dim3(TileShape<NS>::TN);
@@ -339,6 +379,64 @@ int launch_volume_tile_f32(Ctx& c, const double* v, double* out, const AugEpilog
   if (!tile_eligible<NS>(c, v, out, ep)) return 1;
   return ep.dotC ? launch_tile<NS, true>(c, v, out, ep, s) : launch_tile<NS, false>(c, v, out, ep, s);
 }
+
+template <int NS>
+int capture_volume_tile_dev(Ctx& c, KDev* kd, const KFix& f, bool w3, cudaStream_t s) {
+  // eligibility with the buffers every iteration uses (basis rows, their FP32
+  // copies, the b-column copies)
+  AugEpilogue ep;
+  ep.p = 1;
+  ep.dotA = ep.dotB = f.V;
+  ep.dotC = w3 ? f.V : nullptr;
+  ep.v32 = f.V32;
+  if (!f.V32 || !tile_eligible<NS>(c, f.V, f.V, ep)) return 1;
+  if (f.b32 && (reinterpret_cast<uintptr_t>(f.b32) & 15u)) return 1;
+  if ((f.n * sizeof(float)) % 16 != 0) return 1;
+  using L = TileLayout<NS>;
+  const int rc = w3 ? set_tile_smem<NS, true, true>() : set_tile_smem<NS, false, true>();
+  if (rc) return rc;
+  TanVolArgs<float> va{nullptr, c.nodes, c.nelem, c.d_lin_node32, reinterpret_cast<const float*>(c.d_fb), nullptr,
+                       AugEpilogue{}};
+  const long long tiles = (c.nodes + TileShape<NS>::TN - 1) / TileShape<NS>::TN;
+  const int ctas = persistent_ctas(c, tiles);
+  if (ctas < 0) return SW_ECUDA;
+  int* err = c.d_flags + 3;
+  if (w3)
+    volume_tangent_tile_dev_kernel<NS, true><<<ctas, TileShape<NS>::TN, L::bytes, s>>>(kd, f, va, c.dc, err);
+  else
+    volume_tangent_tile_dev_kernel<NS, false><<<ctas, TileShape<NS>::TN, L::bytes, s>>>(kd, f, va, c.dc, err);
+  c.launches++;
+  return cuda_status(cudaGetLastError());
+}
+
+template <int NS>
+int prepare_dev() {
+  if (int rc = set_tile_smem<NS, false, true>()) return rc;
+  return set_tile_smem<NS, true, true>();
+}
+
+int prepare_volume_tile_dev(const Ctx& c) {
+  switch (c.ns) {
+    case 1: return prepare_dev<1>();
+    case 2: return prepare_dev<2>();
+    case 3: return prepare_dev<3>();
+    case 4: return prepare_dev<4>();
+    case 5: return prepare_dev<5>();
+    case 6: return prepare_dev<6>();
+    case 7: return prepare_dev<7>();
+    case 8: return prepare_dev<8>();
+    default: return SW_EINVAL;
+  }
+}
+
+template int capture_volume_tile_dev<1>(Ctx&, KDev*, const KFix&, bool, cudaStream_t);
+template int capture_volume_tile_dev<2>(Ctx&, KDev*, const KFix&, bool, cudaStream_t);
+template int capture_volume_tile_dev<3>(Ctx&, KDev*, const KFix&, bool, cudaStream_t);
+template int capture_volume_tile_dev<4>(Ctx&, KDev*, const KFix&, bool, cudaStream_t);
+template int capture_volume_tile_dev<5>(Ctx&, KDev*, const KFix&, bool, cudaStream_t);
+template int capture_volume_tile_dev<6>(Ctx&, KDev*, const KFix&, bool, cudaStream_t);
+template int capture_volume_tile_dev<7>(Ctx&, KDev*, const KFix&, bool, cudaStream_t);
+template int capture_volume_tile_dev<8>(Ctx&, KDev*, const KFix&, bool, cudaStream_t);
 
 template int launch_volume_tile_f32<1>(Ctx&, const double*, double*, const AugEpilogue&, cudaStream_t);
 template int launch_volume_tile_f32<2>(Ctx&, const double*, double*, const AugEpilogue&, cudaStream_t);

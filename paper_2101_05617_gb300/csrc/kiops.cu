@@ -93,6 +93,7 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
   if (nb < 1 || nb > MAX_NB || !(tau_out > 0) || o.m_min < 1 || o.m_max < o.m_min || o.m_max > 150 || o.iop < 1 ||
       !(o.tol > 0))
     return SW_EINVAL;
+  if (kiops_graph_applies(c, o, use_lin)) return kiops_run_graph(c, dt, tau_out, nb, b, o, w, st, s);
   TraceRange trace("phi-function call");
   int rc = ensure_krylov(c, o.m_max);
   if (rc) return rc;

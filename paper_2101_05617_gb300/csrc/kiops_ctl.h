@@ -10,7 +10,21 @@
 
 #include "swepi_internal.h"
 
+#ifdef __CUDACC__
+#define SW_HD __host__ __device__
+#else
+#define SW_HD
+#endif
+
 namespace swepi {
+
+// plain helpers usable on the host (the glibc functions) and on the device;
+// min and max take the same branches as std::min and std::max (NaN included)
+SW_HD inline double kc_min(double a, double b) { return (b < a) ? b : a; }
+SW_HD inline double kc_max(double a, double b) { return (a < b) ? b : a; }
+SW_HD inline int kc_mini(int a, int b) { return (b < a) ? b : a; }
+SW_HD inline int kc_maxi(int a, int b) { return (a < b) ? b : a; }
+SW_HD inline bool kc_finite(double x) { return x - x == 0.0; }   // false for NaN and +-inf
 
 constexpr int kMaxSubsteps = 100000;   // per call: beyond this the solver gives up (SW_EKRYLOV)
 constexpr int kMaxRejects = 100000;
@@ -43,7 +57,7 @@ struct KiopsController {
   int m_new = 0, j_used = 0;
   double tau_new = 0.0;
 
-  void start(double tau_out, double tol_, double beta0_, const sw_kiops_opts& o, double tau0, int m0) {
+  SW_HD void start(double tau_out, double tol_, double beta0_, const sw_kiops_opts& o, double tau0, int m0) {
     tau_end = tau_out;
     tol = tol_;
     beta0 = beta0_;
@@ -53,11 +67,11 @@ struct KiopsController {
     m = m0;
   }
 
-  bool done() const { return tau_now >= tau_end; }
+  SW_HD bool done() const { return tau_now >= tau_end; }
 
   // Decide after an attempt with Krylov size jnew (happy breakdown or m).
   // beta: norm of the substep's start vector; hsub = h_{j+1,j}; Fjj = F[j-1][j].
-  int decide(bool happy_, int jnew, double beta, double hsub, double Fjj) {
+  SW_HD int decide(bool happy_, int jnew, double beta, double hsub, double Fjj) {
     happy = happy_;
     krylov += jnew - j;
     j = jnew;
@@ -70,31 +84,31 @@ struct KiopsController {
     } else {
       hist_h[nh % 4] = hsub;
       ++nh;
-      err = beta * hsub * std::fabs(Fjj);
+      err = beta * hsub * ::fabs(Fjj);
       const double omega = (tau_end / tau) * err / (tol * beta0);
-      if (!std::isfinite(omega)) return SW_ENONFINITE;
+      if (!kc_finite(omega)) return SW_ENONFINITE;
       accept = omega <= kDelta;
       last_omega = omega;
       const double order = (have_prev && prev_m == m && prev_tau != tau)
-                               ? std::max(1.0, std::log(omega / prev_omega) / std::log(tau / prev_tau))
+                               ? kc_max(1.0, ::log(omega / prev_omega) / ::log(tau / prev_tau))
                                : j / 4.0;
       last_order = order;
       const double kappa = (have_prev && prev_tau == tau && prev_m != m)
-                               ? std::max(1.1, std::pow(omega / prev_omega, 1.0 / (prev_m - m)))
+                               ? kc_max(1.1, ::pow(omega / prev_omega, 1.0 / (prev_m - m)))
                                : 2.0;
       const double remaining = accept ? tau_end - (tau_now + tau) : tau_end - tau_now;
-      const double tau_same = std::min(remaining, tau);
-      double tau_opt = (omega > 0) ? tau * std::pow(kGamma / omega, 1.0 / order) : 5 * tau;
-      tau_opt = std::min(remaining, std::max(tau / 5, std::min(5 * tau, tau_opt)));
-      int m_opt = (omega > 0) ? (int)std::ceil(j + std::log(omega / kGamma) / std::log(kappa)) : m_min;
-      m_opt = std::max(m_min, std::min(m_max, std::max((int)std::floor(3.0 * m / 4.0),
-                                                       std::min(m_opt, (int)std::ceil(4.0 * m / 3.0)))));
+      const double tau_same = kc_min(remaining, tau);
+      double tau_opt = (omega > 0) ? tau * ::pow(kGamma / omega, 1.0 / order) : 5 * tau;
+      tau_opt = kc_min(remaining, kc_max(tau / 5, kc_min(5 * tau, tau_opt)));
+      int m_opt = (omega > 0) ? (int)::ceil(j + ::log(omega / kGamma) / ::log(kappa)) : m_min;
+      m_opt = kc_maxi(m_min, kc_mini(m_max, kc_maxi((int)::floor(3.0 * m / 4.0),
+                                                    kc_mini(m_opt, (int)::ceil(4.0 * m / 3.0)))));
       if (j == m_max) {
         m_new = m;
         tau_new = tau_opt;
       } else {
-        const double cost_tau = tau_opt > 0 ? m * std::ceil(remaining / tau_opt) : 0.0;
-        const double cost_m = tau_same > 0 ? m_opt * std::ceil(remaining / tau_same) : 0.0;
+        const double cost_tau = tau_opt > 0 ? m * ::ceil(remaining / tau_opt) : 0.0;
+        const double cost_m = tau_same > 0 ? m_opt * ::ceil(remaining / tau_same) : 0.0;
         if (cost_tau <= cost_m) {
           m_new = m;
           tau_new = tau_opt;
@@ -116,15 +130,15 @@ struct KiopsController {
       tau_first = tau;
       m_first = j;
       // largest first substep the error model admits: omega ~ tau^order
-      tau_star = (happy || last_omega <= 0) ? tau_end : tau * std::pow(kGamma / last_omega, 1.0 / last_order);
-      tau_star = std::min(tau_end, std::max(tau, tau_star));
+      tau_star = (happy || last_omega <= 0) ? tau_end : tau * ::pow(kGamma / last_omega, 1.0 / last_order);
+      tau_star = kc_min(tau_end, kc_max(tau, tau_star));
     }
     return SW_OK;
   }
 
   // After the caller has combined the basis (on acceptance): advance the state.
   // Returns the new tau_now.  Limits on substeps / rejections -> SW_EKRYLOV.
-  int finish(int max_substeps, int max_rejects) {
+  SW_HD int finish(int max_substeps, int max_rejects) {
     if (accept) {
       tau_now += tau;
       ++substeps;
@@ -137,17 +151,17 @@ struct KiopsController {
       if (m_new < j) j = m_new;
     }
     m = m_new;
-    if (tau_now < tau_end) tau = (tau_new > 0) ? std::min(tau_new, tau_end - tau_now) : tau_end - tau_now;
+    if (tau_now < tau_end) tau = (tau_new > 0) ? kc_min(tau_new, tau_end - tau_now) : tau_end - tau_now;
     return SW_OK;
   }
 
   // tail of the augmented vector after acceptance: mu (tau_now^{p-1}/(p-1)!, ..., tau_now, 1)
-  void tail(int p, double mu, double* out) const {
+  SW_HD void tail(int p, double mu, double* out) const {
     for (int l = 0; l < p; ++l) {
       const int k = p - 1 - l;
       double f = 1.0;
       for (int t = 2; t <= k; ++t) f *= t;
-      out[l] = mu * std::pow(tau_now, k) / f;
+      out[l] = mu * ::pow(tau_now, k) / f;
     }
   }
 };

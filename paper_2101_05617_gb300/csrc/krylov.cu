@@ -145,9 +145,6 @@ __global__ void expm_finish_kernel(const double* __restrict__ P, int N, double* 
     expm_finish_entry(P, N, F, ldh, stat, i);
 }
 
-// z -= h0 V_C + h1 V_A + h2 V_B (the modified Gram-Schmidt updates, oldest
-// first; V_C, V_A may be absent), then ||z||_2 -> *hsub with the
-// happy-breakdown flag below tol
 __global__ void __launch_bounds__(RED_THREADS) update_norm_kernel(double* __restrict__ z, const double* __restrict__ VA,
                                                                   const double* __restrict__ VB, const double* h1p,
                                                                   const double* h2p, long long n, double* partials,
@@ -156,36 +153,9 @@ __global__ void __launch_bounds__(RED_THREADS) update_norm_kernel(double* __rest
                                                                   const double* __restrict__ VC, const double* h0p) {
   pdl_wait();
   pdl_trigger();
-  if (happy[0]) return;
-  const double h1 = VA ? *h1p : 0.0, h2 = *h2p, h0 = VC ? *h0p : 0.0;
-  const double acc = mgs_update_range(z, VA, VB, h1, h2, (long long)blockIdx.x * blockDim.x + threadIdx.x, n,
-                                      (long long)gridDim.x * blockDim.x, VC, h0);
-  double b = block_sum(acc);
-  __shared__ bool last;
-  if (threadIdx.x == 0) {
-    partials[blockIdx.x] = b;
-    __threadfence();
-    last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  double sum = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) sum += __ldcg(partials + i);
-  sum = block_sum(sum);
-  if (threadIdx.x == 0) {
-    const double r = sqrt(sum);
-    *hsub = r;
-    if (r < tol) {
-      happy[0] = 1;
-      happy[1] = happy_value;
-    }
-    *ticket = 0u;
-  }
+  update_norm_dev(z, VA, VB, h1p, h2p, n, partials, ticket, hsub, tol, happy, happy_value, VC, h0p);
 }
 
-// V_next = z / *hsub in place, V_next . V_B -> *c_out and, with V_A, V_next .
-// V_A -> *c2_out (used by the next iterations' orthogonalisation)
 __global__ void __launch_bounds__(RED_THREADS) scale_dot_kernel(double* __restrict__ z, const double* __restrict__ VB,
                                                                 const double* hsub, long long n, double* partials,
                                                                 unsigned int* ticket, double* c_out, const int* happy,
@@ -193,35 +163,7 @@ __global__ void __launch_bounds__(RED_THREADS) scale_dot_kernel(double* __restri
                                                                 float* __restrict__ z32) {
   pdl_wait();
   pdl_trigger();
-  if (happy[0]) return;
-  const double r = 1.0 / *hsub;
-  double acc2 = 0.0;
-  const double acc = scale_dot_range(z, VB, r, (long long)blockIdx.x * blockDim.x + threadIdx.x, n,
-                                     (long long)gridDim.x * blockDim.x, VA, &acc2, z32);
-  const double b = block_sum(acc);
-  const double b2 = VA ? block_sum(acc2) : 0.0;   // uniform condition
-  __shared__ bool last;
-  if (threadIdx.x == 0) {
-    partials[2 * blockIdx.x] = b;
-    partials[2 * blockIdx.x + 1] = b2;
-    __threadfence();
-    last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  double sum = 0.0, sum2 = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
-    sum += __ldcg(partials + 2 * i);
-    if (VA) sum2 += __ldcg(partials + 2 * i + 1);
-  }
-  sum = block_sum(sum);
-  if (VA) sum2 = block_sum(sum2);
-  if (threadIdx.x == 0) {
-    *c_out = sum;
-    if (VA) *c2_out = sum2;
-    *ticket = 0u;
-  }
+  scale_dot_dev(z, VB, hsub, n, partials, ticket, c_out, happy, VA, c2_out, z32);
 }
 
 int blocks_for(long long n, int threads) {

@@ -134,6 +134,83 @@ __device__ __forceinline__ double scale_dot_range(double* __restrict__ z, const 
   return acc;
 }
 
+// The two vector passes of the fused incomplete orthogonalisation, as device
+// functions of a whole grid (the stream kernels of krylov.cu and the
+// device-driven solver call them).
+// z -= h0 V_C + h1 V_A + h2 V_B (the modified Gram-Schmidt updates, oldest
+// first; V_C, V_A may be absent), then ||z||_2 -> *hsub with the
+// happy-breakdown flag below tol
+__device__ __forceinline__ void update_norm_dev(double* __restrict__ z, const double* __restrict__ VA,
+                                                const double* __restrict__ VB, const double* h1p, const double* h2p,
+                                                long long n, double* partials, unsigned int* ticket, double* hsub,
+                                                double tol, int* happy, int happy_value, const double* __restrict__ VC,
+                                                const double* h0p) {
+  if (happy[0]) return;
+  const double h1 = VA ? *h1p : 0.0, h2 = *h2p, h0 = VC ? *h0p : 0.0;
+  const double acc = mgs_update_range(z, VA, VB, h1, h2, (long long)blockIdx.x * blockDim.x + threadIdx.x, n,
+                                      (long long)gridDim.x * blockDim.x, VC, h0);
+  double b = block_sum(acc);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = b;
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double sum = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) sum += __ldcg(partials + i);
+  sum = block_sum(sum);
+  if (threadIdx.x == 0) {
+    const double r = sqrt(sum);
+    *hsub = r;
+    if (r < tol) {
+      happy[0] = 1;
+      happy[1] = happy_value;
+    }
+    *ticket = 0u;
+  }
+}
+
+// V_next = z / *hsub in place, V_next . V_B -> *c_out and, with V_A, V_next .
+// V_A -> *c2_out (used by the next iterations' orthogonalisation); with z32
+// also the FP32 copy of V_next
+__device__ __forceinline__ void scale_dot_dev(double* __restrict__ z, const double* __restrict__ VB,
+                                              const double* hsub, long long n, double* partials, unsigned int* ticket,
+                                              double* c_out, const int* happy, const double* __restrict__ VA,
+                                              double* c2_out, float* __restrict__ z32) {
+  if (happy[0]) return;
+  const double r = 1.0 / *hsub;
+  double acc2 = 0.0;
+  const double acc = scale_dot_range(z, VB, r, (long long)blockIdx.x * blockDim.x + threadIdx.x, n,
+                                     (long long)gridDim.x * blockDim.x, VA, &acc2, z32);
+  const double b = block_sum(acc);
+  const double b2 = VA ? block_sum(acc2) : 0.0;   // uniform condition
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = b;
+    partials[2 * blockIdx.x + 1] = b2;
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double sum = 0.0, sum2 = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    sum += __ldcg(partials + 2 * i);
+    if (VA) sum2 += __ldcg(partials + 2 * i + 1);
+  }
+  sum = block_sum(sum);
+  if (VA) sum2 = block_sum(sum2);
+  if (threadIdx.x == 0) {
+    *c_out = sum;
+    if (VA) *c2_out = sum2;
+    *ticket = 0u;
+  }
+}
+
 // ------------------------------------------------------------ expm
 // F = exp(A), A = t [[H_j, e_1], [0, 0]] (order N = j + 1 <= MAX_EXPM): scaling
 // and squaring (Moler and Van Loan, "Nineteen dubious ways to compute the
@@ -161,13 +238,13 @@ struct ExpmProduct {
 };
 
 // the 8 products before the squarings, for s squarings
-inline void expm_products(int sq, ExpmProduct out[8]) {
+inline __host__ __device__ void expm_products(int sq, ExpmProduct out[8]) {
   double cf[17];
   cf[0] = 1.0;
   for (int k = 1; k <= 16; ++k) cf[k] = cf[k - 1] / k;   // 1/k!
   const MatEpi none{0, 0, 0, 0, -1, -1, -1, 1.0};
   MatEpi sc = none;
-  sc.alpha = std::ldexp(1.0, -sq);
+  sc.alpha = ::ldexp(1.0, -sq);
   out[0] = {XS_X, XS_A, -1, sc};                          // X = A / 2^s
   out[1] = {XS_X2, XS_X, XS_X, none};
   out[2] = {XS_X3, XS_X2, XS_X, none};
@@ -180,9 +257,9 @@ inline void expm_products(int sq, ExpmProduct out[8]) {
 }
 
 // number of squarings for ||A||_1 (-1: too large to be finite)
-inline int expm_squarings(double norm1) {
+inline __host__ __device__ int expm_squarings(double norm1) {
   int sq = 0;
-  if (norm1 > kTaylorTheta) sq = (int)std::ceil(std::log2(norm1 / kTaylorTheta));
+  if (norm1 > kTaylorTheta) sq = (int)::ceil(::log2(norm1 / kTaylorTheta));
   return (sq > 200) ? -1 : sq;
 }
 // squaring q reads slot expm_square_src(q) and writes the other one

@@ -139,6 +139,9 @@ struct Ctx {
   int v32_cap = 0;                  // rows allocated in d_V32
   float* d_b32 = nullptr;           // FP32 copies of nu * b_l of the current phi-function call [MAX_NB][n]
   int b32_cap = 0;                  // vectors allocated in d_b32
+  // device-driven phi-function solver (kiops_graph.cu)
+  int kiops_driver = 0;           // 0: controller on the host (kiops.cu), 1: on the device, one CUDA graph per call
+  void* kg = nullptr;             // its graph, state and staging (owned, kiops_graph.cu)
   // KIOPS call log and learned control
   Mlp* controller = nullptr;      // not owned
   int epi_order = 0;              // EPI order of the current call (0: direct sw_kiops_phi)
@@ -300,6 +303,12 @@ int launch_lincomb(Ctx& c, double* out, long long n, int k, const double* const*
 int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, const double* const* b,
               const sw_kiops_opts& o, double* w, sw_kiops_stats* st, cudaStream_t s, bool use_lin);
 int ensure_krylov(Ctx& c, int m_max);
+// the device-driven solver (kiops_graph.cu): used by kiops_run when selected and
+// applicable (split JVP, window 2 or 3, plain rule, profiling off)
+bool kiops_graph_applies(const Ctx& c, const sw_kiops_opts& o, bool use_lin);
+int kiops_run_graph(Ctx& c, double dt, double tau_out, int nb, const double* const* b, const sw_kiops_opts& o,
+                    double* w, sw_kiops_stats* st, cudaStream_t s);
+void kiops_graph_free(Ctx& c);
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? SW_OK : SW_ECUDA; }
 

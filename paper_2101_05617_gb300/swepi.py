@@ -101,6 +101,7 @@ def lib():
     L.sw_linearize.argtypes = [vp, vp, vp]
     L.sw_jvp_linearized.argtypes = [vp, vp, vp, vp]
     L.sw_set_jvp_mode.argtypes = [vp, ip]
+    L.sw_set_kiops_driver.argtypes = [vp, ip]
     L.sw_kiops_phi.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, ip, ctypes.POINTER(vp),
                                ctypes.POINTER(sw_kiops_opts), vp, ctypes.POINTER(sw_kiops_stats), vp]
     L.sw_epi_step.argtypes = [vp, ip, ctypes.c_double, vp, ctypes.POINTER(sw_kiops_opts),
@@ -154,7 +155,7 @@ def lib():
 
 EXPORTED = ["sw_init", "sw_free", "sw_num_unknowns", "sw_grid_info", "sw_node_xyz", "sw_state_from_fields",
             "sw_set_bottom", "sw_set_bottom_host", "sw_rhs", "sw_jvp", "sw_jvp_static_scratch", "sw_linearize", "sw_jvp_linearized",
-            "sw_set_jvp_mode", "sw_kiops_phi", "sw_epi_step", "sw_epi_step_host", "sw_epi_set_history",
+            "sw_set_jvp_mode", "sw_set_kiops_driver", "sw_kiops_phi", "sw_epi_step", "sw_epi_step_host", "sw_epi_set_history",
             "sw_epi_reset", "sw_epi_coefficients", "sw_dfr_operators", "sw_node_coefficients",
             "sw_interface_transform", "sw_kernel_launches", "sw_profile", "sw_profile_kinds", "sw_profile_read", "sw_fp64_fma_peak",
             "sw_status_str", "sw_mlp_create", "sw_mlp_free", "sw_mlp_set_params", "sw_mlp_get_params",
@@ -277,6 +278,11 @@ def sw_jvp_linearized(ctx, v, Jv, stream=None):
 
 def sw_set_jvp_mode(ctx, mode):
     _check("sw_set_jvp_mode", lib().sw_set_jvp_mode(ctx, int(mode)))
+
+
+def sw_set_kiops_driver(ctx, driver):
+    """0: the phi-function solver's controller on the host; 1: on the device (one CUDA graph per call)."""
+    _check("sw_set_kiops_driver", lib().sw_set_kiops_driver(ctx, int(driver)))
 
 
 def sw_kiops_phi(ctx, q_lin, dt, tau_out, b, w, opts=None, stream=None):
@@ -665,6 +671,9 @@ class SWContext:
 
     def set_jvp_mode(self, mode):
         sw_set_jvp_mode(self.handle, mode)
+
+    def set_kiops_driver(self, driver):
+        sw_set_kiops_driver(self.handle, driver)
 
     def kiops_phi(self, q_lin, dt, b, tau_out=1.0, out=None, stream=None, **opts):
         import torch
