@@ -136,7 +136,7 @@ struct VolShape {
 
 template <int THREADS, bool W3>
 __device__ __forceinline__ void epilogue_finish(const AugEpilogue& ep, double da, double db, double dcc,
-                                                unsigned int blk, unsigned int nblk);
+                                                unsigned int blk, unsigned int nblk, double dab, double dbc);
 
 // Epilogue of the volume kernels (all threads of the block call it; blk/nblk:
 // this block's index and the number of blocks working on the same vector):
@@ -159,7 +159,8 @@ __device__ __forceinline__ void volume_epilogue(const AugEpilogue& ep, bool acti
     coef[l] = (l < ep.p && ep.b[l]) ? ep.nu * ep.tail_in[l] : 0.0;
   }
   __syncthreads();
-  double da = 0.0, db = 0.0, dcc = 0.0;
+  double da = 0.0, db = 0.0, dcc = 0.0, dab = 0.0, dbc = 0.0;
+  const bool cd = ep.cdot_out != nullptr;
   if (active) {
 #pragma unroll
     for (int mu = 0; mu < 3; ++mu) {
@@ -169,107 +170,128 @@ __device__ __forceinline__ void volume_epilogue(const AugEpilogue& ep, bool acti
         if (B64 && l < ep.p && ep.b[l]) o = fma(coef[l], ep.b[l][idx + mu * N], o);
       out[idx + mu * N] = o;
       if (ep.dotB) {
-        db = fma(o, ep.dotB[idx + mu * N], db);
-        if (ep.dotA) da = fma(o, ep.dotA[idx + mu * N], da);
-        if (W3 && ep.dotC) dcc = fma(o, ep.dotC[idx + mu * N], dcc);
+        const double vb = ep.dotB[idx + mu * N];
+        db = fma(o, vb, db);
+        if (ep.dotA) {
+          const double va = ep.dotA[idx + mu * N];
+          da = fma(o, va, da);
+          if (cd) dab = fma(vb, va, dab);
+        }
+        if (W3 && ep.dotC) {
+          const double vc = ep.dotC[idx + mu * N];
+          dcc = fma(o, vc, dcc);
+          if (cd) dbc = fma(vb, vc, dbc);
+        }
       }
     }
   }
-  epilogue_finish<THREADS, W3>(ep, da, db, dcc, blk, nblk);
+  epilogue_finish<THREADS, W3>(ep, da, db, dcc, blk, nblk, dab, dbc);
+}
+
+// Sum of v over the block in a fixed order (warp trees, then the warps in
+// order); the result is valid in thread 0.  THREADS need not be a multiple of
+// 32: the last warp's shuffles name only its existing lanes.
+template <int THREADS, int K>
+__device__ __forceinline__ void block_sums(double v[K], double (*ws)[32]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int cnt = (THREADS - 32 * w) < 32 ? (THREADS - 32 * w) : 32;
+  const unsigned mask = (cnt == 32) ? 0xffffffffu : ((1u << cnt) - 1u);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const double t = __shfl_down_sync(mask, v[k], o);
+      if (lane + o < cnt) v[k] += t;
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) ws[k][w] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    constexpr int NW = (THREADS + 31) / 32;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = 0.0;
+      for (int i = 0; i < NW; ++i) s += ws[k][i];
+      v[k] = s;
+    }
+  }
 }
 
 // Second half of the volume epilogue (all threads of the block call it, with
 // their partial window dots da = z . V_{j-1}, db = z . V_j, dcc = z . V_{j-2}
-// over their nodes): the shift of the augmented tail, the tail's share of the
-// dots, the block sums and -- in the last block to finish -- the modified
-// Gram-Schmidt coefficients.
+// over their nodes, and -- when ep.cdot_out is set -- dab = V_j . V_{j-1} and
+// dbc = V_j . V_{j-2}): the shift of the augmented tail, the tail's share of
+// the dots, the block sums and -- in the last block to finish -- the modified
+// Gram-Schmidt coefficients (with the V . V products of this launch when they
+// are formed here, else those stored by the scale pass).
 template <int THREADS, bool W3>
 __device__ __forceinline__ void epilogue_finish(const AugEpilogue& ep, double da, double db, double dcc,
-                                                unsigned int blk, unsigned int nblk) {
+                                                unsigned int blk, unsigned int nblk, double dab, double dbc) {
   if (ep.tail_out && blk == 0 && threadIdx.x < ep.p)
     ep.tail_out[threadIdx.x] = (threadIdx.x + 1 < ep.p) ? ep.tail_in[threadIdx.x + 1] : 0.0;
   if (!ep.dotB) return;   // uniform over the grid
+  const bool cd = ep.cdot_out != nullptr;   // uniform over the grid
   if (blk == 0 && threadIdx.x == 0) {
     for (int l = 0; l < ep.p; ++l) {
       const double zt = (l + 1 < ep.p) ? ep.tail_in[l + 1] : 0.0;
       db = fma(zt, ep.dotB[ep.n + l], db);
       if (ep.dotA) da = fma(zt, ep.dotA[ep.n + l], da);
       if (W3 && ep.dotC) dcc = fma(zt, ep.dotC[ep.n + l], dcc);
+      if (cd && ep.dotA) dab = fma(ep.tail_in[l], ep.dotA[ep.n + l], dab);
+      if (cd && W3 && ep.dotC) dbc = fma(ep.tail_in[l], ep.dotC[ep.n + l], dbc);
     }
   }
-  __shared__ double sa[THREADS], sb[THREADS], sc[W3 ? THREADS : 1];
+  constexpr int K = 5;
+  __shared__ double ws[K][32];
   __shared__ bool last;
-  const bool three = W3 && ep.dotC != nullptr;   // uniform over the grid
-  sa[threadIdx.x] = da;
-  sb[threadIdx.x] = db;
-  if (three) sc[threadIdx.x] = dcc;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double a = 0.0, b = 0.0, c3 = 0.0;
-    for (int k = threadIdx.x; k < THREADS; k += 32) {
-      a += sa[k];
-      b += sb[k];
-      if (three) c3 += sc[k];
-    }
+  double v[K] = {da, db, dcc, dab, dbc};
+  block_sums<THREADS, K>(v, ws);
+  if (threadIdx.x == 0) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_down_sync(0xffffffffu, a, o);
-      b += __shfl_down_sync(0xffffffffu, b, o);
-      if (three) c3 += __shfl_down_sync(0xffffffffu, c3, o);
-    }
-    if (threadIdx.x == 0) {
-      ep.dpart[3 * blk] = a;
-      ep.dpart[3 * blk + 1] = b;
-      ep.dpart[3 * blk + 2] = c3;
-      __threadfence();
-      const unsigned int t = atomicAdd(ep.dticket, 1u);
-      last = (t == nblk - 1);
-    }
+    for (int k = 0; k < K; ++k) ep.dpart[K * blk + k] = v[k];
+    __threadfence();
+    const unsigned int t = atomicAdd(ep.dticket, 1u);
+    last = (t == nblk - 1);
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
-  double a = 0.0, b = 0.0, c3 = 0.0;
+  double u[K] = {0.0, 0.0, 0.0, 0.0, 0.0};
   for (int k = threadIdx.x; k < (int)nblk; k += THREADS) {
-    a += __ldcg(ep.dpart + 3 * k);
-    b += __ldcg(ep.dpart + 3 * k + 1);
-    if (three) c3 += __ldcg(ep.dpart + 3 * k + 2);
-  }
-  sa[threadIdx.x] = a;
-  sb[threadIdx.x] = b;
-  if (three) sc[threadIdx.x] = c3;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    a = 0.0;
-    b = 0.0;
-    c3 = 0.0;
-    for (int k = threadIdx.x; k < THREADS; k += 32) {
-      a += sa[k];
-      b += sb[k];
-      if (three) c3 += sc[k];
-    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_down_sync(0xffffffffu, a, o);
-      b += __shfl_down_sync(0xffffffffu, b, o);
-      if (three) c3 += __shfl_down_sync(0xffffffffu, c3, o);
+    for (int i = 0; i < K; ++i) u[i] += __ldcg(ep.dpart + K * k + i);
+  }
+  __syncthreads();   // ws is reused
+  block_sums<THREADS, K>(u, ws);
+  if (threadIdx.x == 0) {
+    const double a = u[0], b = u[1], c3 = u[2];
+    const bool three = W3 && ep.dotC != nullptr;
+    double cprev = 0.0, cprevC = 0.0;
+    if (ep.dotA) {
+      cprev = cd ? u[3] : *ep.cprev;
+      if (cd) *ep.cdot_out = u[3];   // V_j . V_{j-1}
     }
-    if (threadIdx.x == 0) {
-      // modified Gram-Schmidt coefficients, oldest vector first
-      if (three) {
-        const double h0 = c3;                               // V_{j-2} . z
-        const double h1 = a - h0 * (*ep.cprevAC);            // V_{j-1} . (z - h0 V_{j-2})
-        *ep.h0_out = h0;
-        *ep.h1_out = h1;
-        *ep.h2_out = b - h0 * (*ep.cprevC) - h1 * (*ep.cprev);
-      } else if (ep.dotA) {
-        *ep.h1_out = a;
-        *ep.h2_out = b - a * (*ep.cprev);   // V_j . (z - h1 V_{j-1})
-      } else {
-        *ep.h2_out = b;
-      }
-      *ep.dticket = 0u;
+    if (three) {
+      cprevC = cd ? u[4] : *ep.cprevC;
+      if (cd) *ep.cdot2_out = u[4];   // V_j . V_{j-2}
     }
+    // modified Gram-Schmidt coefficients, oldest vector first
+    if (three) {
+      const double h0 = c3;                               // V_{j-2} . z
+      const double h1 = a - h0 * (*ep.cprevAC);            // V_{j-1} . (z - h0 V_{j-2})
+      *ep.h0_out = h0;
+      *ep.h1_out = h1;
+      *ep.h2_out = b - h0 * cprevC - h1 * cprev;
+    } else if (ep.dotA) {
+      *ep.h1_out = a;
+      *ep.h2_out = b - a * cprev;   // V_j . (z - h1 V_{j-1})
+    } else {
+      *ep.h2_out = b;
+    }
+    *ep.dticket = 0u;
   }
 }
 

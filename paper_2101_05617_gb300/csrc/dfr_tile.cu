@@ -194,7 +194,8 @@ __device__ __forceinline__ void tile_body(const TanVolArgs<float>& a, const DfrC
   const float sc = f64_to_f32_bits(ep.scale);
   const int t = threadIdx.x;
   const int le = t / NN, node = t % NN, k2 = node / NS, k1 = node % NS;
-  double da = 0.0, db = 0.0, dcc = 0.0;
+  double da = 0.0, db = 0.0, dcc = 0.0, dab = 0.0, dbc = 0.0;
+  const bool cd = ep.cdot_out != nullptr;
   bool ok = true;
   int k = 0;
   for (long long tile = blockIdx.x; tile < ntiles; tile += G, ++k) {
@@ -269,9 +270,18 @@ __device__ __forceinline__ void tile_body(const TanVolArgs<float>& a, const DfrC
         const double o = f32_to_f64_bits(acc);
         a.out[idx + mu * N] = o;
         if (dB) {
-          db = fma(o, sdot[(2 * 3 + mu) * TN + t], db);
-          if (dA) da = fma(o, sdot[(1 * 3 + mu) * TN + t], da);
-          if (dC) dcc = fma(o, sdot[(0 * 3 + mu) * TN + t], dcc);
+          const double vb = sdot[(2 * 3 + mu) * TN + t];
+          db = fma(o, vb, db);
+          if (dA) {
+            const double va = sdot[(1 * 3 + mu) * TN + t];
+            da = fma(o, va, da);
+            if (cd) dab = fma(vb, va, dab);
+          }
+          if (dC) {
+            const double vc = sdot[(0 * 3 + mu) * TN + t];
+            dcc = fma(o, vc, dcc);
+            if (cd) dbc = fma(vb, vc, dbc);
+          }
         }
       }
     }
@@ -279,8 +289,8 @@ __device__ __forceinline__ void tile_body(const TanVolArgs<float>& a, const DfrC
     if (threadIdx.x == 0 && tile + 2 * G < ntiles) issue_tile<NS, W3>(a, tile + 2 * G, st, mbar + s);
   }
   // a CTA that gave up contributes zeros; the reduction protocol still completes
-  if (!ok) da = db = dcc = 0.0;
-  epilogue_finish<TN, W3>(ep, da, db, dcc, blockIdx.x, gridDim.x);
+  if (!ok) da = db = dcc = dab = dbc = 0.0;
+  epilogue_finish<TN, W3>(ep, da, db, dcc, blockIdx.x, gridDim.x, dab, dbc);
 }
 
 template <int NS, bool W3>

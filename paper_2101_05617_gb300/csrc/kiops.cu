@@ -73,7 +73,7 @@ int ensure_krylov(Ctx& c, int m_max) {
   if (cudaMalloc(&c.d_F, sizeof(double) * c.ldh * c.ldh) != cudaSuccess) return SW_ENOMEM;
   if (cudaMalloc(&c.d_expm_ws, sizeof(double) * 8 * 160 * 160) != cudaSuccess) return SW_ENOMEM;
   if (!c.d_partials && cudaMalloc(&c.d_partials, sizeof(double) * 2 * RED_BLOCKS) != cudaSuccess) return SW_ENOMEM;
-  if (!c.d_vpart && cudaMalloc(&c.d_vpart, sizeof(double) * 3 * (c.nelem + 1)) != cudaSuccess) return SW_ENOMEM;
+  if (!c.d_vpart && cudaMalloc(&c.d_vpart, sizeof(double) * 5 * (c.nelem + 1)) != cudaSuccess) return SW_ENOMEM;
   free_ptr(c.d_cdot);
   if (cudaMalloc(&c.d_cdot, sizeof(double) * c.ldh) != cudaSuccess) return SW_ENOMEM;
   free_ptr(c.d_cdot2);
@@ -227,19 +227,24 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
         ep.dticket = (unsigned int*)(c.d_flags + 9);
         ep.n = n;
         ep.v32 = use32 ? c.d_V32 + it * ldv : nullptr;
+        // complex64-bulk form: V_j . V_{j-1} (and V_j . V_{j-2}) from the window
+        // vectors the volume kernel reads anyway; the scale pass forms no dots
+        ep.cdot_out = (use32 && it >= 1) ? c.d_cdot + it : nullptr;
+        ep.cdot2_out = (use32 && o.iop == 3 && it >= 2) ? c.d_cdot2 + it : nullptr;
         rc = use_lin ? launch_jvp_lin(c, Vi, Vn, ep, s, c.jvp_mode == 2) : launch_jvp(c, q_lin, Vi, kEpsJvp, Vn, ep, s);
         if (rc) return rc;
         double* hs = c.d_H + (long long)(it + 1) * c.ldh + it;
         if ((rc = launch_update_norm(c, Vn, ep.dotA, Vi, hA, hB, N, hs, o.tol, it + 1, s, ep.dotC, hC))) return rc;
         // V_{j+1} . V_{j-1} is needed by the window of three two iterations later
         const double* Vprev = (o.iop == 3 && it >= 1) ? V + (it - 1) * ldv : nullptr;
-        if ((rc = launch_scale_dot(c, Vn, Vi, hs, N, c.d_cdot + it + 1, s, Vprev, c.d_cdot2 + it + 1,
-                                   use32 ? c.d_V32 + (it + 1) * ldv : nullptr)))
+        if ((rc = launch_scale_dot(c, Vn, Vi, hs, N, use32 ? nullptr : c.d_cdot + it + 1, s, Vprev,
+                                   c.d_cdot2 + it + 1, use32 ? c.d_V32 + (it + 1) * ldv : nullptr)))
           return rc;
         continue;
       }
       ep.dotA = ep.dotB = ep.dotC = nullptr;
       ep.v32 = nullptr;
+      ep.cdot_out = ep.cdot2_out = nullptr;
       rc = use_lin ? launch_jvp_lin(c, Vi, Vn, ep, s, c.jvp_mode == 2) : launch_jvp(c, q_lin, Vi, kEpsJvp, Vn, ep, s);
       if (rc) return rc;
       for (int i = std::max(0, it - o.iop + 1); i <= it; ++i) {

@@ -76,6 +76,8 @@ __device__ __forceinline__ void iter_epilogue_dev(AugEpilogue& ep, const KDev& k
   ep.dticket = reinterpret_cast<unsigned int*>(f.flags + 9);
   ep.n = f.n;
   ep.v32 = (fp32 && f.V32) ? f.V32 + (long long)it * f.ldv : nullptr;
+  ep.cdot_out = (fp32 && f.V32 && it >= 1) ? f.cdot + it : nullptr;
+  ep.cdot2_out = (fp32 && f.V32 && w3 && it >= 2) ? f.cdot2 + it : nullptr;
 }
 #endif
 

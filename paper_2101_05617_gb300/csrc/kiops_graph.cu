@@ -153,8 +153,9 @@ __global__ void __launch_bounds__(kRedThreads) kg_scale_kernel(const KDev* __res
   const double* hs = f.H + (long long)(it + 1) * f.ldh + it;
   const double* Vprev = (W3 && it >= 1) ? Vi - f.ldv : nullptr;
   float* z32 = f.V32 ? f.V32 + (long long)(it + 1) * f.ldv : nullptr;
-  scale_dot_dev(Vn, Vi, hs, f.N, f.partials, reinterpret_cast<unsigned int*>(f.flags + 8), f.cdot + it + 1, f.flags,
-                Vprev, f.cdot2 + it + 1, z32);
+  // complex64-bulk form (FP32 basis copy): the next volume kernel forms the V . V dots
+  scale_dot_dev(Vn, Vi, hs, f.N, f.partials, reinterpret_cast<unsigned int*>(f.flags + 8),
+                f.V32 ? nullptr : f.cdot + it + 1, f.flags, Vprev, f.cdot2 + it + 1, z32);
 }
 
 __global__ void kg_advance_kernel(KDev* kd, KFix f, cudaGraphConditionalHandle hi) {

@@ -182,6 +182,15 @@ __device__ __forceinline__ void scale_dot_dev(double* __restrict__ z, const doub
                                               double* c2_out, float* __restrict__ z32) {
   if (happy[0]) return;
   const double r = 1.0 / *hsub;
+  if (!c_out) {   // scale only (the next volume kernel forms the dots)
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+      const double v = __ldcg(z + i) * r;
+      z[i] = v;
+      if (z32) z32[i] = f64_to_f32_bits(v);
+    }
+    return;
+  }
   double acc2 = 0.0;
   const double acc = scale_dot_range(z, VB, r, (long long)blockIdx.x * blockDim.x + threadIdx.x, n,
                                      (long long)gridDim.x * blockDim.x, VA, &acc2, z32);

@@ -243,7 +243,13 @@ struct AugEpilogue {
   double* h0_out = nullptr;
   double* h1_out = nullptr;
   double* h2_out = nullptr;
-  double* dpart = nullptr;          // 3 doubles per block
+  // with cdot_out set, V_j . V_{j-1} (and, window of three, V_j . V_{j-2}) are
+  // formed here from the window vectors and written there, instead of being
+  // read from cprev / cprevC (complex64-bulk form: the scale pass then forms
+  // no dots)
+  double* cdot_out = nullptr;
+  double* cdot2_out = nullptr;
+  double* dpart = nullptr;          // 5 doubles per block
   unsigned int* dticket = nullptr;
   long long n = 0;
 };
@@ -265,7 +271,7 @@ int launch_jvp_fb(Ctx& c, const double* q, const double* v, double eps, double* 
                   cudaStream_t s);
 
 // ---- Krylov kernels (krylov.cu)
-constexpr int RED_BLOCKS = 608;   // 4 x 152 SMs
+constexpr int RED_BLOCKS = 760;   // 5 x 152 SMs: all resident at the passes' 48 registers per thread
 int launch_dot(Ctx& c, const double* x, const double* y, long long n, double* dst, const int* skip,
                cudaStream_t s);
 int launch_norm2(Ctx& c, const double* x, long long n, double* dst, double tol, int* happy,
