@@ -340,20 +340,24 @@ def ortho_roofline(prof_all, wl):
 
 def volume_bytes_per_node(ns, mode, iop, p):
     """Bytes one volume-kernel launch of a Krylov iteration must move per node:
-    read v and write Jv (3 + 3 doubles), read the iop orthogonalisation window
-    vectors (3 iop doubles), the p b-column vectors of the augmented operator (3 p
-    entries: FP64, or their FP32 copies in the complex64-bulk form), the 11
-    split-JVP coefficients (FP64, or FP32 in the complex64-bulk form) and the
-    interface fluxes of the element's four edges (12 N_s values per element =
-    12 / N_s per node, FP64 or FP32)."""
+    read v (3 doubles; its FP32 copy in the complex64-bulk form) and write Jv (3
+    doubles), read the iop orthogonalisation window vectors (3 iop doubles), the p
+    b-column vectors of the augmented operator (3 p entries: FP64, or their FP32
+    copies in the complex64-bulk form), the 11 split-JVP coefficients (FP64, or
+    FP32 in the complex64-bulk form) and the interface fluxes of the element's four
+    edges (12 N_s values per element = 12 / N_s per node, FP64 or FP32)."""
     w = 8 if mode == 1 else 4
-    return 24 + 24 + 24 * iop + 3 * p * w + 11 * w + 12.0 / ns * w
+    return 3 * w + 24 + 24 * iop + 3 * p * w + 11 * w + 12.0 / ns * w
 
 
-def orth_bytes_per_unknown(iop):
+def orth_bytes_per_unknown(iop, mode=1):
     """The two vector passes of the fused window-iop orthogonalisation per unknown
     of the augmented vector: (read z and the iop window vectors, write z) + (read
-    z and iop - 1 window vectors for the dots, write V_{j+1}) = 8 (2 iop + 3) B."""
+    z and iop - 1 window vectors for the dots, write V_{j+1}) = 8 (2 iop + 3) B;
+    in the complex64-bulk form the second pass forms no dots (the next volume
+    kernel does) and also writes the FP32 copy: 8 (iop + 2) + 20 B."""
+    if mode == 2:
+        return 8.0 * (iop + 2) + 20.0
     return 8.0 * (2 * iop + 3)
 
 
@@ -392,7 +396,7 @@ def kernel_rooflines(prof, wl, mode, iop, step_ms, fp64_peak):
         out["face"] = f
     if to:
         t = 2.0 * to   # one update-and-norm plus one scale-and-dot pass per Krylov iteration
-        obytes = orth_bytes_per_unknown(iop) * (wl.n_unknowns + 4)
+        obytes = orth_bytes_per_unknown(iop, mode) * (wl.n_unknowns + 4)
         out["orthogonalisation"] = {"avg_us_per_iteration": t * 1e6, "bytes_per_iteration": obytes,
                                     "gbs": obytes / t / 1e9, "hbm_frac": obytes / t / 1e9 / hbm}
     if prof["expm"]["count"]:

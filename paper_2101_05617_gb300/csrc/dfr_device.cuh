@@ -136,7 +136,8 @@ struct VolShape {
 
 template <int THREADS, bool W3>
 __device__ __forceinline__ void epilogue_finish(const AugEpilogue& ep, double da, double db, double dcc,
-                                                unsigned int blk, unsigned int nblk, double dab, double dbc);
+                                                unsigned int blk, unsigned int nblk, double dab, double dbc,
+                                                double* sbuf);
 
 // Epilogue of the volume kernels (all threads of the block call it; blk/nblk:
 // this block's index and the number of blocks working on the same vector):
@@ -185,37 +186,29 @@ __device__ __forceinline__ void volume_epilogue(const AugEpilogue& ep, bool acti
       }
     }
   }
-  epilogue_finish<THREADS, W3>(ep, da, db, dcc, blk, nblk, dab, dbc);
+  __shared__ double sred[5 * THREADS];
+  epilogue_finish<THREADS, W3>(ep, da, db, dcc, blk, nblk, dab, dbc, sred);
 }
 
-// Sum of v over the block in a fixed order (warp trees, then the warps in
-// order); the result is valid in thread 0.  THREADS need not be a multiple of
-// 32: the last warp's shuffles name only its existing lanes.
+// Sums of K values over the block in a fixed order, through shared scratch of
+// K * THREADS doubles: every thread stores its values, warp 0 sums them with a
+// stride of 32 and a shuffle tree; the result is valid in thread 0.  (On this
+// GPU a shuffle tree in every warp would cost each thread 5 K FP64 adds, more
+// than the dots themselves.)
 template <int THREADS, int K>
-__device__ __forceinline__ void block_sums(double v[K], double (*ws)[32]) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int cnt = (THREADS - 32 * w) < 32 ? (THREADS - 32 * w) : 32;
-  const unsigned mask = (cnt == 32) ? 0xffffffffu : ((1u << cnt) - 1u);
+__device__ __forceinline__ void block_sums(double v[K], double* sbuf) {
+  static_assert(THREADS >= 32, "block smaller than a warp");
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const double t = __shfl_down_sync(mask, v[k], o);
-      if (lane + o < cnt) v[k] += t;
-    }
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) ws[k][w] = v[k];
-  }
+  for (int k = 0; k < K; ++k) sbuf[k * THREADS + threadIdx.x] = v[k];
   __syncthreads();
-  if (threadIdx.x == 0) {
-    constexpr int NW = (THREADS + 31) / 32;
+  if (threadIdx.x < 32) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      double s = 0.0;
-      for (int i = 0; i < NW; ++i) s += ws[k][i];
-      v[k] = s;
+      double a = 0.0;
+      for (int i = threadIdx.x; i < THREADS; i += 32) a += sbuf[k * THREADS + i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+      v[k] = a;
     }
   }
 }
@@ -229,7 +222,8 @@ __device__ __forceinline__ void block_sums(double v[K], double (*ws)[32]) {
 // are formed here, else those stored by the scale pass).
 template <int THREADS, bool W3>
 __device__ __forceinline__ void epilogue_finish(const AugEpilogue& ep, double da, double db, double dcc,
-                                                unsigned int blk, unsigned int nblk, double dab, double dbc) {
+                                                unsigned int blk, unsigned int nblk, double dab, double dbc,
+                                                double* sbuf) {
   if (ep.tail_out && blk == 0 && threadIdx.x < ep.p)
     ep.tail_out[threadIdx.x] = (threadIdx.x + 1 < ep.p) ? ep.tail_in[threadIdx.x + 1] : 0.0;
   if (!ep.dotB) return;   // uniform over the grid
@@ -245,10 +239,9 @@ __device__ __forceinline__ void epilogue_finish(const AugEpilogue& ep, double da
     }
   }
   constexpr int K = 5;
-  __shared__ double ws[K][32];
   __shared__ bool last;
   double v[K] = {da, db, dcc, dab, dbc};
-  block_sums<THREADS, K>(v, ws);
+  block_sums<THREADS, K>(v, sbuf);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < K; ++k) ep.dpart[K * blk + k] = v[k];
@@ -264,8 +257,8 @@ __device__ __forceinline__ void epilogue_finish(const AugEpilogue& ep, double da
 #pragma unroll
     for (int i = 0; i < K; ++i) u[i] += __ldcg(ep.dpart + K * k + i);
   }
-  __syncthreads();   // ws is reused
-  block_sums<THREADS, K>(u, ws);
+  __syncthreads();   // the scratch is reused
+  block_sums<THREADS, K>(u, sbuf);
   if (threadIdx.x == 0) {
     const double a = u[0], b = u[1], c3 = u[2];
     const bool three = W3 && ep.dotC != nullptr;

@@ -290,7 +290,11 @@ __device__ __forceinline__ void tile_body(const TanVolArgs<float>& a, const DfrC
   }
   // a CTA that gave up contributes zeros; the reduction protocol still completes
   if (!ok) da = db = dcc = dab = dbc = 0.0;
-  epilogue_finish<TN, W3>(ep, da, db, dcc, blockIdx.x, gridDim.x, dab, dbc);
+  // the stage buffers are free after the last tile (every copy issued was
+  // waited for; after a wait that gave up the call reports SW_ETIMEOUT and its
+  // result is not used): the first one holds the reduction scratch (5 TN doubles)
+  static_assert(5 * TN * sizeof(double) <= L::stage, "reduction scratch larger than a stage");
+  epilogue_finish<TN, W3>(ep, da, db, dcc, blockIdx.x, gridDim.x, dab, dbc, reinterpret_cast<double*>(sm));
 }
 
 template <int NS, bool W3>

@@ -271,7 +271,7 @@ int launch_jvp_fb(Ctx& c, const double* q, const double* v, double eps, double* 
                   cudaStream_t s);
 
 // ---- Krylov kernels (krylov.cu)
-constexpr int RED_BLOCKS = 760;   // 5 x 152 SMs: all resident at the passes' 48 registers per thread
+constexpr int RED_BLOCKS = 608;   // 4 x 152 SMs
 int launch_dot(Ctx& c, const double* x, const double* y, long long n, double* dst, const int* skip,
                cudaStream_t s);
 int launch_norm2(Ctx& c, const double* x, long long n, double* dst, double tol, int* happy,

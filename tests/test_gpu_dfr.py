@@ -15,9 +15,12 @@ pytestmark = pytest.mark.gpu
 # a bound relative to the result itself would measure cancellation, not the
 # kernel.  Each output sums 2 N_s + 4 terms, each the result of ~30 rounded
 # operations (traces, the AUSM flux, the App. C transforms): ~500 u = 1e-13 of
-# the term scale bounds any evaluation order.
-TOL_RHS = 1e-13
-TOL_JVP = 1e-13
+# the term scale bounds any evaluation order.  The errors reached on the GB300
+# over every case below are at most 8.3e-15 (RHS) and 3.5e-14 (JVP, the split
+# and the full evaluation, at eps 1e-30 and 1.5e-8); the bounds sit a factor
+# 2-4 above them.
+TOL_RHS = 3e-14
+TOL_JVP = 8e-14
 
 CASES = [(4, 4, 0, 0.0), (3, 6, 1, 0.0), (2, 8, 2, 0.0), (5, 3, 3, 1500.0), (1, 2, 4, 0.0), (6, 7, 5, 800.0)]
 
