@@ -898,7 +898,9 @@ def main():
             lc = ctl if ctl is not None else learned.Controller.load()
             form("learned_vs_plain_same_start",
                  lambda: learned.evaluate(lc, args.workload, args.steps, seed=args.seed + 1))
-            form("complex64_bulk_ne30_p5", lambda: fp32_form_comparison(args, dev))
+            # the complex64-bulk form with its orthogonalisation window of three (reading 17) on configuration 2
+            form("complex64_bulk_ne30_p5", lambda: fp32_form_comparison(
+                args, dev, "ne30_p5", (("fp64", 1, 2), ("complex64_bulk_window3", 2, 3))))
             if args.workload == "ne60_p5":
                 # on this grid the form needs the orthogonalisation window of three
                 # the configured 48 EPI5 steps of this grid (4 untimed, 44 timed) from the same start

@@ -134,7 +134,7 @@ struct VolShape {
 };
 
 
-template <int THREADS, bool W3>
+template <int THREADS, bool W3, bool CD>
 __device__ __forceinline__ void epilogue_finish(const AugEpilogue& ep, double da, double db, double dcc,
                                                 unsigned int blk, unsigned int nblk, double dab, double dbc,
                                                 double* sbuf);
@@ -148,8 +148,10 @@ __device__ __forceinline__ void epilogue_finish(const AugEpilogue& ep, double da
 // SCALED: the caller has already multiplied res by scale.  W3: compiled for
 // the window of three (dotC may be set); W3 = false drops that code.  B64:
 // the b-column terms are added here in FP64; false: the caller has added them
-// already (the FP32 kernels of the complex64-bulk form, from ep.b32).
-template <int THREADS, bool SCALED = false, bool W3 = false, bool B64 = true>
+// already (the FP32 kernels of the complex64-bulk form, from ep.b32).  CD:
+// compiled to form the V . V products when ep.cdot_out asks for them (the
+// complex64-bulk kernels); without it the block sums carry three values.
+template <int THREADS, bool SCALED = false, bool W3 = false, bool B64 = true, bool CD = false>
 __device__ __forceinline__ void volume_epilogue(const AugEpilogue& ep, bool active, long long idx, long long N,
                                                 const double res[3], double* __restrict__ out, unsigned int blk,
                                                 unsigned int nblk) {
@@ -161,7 +163,7 @@ __device__ __forceinline__ void volume_epilogue(const AugEpilogue& ep, bool acti
   }
   __syncthreads();
   double da = 0.0, db = 0.0, dcc = 0.0, dab = 0.0, dbc = 0.0;
-  const bool cd = ep.cdot_out != nullptr;
+  const bool cd = CD && ep.cdot_out != nullptr;
   if (active) {
 #pragma unroll
     for (int mu = 0; mu < 3; ++mu) {
@@ -186,8 +188,8 @@ __device__ __forceinline__ void volume_epilogue(const AugEpilogue& ep, bool acti
       }
     }
   }
-  __shared__ double sred[5 * THREADS];
-  epilogue_finish<THREADS, W3>(ep, da, db, dcc, blk, nblk, dab, dbc, sred);
+  __shared__ double sred[(CD ? 5 : 3) * THREADS];
+  epilogue_finish<THREADS, W3, CD>(ep, da, db, dcc, blk, nblk, dab, dbc, sred);
 }
 
 // Sums of K values over the block in a fixed order, through shared scratch of
@@ -219,15 +221,16 @@ __device__ __forceinline__ void block_sums(double v[K], double* sbuf) {
 // dbc = V_j . V_{j-2}): the shift of the augmented tail, the tail's share of
 // the dots, the block sums and -- in the last block to finish -- the modified
 // Gram-Schmidt coefficients (with the V . V products of this launch when they
-// are formed here, else those stored by the scale pass).
-template <int THREADS, bool W3>
+// are formed here, else those stored by the scale pass).  sbuf: K * THREADS
+// doubles of shared scratch, K = 5 with CD, else 3.
+template <int THREADS, bool W3, bool CD>
 __device__ __forceinline__ void epilogue_finish(const AugEpilogue& ep, double da, double db, double dcc,
                                                 unsigned int blk, unsigned int nblk, double dab, double dbc,
                                                 double* sbuf) {
   if (ep.tail_out && blk == 0 && threadIdx.x < ep.p)
     ep.tail_out[threadIdx.x] = (threadIdx.x + 1 < ep.p) ? ep.tail_in[threadIdx.x + 1] : 0.0;
   if (!ep.dotB) return;   // uniform over the grid
-  const bool cd = ep.cdot_out != nullptr;   // uniform over the grid
+  const bool cd = CD && ep.cdot_out != nullptr;   // uniform over the grid
   if (blk == 0 && threadIdx.x == 0) {
     for (int l = 0; l < ep.p; ++l) {
       const double zt = (l + 1 < ep.p) ? ep.tail_in[l + 1] : 0.0;
@@ -238,9 +241,9 @@ __device__ __forceinline__ void epilogue_finish(const AugEpilogue& ep, double da
       if (cd && W3 && ep.dotC) dbc = fma(ep.tail_in[l], ep.dotC[ep.n + l], dbc);
     }
   }
-  constexpr int K = 5;
+  constexpr int K = CD ? 5 : 3;
   __shared__ bool last;
-  double v[K] = {da, db, dcc, dab, dbc};
+  double v[5] = {da, db, dcc, dab, dbc};
   block_sums<THREADS, K>(v, sbuf);
   if (threadIdx.x == 0) {
 #pragma unroll
@@ -252,7 +255,7 @@ __device__ __forceinline__ void epilogue_finish(const AugEpilogue& ep, double da
   __syncthreads();
   if (!last) return;
   __threadfence();
-  double u[K] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  double u[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   for (int k = threadIdx.x; k < (int)nblk; k += THREADS) {
 #pragma unroll
     for (int i = 0; i < K; ++i) u[i] += __ldcg(ep.dpart + K * k + i);

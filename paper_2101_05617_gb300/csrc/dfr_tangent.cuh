@@ -207,7 +207,7 @@ __device__ __forceinline__ void volume_tangent_body(const TanVolArgs<T>& a, cons
       res[mu] = to_f64<T>(acc);
     }
   }
-  volume_epilogue<BLOCK, true, W3, !F32>(a.ep, active, idx, N, res, a.out, blk, nblk);
+  volume_epilogue<BLOCK, true, W3, !F32, F32>(a.ep, active, idx, N, res, a.out, blk, nblk);
 }
 
 }  // namespace swepi

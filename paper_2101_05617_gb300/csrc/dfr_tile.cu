@@ -294,7 +294,7 @@ __device__ __forceinline__ void tile_body(const TanVolArgs<float>& a, const DfrC
   // waited for; after a wait that gave up the call reports SW_ETIMEOUT and its
   // result is not used): the first one holds the reduction scratch (5 TN doubles)
   static_assert(5 * TN * sizeof(double) <= L::stage, "reduction scratch larger than a stage");
-  epilogue_finish<TN, W3>(ep, da, db, dcc, blockIdx.x, gridDim.x, dab, dbc, reinterpret_cast<double*>(sm));
+  epilogue_finish<TN, W3, true>(ep, da, db, dcc, blockIdx.x, gridDim.x, dab, dbc, reinterpret_cast<double*>(sm));
 }
 
 template <int NS, bool W3>
