@@ -48,9 +48,10 @@ def flops_per_jvp(ne, ns, p=4, dots=True):
 
 # DRAM bytes (read + write) of one launch of the dominant kernel,
 # volume_tangent_kernel<double, 6>, on the 6 x 60 x 60, p = 5 workload inside
-# the phi-function solver (p = 4, with dots): mean of two launches of one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum = 136.96 MB + 8.35 MB).
-TRAFFIC_BYTES = {"ne60_p5": 145.31e6}
+# the phi-function solver (p = 4, with dots), from one ncu capture of the
+# kernel as it stands (dram__bytes_read.sum + dram__bytes_write.sum); none
+# while the kernel has changed since its last capture.
+TRAFFIC_BYTES = {}
 
 
 def parse():
@@ -322,16 +323,16 @@ def hbm_peak_gbs():
         return 6800.0, "fallback"
 
 
-def ortho_roofline(prof_all, wl):
+def ortho_roofline(prof_all, wl, fused=False):
     """The two vector passes of the window-2 orthogonalisation against HBM:
-    algorithmic bytes per Krylov iteration = (read z, V_{j-1}, V_j, write z) +
-    (read z, V_j, write z) = 56 B per unknown of the augmented vector."""
+    algorithmic bytes per Krylov iteration (orth_bytes_per_unknown) per unknown
+    of the augmented vector; the fused launch counts as the two passes."""
     o = prof_all["orthogonalisation"]
     if not o["count"]:
         return None
     pairs = o["count"] / 2.0
     t = o["ms"] * 1e-3 / pairs
-    nbytes = 56.0 * (wl.n_unknowns + 4)
+    nbytes = orth_bytes_per_unknown(2, 1, fused) * (wl.n_unknowns + 4)
     peak, src = hbm_peak_gbs()
     return {"bound": "hbm", "bytes_per_iteration": nbytes, "avg_ms_per_iteration": t * 1e3,
             "achieved_gbs": nbytes / t / 1e9, "peak_gbs": peak, "frac": nbytes / t / 1e9 / peak,
@@ -350,18 +351,22 @@ def volume_bytes_per_node(ns, mode, iop, p):
     return 3 * w + 24 + 24 * iop + 3 * p * w + 11 * w + 12.0 / ns * w
 
 
-def orth_bytes_per_unknown(iop, mode=1):
+def orth_bytes_per_unknown(iop, mode=1, fused=False):
     """The two vector passes of the fused window-iop orthogonalisation per unknown
     of the augmented vector: (read z and the iop window vectors, write z) + (read
     z and iop - 1 window vectors for the dots, write V_{j+1}) = 8 (2 iop + 3) B;
     in the complex64-bulk form the second pass forms no dots (the next volume
-    kernel does) and also writes the FP32 copy: 8 (iop + 2) + 20 B."""
+    kernel does) and also writes the FP32 copy: 8 (iop + 2) + 20 B.  Both passes
+    in one launch (fused): each vector once, read z and the window vectors, write
+    V_{j+1} = 8 (iop + 2) B, with the FP32 copy 8 (iop + 2) + 4 B."""
+    if fused:
+        return 8.0 * (iop + 2) + (4.0 if mode == 2 else 0.0)
     if mode == 2:
         return 8.0 * (iop + 2) + 20.0
     return 8.0 * (2 * iop + 3)
 
 
-def kernel_rooflines(prof, wl, mode, iop, step_ms, fp64_peak):
+def kernel_rooflines(prof, wl, mode, iop, step_ms, fp64_peak, fused=False):
     """Per-kernel figures of one EPI step with every kernel family bracketed by
     events.  FP64 kernels: algorithmic flops (flops_per_jvp, 6 more per node for
     the third dot of window 3) against the measured FP64 peak.  HBM: the
@@ -396,7 +401,7 @@ def kernel_rooflines(prof, wl, mode, iop, step_ms, fp64_peak):
         out["face"] = f
     if to:
         t = 2.0 * to   # one update-and-norm plus one scale-and-dot pass per Krylov iteration
-        obytes = orth_bytes_per_unknown(iop, mode) * (wl.n_unknowns + 4)
+        obytes = orth_bytes_per_unknown(iop, mode, fused) * (wl.n_unknowns + 4)
         out["orthogonalisation"] = {"avg_us_per_iteration": t * 1e6, "bytes_per_iteration": obytes,
                                     "gbs": obytes / t / 1e9, "hbm_frac": obytes / t / 1e9 / hbm}
     if prof["expm"]["count"]:
@@ -441,6 +446,8 @@ def fp32_form_comparison(args, dev, workload="ne30_p5", variants=(("fp64", 1, 2)
         ctx.set_jvp_mode(mode)
         if extra == "device":   # the phi-function solver's controller on the device (one CUDA graph per call)
             ctx.set_kiops_driver(1)
+        # both vector passes in one launch (the host controller; the device graph keeps two)
+        fused = bool(ctx.set_orth_fused(1)) and extra != "device"
         try:
             for _ in range(warm * mult):
                 ctx.epi_step(wl.order, dt, q, tol=wl.tol, iop=iop)
@@ -469,7 +476,7 @@ def fp32_form_comparison(args, dev, workload="ne30_p5", variants=(("fp64", 1, 2)
                     b1.record()
                     torch.cuda.synchronize()
                     kernels[name] = kernel_rooflines(ctx.profile_read(), wl, mode, iop, b0.elapsed_time(b1),
-                                                     fp64_peak)
+                                                     fp64_peak, fused)
                 except Exception as e:
                     kernels[name] = {"error": f"{type(e).__name__}: {e}"[:200]}
                 ctx.profile(False)
@@ -794,6 +801,7 @@ def main():
     # by events (outside both timed regions).
     ctx = swepi.SWContext(wl.ne, wl.p, f.rotation)
     ctx.set_jvp_mode(args.jvp_mode)
+    fused_main = bool(ctx.set_orth_fused(1))
     q = torch.tensor(q_host, device=dev)
     for k in range(args.warmup):
         if k == args.warmup - 1:
@@ -849,7 +857,7 @@ def main():
                                             "tflops": ff / t_face / 1e12 if t_face else None},
                                    "expm": {"avg_ms": prof_all["expm"]["ms"] / max(1, prof_all["expm"]["count"]),
                                             "launches": prof_all["expm"]["count"]},
-                                   "orthogonalisation": ortho_roofline(prof_all, wl)},
+                                   "orthogonalisation": ortho_roofline(prof_all, wl, fused_main)},
                     "share_of_step": {k: prof_all[k]["ms"] / breakdown_ms
                                       for k in ("volume_jvp", "face_jvp", "orthogonalisation", "expm", "linearize")},
                     "share_note": "the last warm-up EPI step of the end-to-end replay with every kernel family "

@@ -199,6 +199,17 @@ int sw_set_jvp_mode(sw_ctx_t ctx, int mode);
  * Krylov workspace changes. */
 int sw_set_kiops_driver(sw_ctx_t ctx, int driver);
 
+/* The two vector passes of the fused incomplete orthogonalisation (the
+ * modified Gram-Schmidt updates with ||z||, then the scaling with the next
+ * window dot; the KIOPS reading of Eq. 29's Krylov projection) in one launch:
+ * enable = 1 (default) runs them as one cooperative launch whose CTAs wait on
+ * one another for ||z|| (a bounded wait: SW_ETIMEOUT past about a second),
+ * where the GPU holds the whole grid at once; 0 = two launches.  The results
+ * are the same bit for bit.  Applies to the host controller; the device
+ * controller's graph keeps two launches.  *active_out (may be NULL) = 1 when
+ * the next phi-function call will fuse them. */
+int sw_set_orth_fused(sw_ctx_t ctx, int enable, int* active_out);
+
 /* w = sum_{k=0}^{nb-1} tau_out^k phi_k(tau_out dt J(q_lin)) b_k (Eq. 29), J by
  * the complex-step product above.  b_dev_host: host array of nb device
  * pointers (1 <= nb <= 8); a NULL entry means a zero vector.  w_dev: n

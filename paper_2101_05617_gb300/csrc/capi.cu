@@ -608,6 +608,14 @@ int sw_set_kiops_driver(sw_ctx_t c, int driver) {
   return SW_OK;
 }
 
+int sw_set_orth_fused(sw_ctx_t c, int enable, int* active_out) {
+  if (!c || enable < 0 || enable > 1) return SW_EINVAL;
+  if (int rc = check_device(*c)) return rc;
+  c->orth_fuse_enable = enable;
+  if (active_out) *active_out = (enable && swepi::orth_fused_available(*c)) ? 1 : 0;
+  return SW_OK;
+}
+
 int sw_set_jvp_mode(sw_ctx_t c, int mode) {
   if (!c || mode < 0 || mode > 2) return SW_EINVAL;
   if (mode != c->jvp_mode) c->linearized = false;

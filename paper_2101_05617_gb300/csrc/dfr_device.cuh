@@ -151,42 +151,72 @@ __device__ __forceinline__ void epilogue_finish(const AugEpilogue& ep, double da
 // already (the FP32 kernels of the complex64-bulk form, from ep.b32).  CD:
 // compiled to form the V . V products when ep.cdot_out asks for them (the
 // complex64-bulk kernels); without it the block sums carry three values.
+// the tail coefficients nu * y_l of the augmented operator into coef[MAX_NB]
+// (shared memory; the caller synchronises before reading them)
+__device__ __forceinline__ void epilogue_coefs(const AugEpilogue& ep, double* coef) {
+  if (threadIdx.x < MAX_NB) {
+    const int l = threadIdx.x;
+    coef[l] = (l < ep.p && ep.b[l]) ? ep.nu * ep.tail_in[l] : 0.0;
+  }
+}
+
+// Per-node half of the volume epilogue: o = res + sum_l coef_l b_l (B64),
+// stored at out, and this node's terms of the window dots added to the
+// thread's partial sums (da = z . V_{j-1}, db = z . V_j, dcc = z . V_{j-2},
+// and with CD the V . V products dab, dbc).
+template <bool W3, bool B64, bool CD>
+__device__ __forceinline__ void epilogue_node(const AugEpilogue& ep, const double* coef, long long idx, long long N,
+                                              const double res[3], double* __restrict__ out, double& da, double& db,
+                                              double& dcc, double& dab, double& dbc) {
+  double ob[3] = {res[0], res[1], res[2]};
+  // a loop over the p columns, not an unrolled one over MAX_NB with a guard:
+  // guarded-off FP64 instructions still take the FP64 pipe's issue slots
+  if (B64) {
+    const int p = ep.p < MAX_NB ? ep.p : MAX_NB;
+#pragma unroll 1
+    for (int l = 0; l < p; ++l) {
+      const double* bl = ep.b[l];
+      if (!bl) continue;
+      const double cl = coef[l];
+#pragma unroll
+      for (int mu = 0; mu < 3; ++mu) ob[mu] = fma(cl, bl[idx + mu * N], ob[mu]);
+    }
+  }
+  const bool cd = CD && ep.cdot_out != nullptr;
+#pragma unroll
+  for (int mu = 0; mu < 3; ++mu) {
+    const double o = ob[mu];
+    out[idx + mu * N] = o;
+    if (ep.dotB) {
+      const double vb = ep.dotB[idx + mu * N];
+      db = fma(o, vb, db);
+      if (ep.dotA) {
+        const double va = ep.dotA[idx + mu * N];
+        da = fma(o, va, da);
+        if (cd) dab = fma(vb, va, dab);
+      }
+      if (W3 && ep.dotC) {
+        const double vc = ep.dotC[idx + mu * N];
+        dcc = fma(o, vc, dcc);
+        if (cd) dbc = fma(vb, vc, dbc);
+      }
+    }
+  }
+}
+
 template <int THREADS, bool SCALED = false, bool W3 = false, bool B64 = true, bool CD = false>
 __device__ __forceinline__ void volume_epilogue(const AugEpilogue& ep, bool active, long long idx, long long N,
                                                 const double res[3], double* __restrict__ out, unsigned int blk,
                                                 unsigned int nblk) {
-  // the tail coefficients nu * y_l, once per block
   __shared__ double coef[MAX_NB];
-  if (B64 && threadIdx.x < MAX_NB) {
-    const int l = threadIdx.x;
-    coef[l] = (l < ep.p && ep.b[l]) ? ep.nu * ep.tail_in[l] : 0.0;
-  }
+  if (B64) epilogue_coefs(ep, coef);
   __syncthreads();
   double da = 0.0, db = 0.0, dcc = 0.0, dab = 0.0, dbc = 0.0;
-  const bool cd = CD && ep.cdot_out != nullptr;
   if (active) {
+    double r[3];
 #pragma unroll
-    for (int mu = 0; mu < 3; ++mu) {
-      double o = SCALED ? res[mu] : ep.scale * res[mu];
-#pragma unroll
-      for (int l = 0; l < MAX_NB; ++l)
-        if (B64 && l < ep.p && ep.b[l]) o = fma(coef[l], ep.b[l][idx + mu * N], o);
-      out[idx + mu * N] = o;
-      if (ep.dotB) {
-        const double vb = ep.dotB[idx + mu * N];
-        db = fma(o, vb, db);
-        if (ep.dotA) {
-          const double va = ep.dotA[idx + mu * N];
-          da = fma(o, va, da);
-          if (cd) dab = fma(vb, va, dab);
-        }
-        if (W3 && ep.dotC) {
-          const double vc = ep.dotC[idx + mu * N];
-          dcc = fma(o, vc, dcc);
-          if (cd) dbc = fma(vb, vc, dbc);
-        }
-      }
-    }
+    for (int mu = 0; mu < 3; ++mu) r[mu] = SCALED ? res[mu] : ep.scale * res[mu];
+    epilogue_node<W3, B64, CD>(ep, coef, idx, N, r, out, da, db, dcc, dab, dbc);
   }
   __shared__ double sred[(CD ? 5 : 3) * THREADS];
   epilogue_finish<THREADS, W3, CD>(ep, da, db, dcc, blk, nblk, dab, dbc, sred);

@@ -25,6 +25,8 @@
 // path up to rounding; no FP64 division or square root remains per JVP.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "dfr_device.cuh"
 #include "dfr_tangent.cuh"
 #include "kiops_dev.h"
@@ -119,14 +121,15 @@ __global__ void __launch_bounds__(128) face_tangent_kernel(TanFaceArgs<T> a, Dfr
   face_tangent_body<T, NS>(a, dc, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-// W3: with the orthogonalisation window of three in the epilogue
+// W3: with the orthogonalisation window of three in the epilogue; a
+// persistent grid (volume_ctas)
 template <typename T, int NS, bool W3>
-__global__ void __launch_bounds__(VolShape<NS>::THREADS) volume_tangent_kernel(TanVolArgs<T> a, DfrConst dc) {
+__global__ void __launch_bounds__(VolShape<NS>::THREADS, 4) volume_tangent_kernel(TanVolArgs<T> a, DfrConst dc) {
   pdl_wait();
   pdl_trigger();
   if (a.ep.skip && *a.ep.skip) return;
   __shared__ VolSmem<T, NS, VolShape<NS>::EPB> sm;
-  volume_tangent_body<T, NS, VolShape<NS>::EPB, VolShape<NS>::THREADS, W3>(a, dc, blockIdx.x, gridDim.x, sm);
+  volume_tangent_persistent<T, NS, VolShape<NS>::EPB, VolShape<NS>::THREADS, W3>(a, dc, sm);
 }
 
 // the same kernels for the device-driven solver: the Krylov iteration index and
@@ -142,7 +145,7 @@ __global__ void __launch_bounds__(128) face_tangent_dev_kernel(const KDev* __res
 }
 
 template <typename T, int NS, bool W3>
-__global__ void __launch_bounds__(VolShape<NS>::THREADS) volume_tangent_dev_kernel(const KDev* __restrict__ kd, KFix f,
+__global__ void __launch_bounds__(VolShape<NS>::THREADS, 4) volume_tangent_dev_kernel(const KDev* __restrict__ kd, KFix f,
                                                                                    TanVolArgs<T> a0, DfrConst dc) {
   __shared__ TanVolArgs<T> a;
   if (threadIdx.x == 0) {
@@ -155,7 +158,39 @@ __global__ void __launch_bounds__(VolShape<NS>::THREADS) volume_tangent_dev_kern
   __syncthreads();
   if (*a.ep.skip) return;
   __shared__ VolSmem<T, NS, VolShape<NS>::EPB> sm;
-  volume_tangent_body<T, NS, VolShape<NS>::EPB, VolShape<NS>::THREADS, W3>(a, dc, blockIdx.x, gridDim.x, sm);
+  volume_tangent_persistent<T, NS, VolShape<NS>::EPB, VolShape<NS>::THREADS, W3>(a, dc, sm);
+}
+
+// CTAs of a persistent volume grid: as many as fit on the GPU at once (the
+// kernel's occupancy x SMs), at most one per element tile.  Queried once per
+// kernel and device; prepare_volume_dev runs the queries of the device-driven
+// solver's kernels before its stream capture.
+constexpr int kMaxDevices = 64;
+// Element tiles per CTA of a volume grid large enough to fill the GPU three
+// times over: three tiles a CTA, the CTAs in waves.  Measured at 6 x 60 x 60,
+// p = 5 (FP64, live): 149 / 142 / 137 / 151 us per launch with 1 / 2 / 3 / 4
+// tiles a CTA and 142 us with one wave of resident CTAs taking an even share
+// (the four CTAs of an SM then run their load and compute phases in step).
+// Smaller grids take one wave of resident CTAs with an even share each.
+constexpr int kVolTilesPerCta = 3;
+
+template <typename T, int NS, bool W3, bool DEV>
+int volume_ctas(int device, long long tiles) {
+  static int fit[kMaxDevices] = {};
+  if (device < 0 || device >= kMaxDevices) return -1;
+  if (!fit[device]) {
+    int sms = 0, nb = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return -1;
+    const cudaError_t e =
+        DEV ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, volume_tangent_dev_kernel<T, NS, W3>,
+                                                            VolShape<NS>::THREADS, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, volume_tangent_kernel<T, NS, W3>,
+                                                            VolShape<NS>::THREADS, 0);
+    if (e != cudaSuccess || nb < 1) return -1;
+    fit[device] = nb * sms;
+  }
+  if (tiles >= (long long)kVolTilesPerCta * fit[device]) return (int)((tiles + kVolTilesPerCta - 1) / kVolTilesPerCta);
+  return (int)std::min<long long>(std::max<long long>(tiles, 1), fit[device]);
 }
 
 __global__ void to_float_kernel(const double* __restrict__ src, float* __restrict__ dst, long long n) {
@@ -200,9 +235,12 @@ int tangent_ns(Ctx& c, const double* v, double* out, const AugEpilogue& ep, cons
     if (rt == SW_OK) c.launches--;   // counted below
   }
   if (rt != SW_OK) {
-    const cudaError_t ev = ep.dotC ? launch_pdl(volume_tangent_kernel<T, NS, true>, dim3((unsigned)vblocks),
+    const int ctas = ep.dotC ? volume_ctas<T, NS, true, false>(c.device, vblocks)
+                             : volume_ctas<T, NS, false, false>(c.device, vblocks);
+    if (ctas < 1) return SW_ECUDA;
+    const cudaError_t ev = ep.dotC ? launch_pdl(volume_tangent_kernel<T, NS, true>, dim3((unsigned)ctas),
                                                  dim3(VolShape<NS>::THREADS), s, va, c.dc)
-                                   : launch_pdl(volume_tangent_kernel<T, NS, false>, dim3((unsigned)vblocks),
+                                   : launch_pdl(volume_tangent_kernel<T, NS, false>, dim3((unsigned)ctas),
                                                 dim3(VolShape<NS>::THREADS), s, va, c.dc);
     if (ev != cudaSuccess) return SW_ECUDA;
   }
@@ -239,10 +277,13 @@ int capture_iter_ns(Ctx& c, KDev* kd, const KFix& f, bool w3, int p, cudaStream_
   }
   TanVolArgs<T> va{nullptr, c.nodes, c.nelem, ln, fb, nullptr, AugEpilogue{}};
   const long long vblocks = (c.nelem + VolShape<NS>::EPB - 1) / VolShape<NS>::EPB;
+  const int ctas = w3 ? volume_ctas<T, NS, true, true>(c.device, vblocks)
+                      : volume_ctas<T, NS, false, true>(c.device, vblocks);
+  if (ctas < 1) return SW_ECUDA;
   if (w3)
-    volume_tangent_dev_kernel<T, NS, true><<<(unsigned)vblocks, VolShape<NS>::THREADS, 0, s>>>(kd, f, va, c.dc);
+    volume_tangent_dev_kernel<T, NS, true><<<(unsigned)ctas, VolShape<NS>::THREADS, 0, s>>>(kd, f, va, c.dc);
   else
-    volume_tangent_dev_kernel<T, NS, false><<<(unsigned)vblocks, VolShape<NS>::THREADS, 0, s>>>(kd, f, va, c.dc);
+    volume_tangent_dev_kernel<T, NS, false><<<(unsigned)ctas, VolShape<NS>::THREADS, 0, s>>>(kd, f, va, c.dc);
   c.launches++;
   return cuda_status(cudaGetLastError());
 }
@@ -252,7 +293,28 @@ int capture_iter_any(Ctx& c, KDev* kd, const KFix& f, bool fp32, bool w3, int p,
   return fp32 ? capture_iter_ns<float, NS>(c, kd, f, w3, p, s) : capture_iter_ns<double, NS>(c, kd, f, w3, p, s);
 }
 
+template <int NS>
+int prepare_dev_ns(const Ctx& c, bool fp32) {
+  const int a = fp32 ? volume_ctas<float, NS, false, true>(c.device, 1) : volume_ctas<double, NS, false, true>(c.device, 1);
+  const int b = fp32 ? volume_ctas<float, NS, true, true>(c.device, 1) : volume_ctas<double, NS, true, true>(c.device, 1);
+  return (a < 1 || b < 1) ? SW_ECUDA : SW_OK;
+}
+
 }  // namespace
+
+int prepare_volume_dev(const Ctx& c, bool fp32) {
+  switch (c.ns) {
+    case 1: return prepare_dev_ns<1>(c, fp32);
+    case 2: return prepare_dev_ns<2>(c, fp32);
+    case 3: return prepare_dev_ns<3>(c, fp32);
+    case 4: return prepare_dev_ns<4>(c, fp32);
+    case 5: return prepare_dev_ns<5>(c, fp32);
+    case 6: return prepare_dev_ns<6>(c, fp32);
+    case 7: return prepare_dev_ns<7>(c, fp32);
+    case 8: return prepare_dev_ns<8>(c, fp32);
+    default: return SW_EINVAL;
+  }
+}
 
 int capture_iter_jvp(Ctx& c, KDev* kd, const KFix& f, bool fp32, bool w3, int p, cudaStream_t s) {
   switch (c.ns) {

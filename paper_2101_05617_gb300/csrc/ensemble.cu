@@ -276,7 +276,7 @@ __device__ void update_task(const EnsDesc& d, EnsDyn& y, unsigned int local, Ens
     const long long i0 = (long long)local * d.vec_len, i1 = min(i0 + d.vec_len, N);
     acc = mgs_update_range(z, VA, VB, h1, h2, i0 + threadIdx.x, i1, BLOCK);
   }
-  const double b = block_sum(acc);
+  const double b = block_sum<BLOCK>(acc);
   __shared__ bool last;
   if (threadIdx.x == 0) {
     d.upart[local] = b;
@@ -288,7 +288,7 @@ __device__ void update_task(const EnsDesc& d, EnsDyn& y, unsigned int local, Ens
     __threadfence();
     double s = 0.0;
     for (unsigned int k = threadIdx.x; k < d.n_vec; k += BLOCK) s += __ldcg(d.upart + k);
-    s = block_sum(s);
+    s = block_sum<BLOCK>(s);
     if (threadIdx.x == 0) {
       if (!skip) {
         const double r = sqrt(s);
@@ -321,7 +321,7 @@ __device__ void scale_task(const EnsDesc& d, EnsDyn& y, unsigned int local, EnsC
     const long long i0 = (long long)local * d.vec_len, i1 = min(i0 + d.vec_len, N);
     acc = scale_dot_range(z, VB, r, i0 + threadIdx.x, i1, BLOCK);
   }
-  const double b = block_sum(acc);
+  const double b = block_sum<BLOCK>(acc);
   __shared__ bool last;
   if (threadIdx.x == 0) {
     d.upart[local] = b;
@@ -333,7 +333,7 @@ __device__ void scale_task(const EnsDesc& d, EnsDyn& y, unsigned int local, EnsC
   __threadfence();
   double s = 0.0;
   for (unsigned int k = threadIdx.x; k < d.n_vec; k += BLOCK) s += __ldcg(d.upart + k);
-  s = block_sum(s);
+  s = block_sum<BLOCK>(s);
   if (threadIdx.x == 0) {
     if (!skip) d.cdot[j + 1] = s;
     y.face_done = 0u;

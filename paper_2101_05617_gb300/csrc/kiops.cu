@@ -113,6 +113,8 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
     }
   }
   if (cudaMemsetAsync(c.d_flags + 3, 0, sizeof(int), s) != cudaSuccess) return SW_ECUDA;
+  // the pass and epilogue tickets, in case a wait that gave up left them mid-count
+  if (cudaMemsetAsync(c.d_flags + 8, 0, sizeof(int) * 2, s) != cudaSuccess) return SW_ECUDA;
   // X = [b_0; 0 .. 0 mu]
   if (bk[0]) {
     if (cudaMemcpyAsync(c.d_X, bk[0], sizeof(double) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return SW_ECUDA;
@@ -186,6 +188,7 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
   // complex64-bulk form with a fused window: an FP32 copy of the basis, written
   // by the scale pass with each new vector, feeds the FP32 kernels
   const bool use32 = use_lin && c.jvp_mode == 2 && (o.iop == 2 || o.iop == 3);
+  const bool fused = c.orth_fuse_enable && orth_fused_available(c);
   if (use32 && c.v32_cap < c.vcap) {
     if (c.d_V32) cudaFree(c.d_V32);
     c.d_V32 = nullptr;
@@ -234,12 +237,17 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
         rc = use_lin ? launch_jvp_lin(c, Vi, Vn, ep, s, c.jvp_mode == 2) : launch_jvp(c, q_lin, Vi, kEpsJvp, Vn, ep, s);
         if (rc) return rc;
         double* hs = c.d_H + (long long)(it + 1) * c.ldh + it;
-        if ((rc = launch_update_norm(c, Vn, ep.dotA, Vi, hA, hB, N, hs, o.tol, it + 1, s, ep.dotC, hC))) return rc;
         // V_{j+1} . V_{j-1} is needed by the window of three two iterations later
         const double* Vprev = (o.iop == 3 && it >= 1) ? V + (it - 1) * ldv : nullptr;
-        if ((rc = launch_scale_dot(c, Vn, Vi, hs, N, use32 ? nullptr : c.d_cdot + it + 1, s, Vprev,
-                                   c.d_cdot2 + it + 1, use32 ? c.d_V32 + (it + 1) * ldv : nullptr)))
-          return rc;
+        double* cn = use32 ? nullptr : c.d_cdot + it + 1;
+        float* z32 = use32 ? c.d_V32 + (it + 1) * ldv : nullptr;
+        if (fused) {
+          rc = launch_orth_fused(c, Vn, ep.dotA, Vi, hA, hB, N, hs, o.tol, it + 1, ep.dotC, hC, cn, Vprev,
+                                 c.d_cdot2 + it + 1, z32, s);
+        } else if (!(rc = launch_update_norm(c, Vn, ep.dotA, Vi, hA, hB, N, hs, o.tol, it + 1, s, ep.dotC, hC))) {
+          rc = launch_scale_dot(c, Vn, Vi, hs, N, cn, s, Vprev, c.d_cdot2 + it + 1, z32);
+        }
+        if (rc) return rc;
         continue;
       }
       ep.dotA = ep.dotB = ep.dotC = nullptr;

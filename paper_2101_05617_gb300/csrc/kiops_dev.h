@@ -90,5 +90,8 @@ template <int NS>
 int capture_volume_tile_dev(Ctx& c, KDev* kd, const KFix& f, bool w3, cudaStream_t s);
 // function attributes of that kernel, set before any stream capture (dfr_tile.cu)
 int prepare_volume_tile_dev(const Ctx& c);
+// the grid-size queries of the persistent volume kernels in that form, run
+// before any stream capture (dfr_split.cu)
+int prepare_volume_dev(const Ctx& c, bool fp32);
 
 }  // namespace swepi

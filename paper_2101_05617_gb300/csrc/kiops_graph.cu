@@ -39,7 +39,7 @@ namespace swepi {
 
 namespace {
 
-constexpr int kRedThreads = 256;   // threads of the reduction launches (as krylov.cu)
+constexpr int kRedThreads = kPassThreads;   // threads of the reduction launches (as krylov.cu)
 
 struct KGraph {
   cudaGraph_t graph = nullptr;
@@ -503,6 +503,7 @@ int kiops_run_graph(Ctx& c, double dt, double tau_out, int nb, const double* con
     const unsigned prof = c.prof;
     c.prof = 0;   // no event records inside the graph
     rc = fp32 ? prepare_volume_tile_dev(c) : SW_OK;
+    if (rc == SW_OK) rc = prepare_volume_dev(c, fp32);
     if (rc == SW_OK) {   // the device attribute query of the persistent grid, before capture too
       int sms = 0;
       rc = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device) == cudaSuccess ? SW_OK : SW_ECUDA;

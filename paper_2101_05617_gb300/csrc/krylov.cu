@@ -13,7 +13,7 @@ namespace swepi {
 
 namespace {
 
-constexpr int RED_THREADS = 256;
+constexpr int RED_THREADS = kPassThreads;
 
 enum { OP_DOT = 0, OP_NORM2 = 1, OP_NORM1 = 2 };
 
@@ -166,6 +166,17 @@ __global__ void __launch_bounds__(RED_THREADS) scale_dot_kernel(double* __restri
   scale_dot_dev(z, VB, hsub, n, partials, ticket, c_out, happy, VA, c2_out, z32);
 }
 
+// both passes in one cooperative launch (orth_fused_dev)
+__global__ void __launch_bounds__(RED_THREADS) orth_fused_kernel(
+    double* __restrict__ z, const double* __restrict__ VA, const double* __restrict__ VB, const double* h1p,
+    const double* h2p, long long n, double* partials, unsigned int* ticket, double* hsub, double tol, int* happy,
+    int happy_value, const double* __restrict__ VC, const double* h0p, double* c_out, const double* __restrict__ VA2,
+    double* c2_out, float* __restrict__ z32, unsigned int* gen, int* err) {
+  pdl_trigger();
+  orth_fused_dev(z, VA, VB, h1p, h2p, n, partials, ticket, hsub, tol, happy, happy_value, VC, h0p, c_out, VA2, c2_out,
+                 z32, gen, err);
+}
+
 int blocks_for(long long n, int threads) {
   long long b = (n + threads - 1) / threads;
   if (b > 4 * 152 * 4) b = 4 * 152 * 4;
@@ -289,6 +300,51 @@ int launch_scale_dot(Ctx& c, double* z, const double* VB, const double* hsub, lo
   if (prof_on(c, PK_ORTH)) {
     cudaEventRecord(e1, s);
     prof_record(c, PK_ORTH, e0, e1);
+  }
+  c.launches++;
+  return cuda_status(cudaGetLastError());
+}
+
+int orth_fused_available(Ctx& c) {
+  if (c.orth_fused == 0) {
+    int coop = 0, sms = 0, nb = 0;
+    c.orth_fused = -1;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c.device) == cudaSuccess && coop &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, orth_fused_kernel, RED_THREADS, 0) == cudaSuccess &&
+        (long long)nb * sms >= RED_BLOCKS)
+      c.orth_fused = 1;
+  }
+  return c.orth_fused > 0;
+}
+
+int launch_orth_fused(Ctx& c, double* z, const double* VA, const double* VB, const double* h1, const double* h2,
+                      long long N, double* hsub, double tol, int happy_value, const double* VC, const double* h0,
+                      double* c_out, const double* VA2, double* c2_out, float* z32, cudaStream_t s) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (prof_on(c, PK_ORTH)) {
+    e0 = prof_event(c);
+    e1 = prof_event(c);
+    cudaEventRecord(e0, s);
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(RED_BLOCKS);
+  cfg.blockDim = dim3(RED_THREADS);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, orth_fused_kernel, z, VA, VB, h1, h2, N, c.d_partials,
+                         reinterpret_cast<unsigned int*>(c.d_flags + 8), hsub, tol, c.d_flags, happy_value, VC, h0,
+                         c_out, VA2, c2_out, z32, reinterpret_cast<unsigned int*>(c.d_flags + 10),
+                         c.d_flags + 3) != cudaSuccess)
+    return SW_ECUDA;
+  if (prof_on(c, PK_ORTH)) {
+    cudaEventRecord(e1, s);
+    prof_record(c, PK_ORTH, e0, e1);
+    prof_record(c, PK_ORTH, e1, e1);   // counted as the two passes it replaces
   }
   c.launches++;
   return cuda_status(cudaGetLastError());

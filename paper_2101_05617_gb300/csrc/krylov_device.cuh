@@ -17,17 +17,27 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// block sum in a fixed order; result valid in thread 0
+// threads of the vector-pass and reduction launches (krylov.cu, the
+// device-driven solver)
+constexpr int kPassThreads = 256;
+
+// block sum in a fixed order over a block of THREADS threads (all of which
+// call it); result valid in thread 0.  Every thread stores its value in shared
+// memory and warp 0 alone sums them (a stride of 32, then a shuffle tree): on
+// this GPU a shuffle tree in every warp would cost each warp five FP64 adds on
+// the slow FP64 pipe.
+template <int THREADS = kPassThreads>
 __device__ __forceinline__ double block_sum(double v) {
-  __shared__ double ws[32];
-  v = warp_sum(v);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) ws[w] = v;
+  static_assert(THREADS >= 32 && THREADS <= 1024 && THREADS % 32 == 0, "block of whole warps");
+  __shared__ double sb[THREADS];
+  __syncthreads();   // an earlier call's readers are done with sb
+  if (threadIdx.x < THREADS) sb[threadIdx.x] = v;
   __syncthreads();
   double r = 0.0;
-  if (w == 0) {
-    r = (lane < (int)(blockDim.x >> 5)) ? ws[lane] : 0.0;
+  if (threadIdx.x < 32) {
+    r = sb[threadIdx.x];
+#pragma unroll
+    for (int i = threadIdx.x + 32; i < THREADS; i += 32) r += sb[i];
     r = warp_sum(r);
   }
   return r;
@@ -39,24 +49,27 @@ __device__ __forceinline__ double block_sum(double v) {
 // (z was written by another kernel or CTA: read through L2).
 //   z -= h0 VC + h1 VA + h2 VB (VC, VA may be null; oldest first); returns the
 //   thread's sum of z_i^2
-__device__ __forceinline__ double mgs_update_range(double* __restrict__ z, const double* __restrict__ VA,
-                                                   const double* __restrict__ VB, double h1, double h2, long long i,
-                                                   long long i1, long long stride,
-                                                   const double* __restrict__ VC = nullptr, double h0 = 0.0) {
+// HA, HC: VA, VC present (compiled in, so that no guarded-off FP64
+// instruction takes the FP64 pipe's issue slots)
+template <bool HA, bool HC>
+__device__ __forceinline__ double mgs_update_range_t(double* __restrict__ z, const double* __restrict__ VA,
+                                                     const double* __restrict__ VB, double h1, double h2, long long i,
+                                                     long long i1, long long stride, const double* __restrict__ VC,
+                                                     double h0) {
   double acc = 0.0;
   for (; i + 3 * stride < i1; i += 4 * stride) {
-    double v[4], b[4], a[4] = {0.0, 0.0, 0.0, 0.0}, c[4] = {0.0, 0.0, 0.0, 0.0};
+    double v[4], b[4], a[4], c[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       v[k] = __ldcg(z + i + k * stride);
       b[k] = VB[i + k * stride];
-      if (VA) a[k] = VA[i + k * stride];
-      if (VC) c[k] = VC[i + k * stride];
+      if (HA) a[k] = VA[i + k * stride];
+      if (HC) c[k] = VC[i + k * stride];
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      if (VC) v[k] = fma(-h0, c[k], v[k]);
-      if (VA) v[k] = fma(-h1, a[k], v[k]);
+      if (HC) v[k] = fma(-h0, c[k], v[k]);
+      if (HA) v[k] = fma(-h1, a[k], v[k]);
       v[k] = fma(-h2, b[k], v[k]);
       z[i + k * stride] = v[k];
       acc = fma(v[k], v[k], acc);
@@ -64,13 +77,25 @@ __device__ __forceinline__ double mgs_update_range(double* __restrict__ z, const
   }
   for (; i < i1; i += stride) {
     double v = __ldcg(z + i);
-    if (VC) v = fma(-h0, VC[i], v);
-    if (VA) v = fma(-h1, VA[i], v);
+    if (HC) v = fma(-h0, VC[i], v);
+    if (HA) v = fma(-h1, VA[i], v);
     v = fma(-h2, VB[i], v);
     z[i] = v;
     acc = fma(v, v, acc);
   }
   return acc;
+}
+
+__device__ __forceinline__ double mgs_update_range(double* __restrict__ z, const double* __restrict__ VA,
+                                                   const double* __restrict__ VB, double h1, double h2, long long i,
+                                                   long long i1, long long stride,
+                                                   const double* __restrict__ VC = nullptr, double h0 = 0.0) {
+  if (VC) {
+    return VA ? mgs_update_range_t<true, true>(z, VA, VB, h1, h2, i, i1, stride, VC, h0)
+              : mgs_update_range_t<false, true>(z, VA, VB, h1, h2, i, i1, stride, VC, h0);
+  }
+  return VA ? mgs_update_range_t<true, false>(z, VA, VB, h1, h2, i, i1, stride, VC, h0)
+            : mgs_update_range_t<false, false>(z, VA, VB, h1, h2, i, i1, stride, VC, h0);
 }
 
 //   z *= r; returns the thread's sum of z_i VB_i, and with VA also the sum of
@@ -139,13 +164,15 @@ __device__ __forceinline__ double scale_dot_range(double* __restrict__ z, const 
 // device-driven solver call them).
 // z -= h0 V_C + h1 V_A + h2 V_B (the modified Gram-Schmidt updates, oldest
 // first; V_C, V_A may be absent), then ||z||_2 -> *hsub with the
-// happy-breakdown flag below tol
-__device__ __forceinline__ void update_norm_dev(double* __restrict__ z, const double* __restrict__ VA,
-                                                const double* __restrict__ VB, const double* h1p, const double* h2p,
-                                                long long n, double* partials, unsigned int* ticket, double* hsub,
-                                                double tol, int* happy, int happy_value, const double* __restrict__ VC,
-                                                const double* h0p) {
-  if (happy[0]) return;
+// happy-breakdown flag below tol.  Returns 0 when the basis had already broken
+// down (nothing done), 2 in the CTA that finished last (it wrote *hsub), else 1
+// (uniform over each CTA).
+__device__ __forceinline__ int update_norm_dev(double* __restrict__ z, const double* __restrict__ VA,
+                                               const double* __restrict__ VB, const double* h1p, const double* h2p,
+                                               long long n, double* partials, unsigned int* ticket, double* hsub,
+                                               double tol, int* happy, int happy_value, const double* __restrict__ VC,
+                                               const double* h0p) {
+  if (__ldcg(happy)) return 0;
   const double h1 = VA ? *h1p : 0.0, h2 = *h2p, h0 = VC ? *h0p : 0.0;
   const double acc = mgs_update_range(z, VA, VB, h1, h2, (long long)blockIdx.x * blockDim.x + threadIdx.x, n,
                                       (long long)gridDim.x * blockDim.x, VC, h0);
@@ -157,7 +184,7 @@ __device__ __forceinline__ void update_norm_dev(double* __restrict__ z, const do
     last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
   }
   __syncthreads();
-  if (!last) return;
+  if (!last) return 1;
   __threadfence();
   double sum = 0.0;
   for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) sum += __ldcg(partials + i);
@@ -171,6 +198,7 @@ __device__ __forceinline__ void update_norm_dev(double* __restrict__ z, const do
     }
     *ticket = 0u;
   }
+  return 2;
 }
 
 // V_next = z / *hsub in place, V_next . V_B -> *c_out and, with V_A, V_next .
@@ -180,8 +208,9 @@ __device__ __forceinline__ void scale_dot_dev(double* __restrict__ z, const doub
                                               const double* hsub, long long n, double* partials, unsigned int* ticket,
                                               double* c_out, const int* happy, const double* __restrict__ VA,
                                               double* c2_out, float* __restrict__ z32) {
-  if (happy[0]) return;
-  const double r = 1.0 / *hsub;
+  // through L2: in the fused launch another CTA has just written them
+  if (__ldcg(happy)) return;
+  const double r = 1.0 / __ldcg(hsub);
   if (!c_out) {   // scale only (the next volume kernel forms the dots)
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -218,6 +247,55 @@ __device__ __forceinline__ void scale_dot_dev(double* __restrict__ z, const doub
     if (VA) *c2_out = sum2;
     *ticket = 0u;
   }
+}
+
+// polls of the fused pass's grid-wide wait (each after a short sleep: about a
+// second in all) before it gives up
+constexpr unsigned int kOrthWaitPolls = 1u << 23;
+
+// Both passes in one launch of a grid whose CTAs are all resident at once (a
+// cooperative launch): the update pass, then -- once the CTA that finished it
+// last has published ||z|| by advancing the counter *gen -- the scale pass.
+// The same arithmetic in the same order as update_norm_dev followed by
+// scale_dot_dev on the same grid (bitwise the same results); it saves the
+// second launch and its ramp.  A CTA that waits past the bound sets *err and
+// leaves its share of the scale pass undone (the caller reports a timeout).
+__device__ __forceinline__ void orth_fused_dev(double* __restrict__ z, const double* __restrict__ VA,
+                                               const double* __restrict__ VB, const double* h1p, const double* h2p,
+                                               long long n, double* partials, unsigned int* ticket, double* hsub,
+                                               double tol, int* happy, int happy_value, const double* __restrict__ VC,
+                                               const double* h0p, double* c_out, const double* __restrict__ VA2,
+                                               double* c2_out, float* __restrict__ z32, unsigned int* gen, int* err) {
+  __shared__ unsigned int g0;
+  __shared__ int gave_up;
+  // read before this CTA's ticket (ordered by the fence ahead of it): the
+  // counter can only advance after every CTA has taken its ticket
+  if (threadIdx.x == 0) {
+    g0 = *reinterpret_cast<volatile unsigned int*>(gen);
+    gave_up = 0;
+  }
+  const int st = update_norm_dev(z, VA, VB, h1p, h2p, n, partials, ticket, hsub, tol, happy, happy_value, VC, h0p);
+  if (st == 0) return;   // uniform over the grid
+  if (threadIdx.x == 0) {
+    if (st == 2) {
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      unsigned int polls = 0;
+      while (*reinterpret_cast<volatile unsigned int*>(gen) == g0) {
+        if (++polls > kOrthWaitPolls) {
+          gave_up = 1;
+          atomicExch(err, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+      __threadfence();
+    }
+  }
+  __syncthreads();
+  if (gave_up) return;
+  scale_dot_dev(z, VB, hsub, n, partials, ticket, c_out, happy, VA2, c2_out, z32);
 }
 
 // ------------------------------------------------------------ expm

@@ -141,6 +141,8 @@ struct Ctx {
   int b32_cap = 0;                  // vectors allocated in d_b32
   // device-driven phi-function solver (kiops_graph.cu)
   int kiops_driver = 0;           // 0: controller on the host (kiops.cu), 1: on the device, one CUDA graph per call
+  int orth_fused = 0;             // the GPU holds the fused orthogonalisation grid: 0 unknown, 1 yes, -1 no
+  int orth_fuse_enable = 1;       // both orthogonalisation passes in one cooperative launch where it can
   void* kg = nullptr;             // its graph, state and staging (owned, kiops_graph.cu)
   // KIOPS call log and learned control
   Mlp* controller = nullptr;      // not owned
@@ -299,6 +301,13 @@ int launch_scale_dot(Ctx& c, double* z, const double* VB, const double* hsub, lo
                      cudaStream_t s, const double* VA = nullptr, double* c2_out = nullptr, float* z32 = nullptr);
 // dst = src rounded to FP32 (n entries)
 int launch_to_float(Ctx& c, const double* src, float* dst, long long n, cudaStream_t s);
+// both orthogonalisation passes (launch_update_norm, then launch_scale_dot with
+// c_out, VA2, c2_out, z32) in one cooperative launch, where the GPU holds its
+// whole grid at once (orth_fused_available); a wait past its bound sets d_flags[3]
+int orth_fused_available(Ctx& c);
+int launch_orth_fused(Ctx& c, double* z, const double* VA, const double* VB, const double* h1, const double* h2,
+                      long long N, double* hsub, double tol, int happy_value, const double* VC, const double* h0,
+                      double* c_out, const double* VA2, double* c2_out, float* z32, cudaStream_t s);
 double fp64_fma_peak_tflops();
 int launch_set_tail(Ctx& c, double* x, long long n, int p, const double* vals, cudaStream_t s);
 int launch_lincomb(Ctx& c, double* out, long long n, int k, const double* const* xs,

@@ -102,6 +102,7 @@ def lib():
     L.sw_jvp_linearized.argtypes = [vp, vp, vp, vp]
     L.sw_set_jvp_mode.argtypes = [vp, ip]
     L.sw_set_kiops_driver.argtypes = [vp, ip]
+    L.sw_set_orth_fused.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int)]
     L.sw_kiops_phi.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, ip, ctypes.POINTER(vp),
                                ctypes.POINTER(sw_kiops_opts), vp, ctypes.POINTER(sw_kiops_stats), vp]
     L.sw_epi_step.argtypes = [vp, ip, ctypes.c_double, vp, ctypes.POINTER(sw_kiops_opts),
@@ -155,7 +156,7 @@ def lib():
 
 EXPORTED = ["sw_init", "sw_free", "sw_num_unknowns", "sw_grid_info", "sw_node_xyz", "sw_state_from_fields",
             "sw_set_bottom", "sw_set_bottom_host", "sw_rhs", "sw_jvp", "sw_jvp_static_scratch", "sw_linearize", "sw_jvp_linearized",
-            "sw_set_jvp_mode", "sw_set_kiops_driver", "sw_kiops_phi", "sw_epi_step", "sw_epi_step_host", "sw_epi_set_history",
+            "sw_set_jvp_mode", "sw_set_kiops_driver", "sw_set_orth_fused", "sw_kiops_phi", "sw_epi_step", "sw_epi_step_host", "sw_epi_set_history",
             "sw_epi_reset", "sw_epi_coefficients", "sw_dfr_operators", "sw_node_coefficients",
             "sw_interface_transform", "sw_kernel_launches", "sw_profile", "sw_profile_kinds", "sw_profile_read", "sw_fp64_fma_peak",
             "sw_status_str", "sw_mlp_create", "sw_mlp_free", "sw_mlp_set_params", "sw_mlp_get_params",
@@ -278,6 +279,14 @@ def sw_jvp_linearized(ctx, v, Jv, stream=None):
 
 def sw_set_jvp_mode(ctx, mode):
     _check("sw_set_jvp_mode", lib().sw_set_jvp_mode(ctx, int(mode)))
+
+
+def sw_set_orth_fused(ctx, enable):
+    """Both orthogonalisation passes in one cooperative launch (1) or two (0);
+    returns 1 when the next phi-function call will fuse them."""
+    active = ctypes.c_int(0)
+    _check("sw_set_orth_fused", lib().sw_set_orth_fused(ctx, int(enable), ctypes.byref(active)))
+    return active.value
 
 
 def sw_set_kiops_driver(ctx, driver):
@@ -674,6 +683,9 @@ class SWContext:
 
     def set_kiops_driver(self, driver):
         sw_set_kiops_driver(self.handle, driver)
+
+    def set_orth_fused(self, enable):
+        return sw_set_orth_fused(self.handle, enable)
 
     def kiops_phi(self, q_lin, dt, b, tau_out=1.0, out=None, stream=None, **opts):
         import torch

@@ -55,6 +55,17 @@ def test_flop_counts():
     assert fv == 6 * 3600 * 36 * 165 and ff == 12 * 3600 * 6 * 112
 
 
+def test_orth_bytes_fused():
+    """Both passes in one launch move each vector once: z and the window vectors
+    read, V_{j+1} written (and its FP32 copy in the complex64-bulk form)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.orth_bytes_per_unknown(2, 1, True) == 8 * (1 + 2 + 1)
+    assert bench.orth_bytes_per_unknown(3, 1, True) == 8 * (1 + 3 + 1)
+    assert bench.orth_bytes_per_unknown(3, 2, True) == 8 * (1 + 3 + 1) + 4
+    assert bench.orth_bytes_per_unknown(2, 1) == 56 and bench.orth_bytes_per_unknown(3, 2) == 60
+
+
 def test_kernel_rooflines_arithmetic():
     """Per-kernel figures of a profiled EPI step: algorithmic flops and bytes per
     launch (the volume kernel: v and Jv, the window vectors, 4 b-columns, 11

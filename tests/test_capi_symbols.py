@@ -69,6 +69,7 @@ def test_argument_checks_without_gpu():
     assert L.sw_epi_set_history(None, 1, x, x, None) == EINVAL
     assert L.sw_epi_reset(None) == EINVAL
     assert L.sw_set_jvp_mode(None, 1) == EINVAL and L.sw_set_kiops_driver(None, 1) == EINVAL
+    assert L.sw_set_orth_fused(None, 1, None) == EINVAL
     assert L.sw_set_bottom(None, x) == EINVAL and L.sw_set_bottom_host(None, x) == EINVAL
     assert L.sw_node_xyz(None, x) == EINVAL
     assert L.sw_state_from_fields(None, x, x, x, x) == EINVAL
