@@ -12,7 +12,7 @@
 namespace swepi {
 
 constexpr int kDevMaxAttempts = 2000;    // substep attempts per call (then SW_EKRYLOV)
-constexpr int kDevMaxSquarings = 64;     // squarings of one exponential (then SW_ENONFINITE)
+constexpr int kDevMaxSquarings = 200;    // squarings of one exponential, the host driver's bound (then SW_ENONFINITE)
 constexpr int kTileMaxB = 4;             // b-column vectors the staged complex64-bulk volume kernel takes
 
 struct KDev {
