@@ -448,9 +448,12 @@ def fp32_form_comparison(args, dev, workload="ne30_p5", variants=(("fp64", 1, 2)
             ctx.set_kiops_driver(1)
         # both vector passes in one launch (the host controller; the device graph keeps two)
         fused = bool(ctx.set_orth_fused(1)) and extra != "device"
+        h0max = float(q.view(3, -1)[0].abs().max())
+        done = 0   # EPI steps completed (reported with a failure)
         try:
             for _ in range(warm * mult):
                 ctx.epi_step(wl.order, dt, q, tol=wl.tol, iop=iop)
+                done += 1
             if use_ctl:
                 ctl = ctl or learned.Controller.load()
                 swepi.sw_set_controller(ctx.handle, ctl.handle)
@@ -461,6 +464,7 @@ def fp32_form_comparison(args, dev, workload="ne30_p5", variants=(("fp64", 1, 2)
             e0.record()
             for _ in range(timed * mult):
                 kry += ctx.epi_step(wl.order, dt, q, tol=wl.tol, iop=iop)["krylov_iters"]
+                done += 1
             e1.record()
             torch.cuda.synchronize()
             res[name] = timed * mult / (e0.elapsed_time(e1) * 1e-3)
@@ -481,7 +485,10 @@ def fp32_form_comparison(args, dev, workload="ne30_p5", variants=(("fp64", 1, 2)
                     kernels[name] = {"error": f"{type(e).__name__}: {e}"[:200]}
                 ctx.profile(False)
         except Exception as e:   # e.g. a variant that left the finite range: reported per variant
-            res[name] = f"{type(e).__name__}: {e}"[:200]
+            torch.cuda.synchronize()
+            growth = float(q.view(3, -1)[0].abs().max()) / h0max
+            res[name] = (f"{type(e).__name__}: {e}"[:160] + f" in step {done + 1}; max |q^0| at the failing "
+                         f"step's start / initial = {growth:.3g}")
             states[name] = None
         swepi.sw_set_controller(ctx.handle, None)
         ctx.close()
