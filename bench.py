@@ -342,13 +342,15 @@ def ortho_roofline(prof_all, wl, fused=False):
 def volume_bytes_per_node(ns, mode, iop, p):
     """Bytes one volume-kernel launch of a Krylov iteration must move per node:
     read v (3 doubles; its FP32 copy in the complex64-bulk form) and write Jv (3
-    doubles), read the iop orthogonalisation window vectors (3 iop doubles), the p
+    doubles), read the iop orthogonalisation window vectors (3 iop doubles; none in
+    the complex64-bulk form, whose dots are a pass of their own), the p
     b-column vectors of the augmented operator (3 p entries: FP64, or their FP32
     copies in the complex64-bulk form), the 11 split-JVP coefficients (FP64, or
     FP32 in the complex64-bulk form) and the interface fluxes of the element's four
     edges (12 N_s values per element = 12 / N_s per node, FP64 or FP32)."""
     w = 8 if mode == 1 else 4
-    return 3 * w + 24 + 24 * iop + 3 * p * w + 11 * w + 12.0 / ns * w
+    window = 24 * iop if mode == 1 else 0   # the complex64-bulk form's volume kernel reads no window vectors
+    return 3 * w + 24 + window + 3 * p * w + 11 * w + 12.0 / ns * w
 
 
 def orth_bytes_per_unknown(iop, mode=1, fused=False):
@@ -358,7 +360,8 @@ def orth_bytes_per_unknown(iop, mode=1, fused=False):
     in the complex64-bulk form the second pass forms no dots (the next volume
     kernel does) and also writes the FP32 copy: 8 (iop + 2) + 20 B.  Both passes
     in one launch (fused): each vector once, read z and the window vectors, write
-    V_{j+1} = 8 (iop + 2) B, with the FP32 copy 8 (iop + 2) + 4 B."""
+    V_{j+1} = 8 (iop + 2) B; in the complex64-bulk form the launch also forms the
+    window dots and writes the FP32 copy: 8 (iop + 2) + 4 B."""
     if fused:
         return 8.0 * (iop + 2) + (4.0 if mode == 2 else 0.0)
     if mode == 2:

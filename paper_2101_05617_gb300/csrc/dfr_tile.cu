@@ -54,14 +54,17 @@ struct TileShape {
 constexpr size_t up16(size_t b) { return (b + 15) / 16 * 16; }
 
 // byte offsets of the regions of the dynamic shared memory: two stages of the
-// staged operands of one tile, then the scratch of the tile being computed
-template <int NS>
+// staged operands of one tile, then the scratch of the tile being computed.
+// DOTS: the stages hold the three FP64 window vectors of the orthogonalisation
+// dots; without them (the dots in a pass of their own) a stage is about two
+// thirds of the size and three CTAs fit on an SM.
+template <int NS, bool DOTS = true>
 struct TileLayout {
   static constexpr int TN = TileShape<NS>::TN, EPB = TileShape<NS>::EPB, NN = NS * NS;
   // one stage
   static constexpr size_t v = 0;                                            // double [3][TN]
   static constexpr size_t dots = v + up16(sizeof(double) * 3 * TN);         // double [3 (C, A, B)][3][TN]
-  static constexpr size_t ln = dots + up16(sizeof(double) * 9 * TN);        // float [LN_COUNT][TN]
+  static constexpr size_t ln = dots + (DOTS ? up16(sizeof(double) * 9 * TN) : 0);   // float [LN_COUNT][TN]
   static constexpr size_t b32 = ln + up16(sizeof(float) * LN_COUNT * TN);   // float [KMAXB][3][TN]
   static constexpr size_t fb = b32 + up16(sizeof(float) * KMAXB * 3 * TN);  // float [EPB][4][3][NS]
   static constexpr size_t stage = fb + up16(sizeof(float) * EPB * 12 * NS);
@@ -107,17 +110,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, unsigned parit
 }
 
 // issue the bulk copies of tile `tile` into stage buffer `st` (one thread)
-template <int NS, bool W3>
+template <int NS, bool W3, bool DOTS>
 __device__ __forceinline__ void issue_tile(const TanVolArgs<float>& a, long long tile, unsigned char* st,
                                            uint64_t* mbar) {
-  using L = TileLayout<NS>;
+  using L = TileLayout<NS, DOTS>;
   constexpr int NN = NS * NS, EPB = TileShape<NS>::EPB, TN = TileShape<NS>::TN;
   const AugEpilogue& ep = a.ep;
   const long long N = a.nodes, tile0 = tile * TN;
   const int tn = (N - tile0) < TN ? (int)(N - tile0) : TN;
   const int ne = tn / NN;
   const unsigned bd = (unsigned)(sizeof(double) * tn), bf = (unsigned)(sizeof(float) * tn);
-  const double* dsrc[3] = {W3 ? ep.dotC : nullptr, ep.dotA, ep.dotB};
+  const double* dsrc[3] = {(DOTS && W3) ? ep.dotC : nullptr, DOTS ? ep.dotA : nullptr, DOTS ? ep.dotB : nullptr};
   unsigned tx = 3 * (ep.v32 ? bf : bd) + LN_COUNT * bf + (unsigned)(sizeof(float) * ne * 12 * NS);
   for (int k = 0; k < 3; ++k)
     if (dsrc[k]) tx += 3 * bd;
@@ -154,10 +157,10 @@ __device__ __forceinline__ void issue_tile(const TanVolArgs<float>& a, long long
 // the copies of the next tile are in flight while the current one computes.
 // Each thread accumulates its window dots over all its tiles; one block
 // reduction per CTA then feeds the shared epilogue.
-template <int NS, bool W3>
+template <int NS, bool W3, bool DOTS>
 __device__ __forceinline__ void tile_body(const TanVolArgs<float>& a, const DfrConst& dc, int* err,
                                           unsigned char* sm) {
-  using L = TileLayout<NS>;
+  using L = TileLayout<NS, DOTS>;
   constexpr int NN = NS * NS, TN = TileShape<NS>::TN;
   float (*sF)[2][3][NN] = reinterpret_cast<float (*)[2][3][NN]>(sm + L::flux);
   float (*sD)[NS + 3] = reinterpret_cast<float (*)[NS + 3]>(sm + L::dmat);
@@ -168,7 +171,7 @@ __device__ __forceinline__ void tile_body(const TanVolArgs<float>& a, const DfrC
   const long long N = a.nodes;
   const long long ntiles = (N + TN - 1) / TN;
   const long long G = gridDim.x;
-  const bool dA = ep.dotA != nullptr, dB = ep.dotB != nullptr, dC = W3 && ep.dotC != nullptr;
+  const bool dA = DOTS && ep.dotA != nullptr, dB = DOTS && ep.dotB != nullptr, dC = DOTS && W3 && ep.dotC != nullptr;
   const bool f32v = ep.v32 != nullptr;
 
   if (threadIdx.x == 0) {
@@ -180,7 +183,7 @@ __device__ __forceinline__ void tile_body(const TanVolArgs<float>& a, const DfrC
   if (threadIdx.x == 0) {
     for (int s = 0; s < 2; ++s) {
       const long long tile = blockIdx.x + s * G;
-      if (tile < ntiles) issue_tile<NS, W3>(a, tile, sm + s * L::stage, mbar + s);
+      if (tile < ntiles) issue_tile<NS, W3, DOTS>(a, tile, sm + s * L::stage, mbar + s);
     }
   }
   const double dscale = -dc.two_over_dx * ep.scale;
@@ -195,7 +198,7 @@ __device__ __forceinline__ void tile_body(const TanVolArgs<float>& a, const DfrC
   const int t = threadIdx.x;
   const int le = t / NN, node = t % NN, k2 = node / NS, k1 = node % NS;
   double da = 0.0, db = 0.0, dcc = 0.0, dab = 0.0, dbc = 0.0;
-  const bool cd = ep.cdot_out != nullptr;
+  const bool cd = DOTS && ep.cdot_out != nullptr;
   bool ok = true;
   int k = 0;
   for (long long tile = blockIdx.x; tile < ntiles; tile += G, ++k) {
@@ -269,7 +272,7 @@ __device__ __forceinline__ void tile_body(const TanVolArgs<float>& a, const DfrC
           if (l < ep.p && ep.b32[l]) acc = fmaf(coef32[l], sb32[(l * 3 + mu) * TN + t], acc);
         const double o = f32_to_f64_bits(acc);
         a.out[idx + mu * N] = o;
-        if (dB) {
+        if (DOTS && dB) {
           const double vb = sdot[(2 * 3 + mu) * TN + t];
           db = fma(o, vb, db);
           if (dA) {
@@ -286,7 +289,7 @@ __device__ __forceinline__ void tile_body(const TanVolArgs<float>& a, const DfrC
       }
     }
     __syncthreads();   // stage s and the flux scratch are free again
-    if (threadIdx.x == 0 && tile + 2 * G < ntiles) issue_tile<NS, W3>(a, tile + 2 * G, st, mbar + s);
+    if (threadIdx.x == 0 && tile + 2 * G < ntiles) issue_tile<NS, W3, DOTS>(a, tile + 2 * G, st, mbar + s);
   }
   // a CTA that gave up contributes zeros; the reduction protocol still completes
   if (!ok) da = db = dcc = dab = dbc = 0.0;
@@ -297,21 +300,24 @@ __device__ __forceinline__ void tile_body(const TanVolArgs<float>& a, const DfrC
   epilogue_finish<TN, W3, true>(ep, da, db, dcc, blockIdx.x, gridDim.x, dab, dbc, reinterpret_cast<double*>(sm));
 }
 
-template <int NS, bool W3>
-__global__ void __launch_bounds__(TileShape<NS>::TN, 2) volume_tangent_tile_f32_kernel(TanVolArgs<float> a,
-                                                                                      DfrConst dc, int* err) {
+// CTAs of the persistent grid per SM: two with the window vectors staged, three without
+template <bool DOTS>
+constexpr int tile_ctas_per_sm() { return DOTS ? 2 : 3; }
+
+template <int NS, bool W3, bool DOTS>
+__global__ void __launch_bounds__(TileShape<NS>::TN, tile_ctas_per_sm<DOTS>()) volume_tangent_tile_f32_kernel(
+    TanVolArgs<float> a, DfrConst dc, int* err) {
   extern __shared__ __align__(16) unsigned char sm[];
   pdl_wait();
   pdl_trigger();
-  tile_body<NS, W3>(a, dc, err, sm);
+  tile_body<NS, W3, DOTS>(a, dc, err, sm);
 }
 
 // the same for the device-driven solver: the iteration index and the augmented
 // operator come from its device state
-template <int NS, bool W3>
-__global__ void __launch_bounds__(TileShape<NS>::TN, 2) volume_tangent_tile_dev_kernel(const KDev* __restrict__ kd,
-                                                                                     KFix f, TanVolArgs<float> a0,
-                                                                                     DfrConst dc, int* err) {
+template <int NS, bool W3, bool DOTS>
+__global__ void __launch_bounds__(TileShape<NS>::TN, tile_ctas_per_sm<DOTS>()) volume_tangent_tile_dev_kernel(
+    const KDev* __restrict__ kd, KFix f, TanVolArgs<float> a0, DfrConst dc, int* err) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ TanVolArgs<float> a;
   if (threadIdx.x == 0) {
@@ -322,27 +328,28 @@ __global__ void __launch_bounds__(TileShape<NS>::TN, 2) volume_tangent_tile_dev_
     iter_epilogue_dev(a.ep, *kd, f, it, W3, true);
   }
   __syncthreads();
-  tile_body<NS, W3>(a, dc, err, sm);
+  tile_body<NS, W3, DOTS>(a, dc, err, sm);
 }
 
-template <int NS, bool W3, bool DEV>
+template <int NS, bool W3, bool DEV, bool DOTS>
 int set_tile_smem() {
   static bool configured = false;
   if (configured) return SW_OK;
+  const int bytes = (int)TileLayout<NS, DOTS>::bytes;
   const cudaError_t e =
-      DEV ? cudaFuncSetAttribute(volume_tangent_tile_dev_kernel<NS, W3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)TileLayout<NS>::bytes)
-          : cudaFuncSetAttribute(volume_tangent_tile_f32_kernel<NS, W3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)TileLayout<NS>::bytes);
+      DEV ? cudaFuncSetAttribute(volume_tangent_tile_dev_kernel<NS, W3, DOTS>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+          : cudaFuncSetAttribute(volume_tangent_tile_f32_kernel<NS, W3, DOTS>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return SW_ECUDA;
   configured = true;
   return SW_OK;
 }
 
-int persistent_ctas(const Ctx& c, long long tiles) {
+int persistent_ctas(const Ctx& c, long long tiles, int per_sm) {
   static int sms = 0;
   if (!sms && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess) return -1;
-  return (int)std::min<long long>(tiles, 2LL * sms);   // two persistent CTAs per SM
+  return (int)std::min<long long>(tiles, (long long)per_sm * sms);
 }
 
 template <int NS>
@@ -359,14 +366,14 @@ bool tile_eligible(const Ctx& c, const double* v, const double* out, const AugEp
   return true;
 }
 
-template <int NS, bool W3>
+template <int NS, bool W3, bool DOTS>
 int launch_tile(Ctx& c, const double* v, double* out, const AugEpilogue& ep, cudaStream_t s) {
-  using L = TileLayout<NS>;
-  auto kernel = volume_tangent_tile_f32_kernel<NS, W3>;
-  if (int rc = set_tile_smem<NS, W3, false>()) return rc;
+  using L = TileLayout<NS, DOTS>;
+  auto kernel = volume_tangent_tile_f32_kernel<NS, W3, DOTS>;
+  if (int rc = set_tile_smem<NS, W3, false, DOTS>()) return rc;
   TanVolArgs<float> va{v, c.nodes, c.nelem, c.d_lin_node32, reinterpret_cast<const float*>(c.d_fb), out, ep};
   const long long tiles = (c.nodes + TileShape<NS>::TN - 1) / TileShape<NS>::TN;
-  const int ctas = persistent_ctas(c, tiles);
+  const int ctas = persistent_ctas(c, tiles, tile_ctas_per_sm<DOTS>());
   if (ctas < 0) return SW_ECUDA;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)ctas);
@@ -391,42 +398,39 @@ int launch_tile(Ctx& c, const double* v, double* out, const AugEpilogue& ep, cud
 template <int NS>
 int launch_volume_tile_f32(Ctx& c, const double* v, double* out, const AugEpilogue& ep, cudaStream_t s) {
   if (!tile_eligible<NS>(c, v, out, ep)) return 1;
-  return ep.dotC ? launch_tile<NS, true>(c, v, out, ep, s) : launch_tile<NS, false>(c, v, out, ep, s);
+  if (!ep.dotB) return launch_tile<NS, false, false>(c, v, out, ep, s);   // the dots in a pass of their own
+  return ep.dotC ? launch_tile<NS, true, true>(c, v, out, ep, s) : launch_tile<NS, false, true>(c, v, out, ep, s);
 }
 
+// the device-driven solver's form: the dots in a pass of their own, so the
+// staged kernel without window vectors
 template <int NS>
 int capture_volume_tile_dev(Ctx& c, KDev* kd, const KFix& f, bool w3, cudaStream_t s) {
+  (void)w3;
   // eligibility with the buffers every iteration uses (basis rows, their FP32
   // copies, the b-column copies)
   AugEpilogue ep;
   ep.p = 1;
-  ep.dotA = ep.dotB = f.V;
-  ep.dotC = w3 ? f.V : nullptr;
   ep.v32 = f.V32;
   if (!f.V32 || !tile_eligible<NS>(c, f.V, f.V, ep)) return 1;
   if (f.b32 && (reinterpret_cast<uintptr_t>(f.b32) & 15u)) return 1;
   if ((f.n * sizeof(float)) % 16 != 0) return 1;
-  using L = TileLayout<NS>;
-  const int rc = w3 ? set_tile_smem<NS, true, true>() : set_tile_smem<NS, false, true>();
-  if (rc) return rc;
+  using L = TileLayout<NS, false>;
+  if (int rc = set_tile_smem<NS, false, true, false>()) return rc;
   TanVolArgs<float> va{nullptr, c.nodes, c.nelem, c.d_lin_node32, reinterpret_cast<const float*>(c.d_fb), nullptr,
                        AugEpilogue{}};
   const long long tiles = (c.nodes + TileShape<NS>::TN - 1) / TileShape<NS>::TN;
-  const int ctas = persistent_ctas(c, tiles);
+  const int ctas = persistent_ctas(c, tiles, tile_ctas_per_sm<false>());
   if (ctas < 0) return SW_ECUDA;
   int* err = c.d_flags + 3;
-  if (w3)
-    volume_tangent_tile_dev_kernel<NS, true><<<ctas, TileShape<NS>::TN, L::bytes, s>>>(kd, f, va, c.dc, err);
-  else
-    volume_tangent_tile_dev_kernel<NS, false><<<ctas, TileShape<NS>::TN, L::bytes, s>>>(kd, f, va, c.dc, err);
+  volume_tangent_tile_dev_kernel<NS, false, false><<<ctas, TileShape<NS>::TN, L::bytes, s>>>(kd, f, va, c.dc, err);
   c.launches++;
   return cuda_status(cudaGetLastError());
 }
 
 template <int NS>
 int prepare_dev() {
-  if (int rc = set_tile_smem<NS, false, true>()) return rc;
-  return set_tile_smem<NS, true, true>();
+  return set_tile_smem<NS, false, true, false>();
 }
 
 int prepare_volume_tile_dev(const Ctx& c) {

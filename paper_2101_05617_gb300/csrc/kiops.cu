@@ -72,7 +72,7 @@ int ensure_krylov(Ctx& c, int m_max) {
   if (cudaMalloc(&c.d_H, sizeof(double) * c.ldh * c.ldh) != cudaSuccess) return SW_ENOMEM;
   if (cudaMalloc(&c.d_F, sizeof(double) * c.ldh * c.ldh) != cudaSuccess) return SW_ENOMEM;
   if (cudaMalloc(&c.d_expm_ws, sizeof(double) * 8 * 160 * 160) != cudaSuccess) return SW_ENOMEM;
-  if (!c.d_partials && cudaMalloc(&c.d_partials, sizeof(double) * 2 * RED_BLOCKS) != cudaSuccess) return SW_ENOMEM;
+  if (!c.d_partials && cudaMalloc(&c.d_partials, sizeof(double) * 5 * RED_BLOCKS) != cudaSuccess) return SW_ENOMEM;
   if (!c.d_vpart && cudaMalloc(&c.d_vpart, sizeof(double) * 5 * (c.nelem + 1)) != cudaSuccess) return SW_ENOMEM;
   free_ptr(c.d_cdot);
   if (cudaMalloc(&c.d_cdot, sizeof(double) * c.ldh) != cudaSuccess) return SW_ENOMEM;
@@ -217,9 +217,14 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
         double* hB = c.d_H + (long long)it * c.ldh + it;
         double* hA = (it >= 1) ? c.d_H + (long long)(it - 1) * c.ldh + it : nullptr;
         double* hC = (o.iop == 3 && it >= 2) ? c.d_H + (long long)(it - 2) * c.ldh + it : nullptr;
-        ep.dotA = (it >= 1) ? V + (it - 1) * ldv : nullptr;
-        ep.dotB = Vi;
-        ep.dotC = hC ? V + (it - 2) * ldv : nullptr;
+        // the window: V_{j-1}, V_j, V_{j-2}
+        const double* wA = (it >= 1) ? V + (it - 1) * ldv : nullptr;
+        const double* wC = hC ? V + (it - 2) * ldv : nullptr;
+        // complex64-bulk form: the FP32 volume kernel forms no dots; a pass of
+        // their own (orth_dots_dev) takes them and the V . V products
+        ep.dotA = use32 ? nullptr : wA;
+        ep.dotB = use32 ? nullptr : Vi;
+        ep.dotC = use32 ? nullptr : wC;
         ep.cprev = c.d_cdot + it;
         ep.cprevC = c.d_cdot2 + it;
         ep.cprevAC = (it >= 1) ? c.d_cdot + it - 1 : nullptr;
@@ -230,22 +235,32 @@ int kiops_run(Ctx& c, const double* q_lin, double dt, double tau_out, int nb, co
         ep.dticket = (unsigned int*)(c.d_flags + 9);
         ep.n = n;
         ep.v32 = use32 ? c.d_V32 + it * ldv : nullptr;
-        // complex64-bulk form: V_j . V_{j-1} (and V_j . V_{j-2}) from the window
-        // vectors the volume kernel reads anyway; the scale pass forms no dots
-        ep.cdot_out = (use32 && it >= 1) ? c.d_cdot + it : nullptr;
-        ep.cdot2_out = (use32 && o.iop == 3 && it >= 2) ? c.d_cdot2 + it : nullptr;
+        ep.cdot_out = ep.cdot2_out = nullptr;
         rc = use_lin ? launch_jvp_lin(c, Vi, Vn, ep, s, c.jvp_mode == 2) : launch_jvp(c, q_lin, Vi, kEpsJvp, Vn, ep, s);
         if (rc) return rc;
         double* hs = c.d_H + (long long)(it + 1) * c.ldh + it;
+        if (use32) {
+          double* cd = wA ? c.d_cdot + it : nullptr;
+          double* cd2 = wC ? c.d_cdot2 + it : nullptr;
+          const double* cpac = wC ? c.d_cdot + it - 1 : nullptr;
+          float* z32 = c.d_V32 + (it + 1) * ldv;
+          if (fused) {
+            rc = launch_orth3_fused(c, Vn, wA, Vi, wC, N, o.tol, it + 1, hC, hA, hB, hs, cd, cd2, cpac, z32, s);
+          } else if (!(rc = launch_orth_dots(c, Vn, Vi, wA, wC, N, hC, hA, hB, cd, cd2, cpac, s)) &&
+                     !(rc = launch_update_norm(c, Vn, wA, Vi, hA, hB, N, hs, o.tol, it + 1, s, wC, hC))) {
+            rc = launch_scale_dot(c, Vn, Vi, hs, N, nullptr, s, nullptr, nullptr, z32);
+          }
+          if (rc) return rc;
+          continue;
+        }
         // V_{j+1} . V_{j-1} is needed by the window of three two iterations later
         const double* Vprev = (o.iop == 3 && it >= 1) ? V + (it - 1) * ldv : nullptr;
-        double* cn = use32 ? nullptr : c.d_cdot + it + 1;
-        float* z32 = use32 ? c.d_V32 + (it + 1) * ldv : nullptr;
+        double* cn = c.d_cdot + it + 1;
         if (fused) {
-          rc = launch_orth_fused(c, Vn, ep.dotA, Vi, hA, hB, N, hs, o.tol, it + 1, ep.dotC, hC, cn, Vprev,
-                                 c.d_cdot2 + it + 1, z32, s);
-        } else if (!(rc = launch_update_norm(c, Vn, ep.dotA, Vi, hA, hB, N, hs, o.tol, it + 1, s, ep.dotC, hC))) {
-          rc = launch_scale_dot(c, Vn, Vi, hs, N, cn, s, Vprev, c.d_cdot2 + it + 1, z32);
+          rc = launch_orth_fused(c, Vn, wA, Vi, hA, hB, N, hs, o.tol, it + 1, wC, hC, cn, Vprev,
+                                 c.d_cdot2 + it + 1, nullptr, s);
+        } else if (!(rc = launch_update_norm(c, Vn, wA, Vi, hA, hB, N, hs, o.tol, it + 1, s, wC, hC))) {
+          rc = launch_scale_dot(c, Vn, Vi, hs, N, cn, s, Vprev, c.d_cdot2 + it + 1, nullptr);
         }
         if (rc) return rc;
         continue;

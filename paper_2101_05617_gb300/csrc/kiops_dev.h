@@ -63,9 +63,11 @@ __device__ __forceinline__ void iter_epilogue_dev(AugEpilogue& ep, const KDev& k
   ep.tail_in = Vi + f.n;
   ep.tail_out = Vn + f.n;
   ep.skip = f.flags;
-  ep.dotA = (it >= 1) ? Vi - f.ldv : nullptr;
-  ep.dotB = Vi;
-  ep.dotC = (w3 && it >= 2) ? Vi - 2 * f.ldv : nullptr;
+  // complex64-bulk form (FP32 basis copy): the dots in a pass of their own
+  const bool sep = fp32 && f.V32;
+  ep.dotA = (!sep && it >= 1) ? Vi - f.ldv : nullptr;
+  ep.dotB = sep ? nullptr : Vi;
+  ep.dotC = (!sep && w3 && it >= 2) ? Vi - 2 * f.ldv : nullptr;
   ep.cprev = f.cdot + it;
   ep.cprevC = f.cdot2 + it;
   ep.cprevAC = (it >= 1) ? f.cdot + it - 1 : nullptr;
@@ -75,9 +77,8 @@ __device__ __forceinline__ void iter_epilogue_dev(AugEpilogue& ep, const KDev& k
   ep.dpart = f.vpart;
   ep.dticket = reinterpret_cast<unsigned int*>(f.flags + 9);
   ep.n = f.n;
-  ep.v32 = (fp32 && f.V32) ? f.V32 + (long long)it * f.ldv : nullptr;
-  ep.cdot_out = (fp32 && f.V32 && it >= 1) ? f.cdot + it : nullptr;
-  ep.cdot2_out = (fp32 && f.V32 && w3 && it >= 2) ? f.cdot2 + it : nullptr;
+  ep.v32 = sep ? f.V32 + (long long)it * f.ldv : nullptr;
+  ep.cdot_out = ep.cdot2_out = nullptr;
 }
 #endif
 

@@ -130,6 +130,21 @@ __global__ void to_float_skip_kernel(const double* __restrict__ src, float* __re
     dst[i] = f64_to_f32_bits(src[i]);
 }
 
+// the complex64-bulk form's dot pass (orth_dots_dev), as the host driver runs it
+template <bool W3>
+__global__ void __launch_bounds__(kRedThreads) kg_dots_kernel(const KDev* __restrict__ kd, KFix f) {
+  const int it = kd->it;
+  const double* Vi = f.V + (long long)it * f.ldv;
+  const double* Vn = Vi + f.ldv;
+  const double* VA = (it >= 1) ? Vi - f.ldv : nullptr;
+  const double* VC = (W3 && it >= 2) ? Vi - 2 * f.ldv : nullptr;
+  double* hA = (it >= 1) ? f.H + (long long)(it - 1) * f.ldh + it : nullptr;
+  double* hB = f.H + (long long)it * f.ldh + it;
+  double* hC = (W3 && it >= 2) ? f.H + (long long)(it - 2) * f.ldh + it : nullptr;
+  orth_dots_dev(Vn, Vi, VA, VC, f.N, f.partials, reinterpret_cast<unsigned int*>(f.flags + 8), f.flags, hC, hA, hB,
+                VA ? f.cdot + it : nullptr, VC ? f.cdot2 + it : nullptr, VC ? f.cdot + it - 1 : nullptr);
+}
+
 template <bool W3>
 __global__ void __launch_bounds__(kRedThreads) kg_update_kernel(const KDev* __restrict__ kd, KFix f) {
   const int it = kd->it;
@@ -369,6 +384,12 @@ int build(Ctx& c, KGraph& G, int p, int iop, bool fp32, int mmax) {
   std::vector<cudaGraphNode_t> it;
   rc = capture_into(iter, it, G.cap, [&](cudaStream_t s) {
     if (int r = capture_iter_jvp(c, kd, f, fp32, w3, p, s)) return r;
+    if (fp32) {   // complex64-bulk form: the dots in a pass of their own
+      if (w3)
+        kg_dots_kernel<true><<<RED_BLOCKS, kRedThreads, 0, s>>>(kd, f);
+      else
+        kg_dots_kernel<false><<<RED_BLOCKS, kRedThreads, 0, s>>>(kd, f);
+    }
     if (w3) {
       kg_update_kernel<true><<<RED_BLOCKS, kRedThreads, 0, s>>>(kd, f);
       kg_scale_kernel<true><<<RED_BLOCKS, kRedThreads, 0, s>>>(kd, f);

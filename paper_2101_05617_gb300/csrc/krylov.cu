@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(RED_THREADS) scale_dot_kernel(double* __restri
 }
 
 // both passes in one cooperative launch (orth_fused_dev)
-__global__ void __launch_bounds__(RED_THREADS) orth_fused_kernel(
+__global__ void __launch_bounds__(RED_THREADS, 4) orth_fused_kernel(
     double* __restrict__ z, const double* __restrict__ VA, const double* __restrict__ VB, const double* h1p,
     const double* h2p, long long n, double* partials, unsigned int* ticket, double* hsub, double tol, int* happy,
     int happy_value, const double* __restrict__ VC, const double* h0p, double* c_out, const double* __restrict__ VA2,
@@ -175,6 +175,27 @@ __global__ void __launch_bounds__(RED_THREADS) orth_fused_kernel(
   pdl_trigger();
   orth_fused_dev(z, VA, VB, h1p, h2p, n, partials, ticket, hsub, tol, happy, happy_value, VC, h0p, c_out, VA2, c2_out,
                  z32, gen, err);
+}
+
+// the dot pass of the complex64-bulk form (orth_dots_dev)
+__global__ void __launch_bounds__(RED_THREADS) orth_dots_kernel(
+    const double* __restrict__ z, const double* __restrict__ VB, const double* __restrict__ VA,
+    const double* __restrict__ VC, long long n, double* partials, unsigned int* ticket, const int* happy,
+    double* h0_out, double* h1_out, double* h2_out, double* cdot_out, double* cdot2_out, const double* cprevAC) {
+  pdl_wait();
+  pdl_trigger();
+  orth_dots_dev(z, VB, VA, VC, n, partials, ticket, happy, h0_out, h1_out, h2_out, cdot_out, cdot2_out, cprevAC);
+}
+
+// the dot, update and scale passes in one cooperative launch (orth3_fused_dev)
+__global__ void __launch_bounds__(RED_THREADS, 4) orth3_fused_kernel(
+    double* __restrict__ z, const double* __restrict__ VA, const double* __restrict__ VB,
+    const double* __restrict__ VC, long long n, double* partials, unsigned int* ticket, double tol, int* happy,
+    int happy_value, double* h0p, double* h1p, double* h2p, double* hsub, double* cdot_out, double* cdot2_out,
+    const double* cprevAC, float* __restrict__ z32, unsigned int* gen, int* err) {
+  pdl_trigger();
+  orth3_fused_dev(z, VA, VB, VC, n, partials, ticket, tol, happy, happy_value, h0p, h1p, h2p, hsub, cdot_out,
+                  cdot2_out, cprevAC, z32, gen, err);
 }
 
 int blocks_for(long long n, int threads) {
@@ -307,15 +328,70 @@ int launch_scale_dot(Ctx& c, double* z, const double* VB, const double* hsub, lo
 
 int orth_fused_available(Ctx& c) {
   if (c.orth_fused == 0) {
-    int coop = 0, sms = 0, nb = 0;
+    // both cooperative kernels (two and three phases) hold the whole grid at once
+    int coop = 0, sms = 0, nb = 0, nb3 = 0;
     c.orth_fused = -1;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c.device) == cudaSuccess && coop &&
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device) == cudaSuccess &&
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, orth_fused_kernel, RED_THREADS, 0) == cudaSuccess &&
-        (long long)nb * sms >= RED_BLOCKS)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb3, orth3_fused_kernel, RED_THREADS, 0) == cudaSuccess &&
+        (long long)nb * sms >= RED_BLOCKS && (long long)nb3 * sms >= RED_BLOCKS)
       c.orth_fused = 1;
   }
   return c.orth_fused > 0;
+}
+
+int launch_orth_dots(Ctx& c, const double* z, const double* VB, const double* VA, const double* VC, long long N,
+                     double* h0_out, double* h1_out, double* h2_out, double* cdot_out, double* cdot2_out,
+                     const double* cprevAC, cudaStream_t s) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (prof_on(c, PK_ORTH)) {
+    e0 = prof_event(c);
+    e1 = prof_event(c);
+    cudaEventRecord(e0, s);
+  }
+  if (launch_pdl(orth_dots_kernel, dim3(RED_BLOCKS), dim3(RED_THREADS), s, z, VB, VA, VC, N, c.d_partials,
+                 reinterpret_cast<unsigned int*>(c.d_flags + 8), static_cast<const int*>(c.d_flags), h0_out, h1_out,
+                 h2_out, cdot_out, cdot2_out, cprevAC) != cudaSuccess)
+    return SW_ECUDA;
+  if (prof_on(c, PK_ORTH)) {
+    cudaEventRecord(e1, s);
+    prof_record(c, PK_ORTH, e0, e1);
+  }
+  c.launches++;
+  return cuda_status(cudaGetLastError());
+}
+
+int launch_orth3_fused(Ctx& c, double* z, const double* VA, const double* VB, const double* VC, long long N,
+                       double tol, int happy_value, double* h0p, double* h1p, double* h2p, double* hsub,
+                       double* cdot_out, double* cdot2_out, const double* cprevAC, float* z32, cudaStream_t s) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (prof_on(c, PK_ORTH)) {
+    e0 = prof_event(c);
+    e1 = prof_event(c);
+    cudaEventRecord(e0, s);
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(RED_BLOCKS);
+  cfg.blockDim = dim3(RED_THREADS);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, orth3_fused_kernel, z, VA, VB, VC, N, c.d_partials,
+                         reinterpret_cast<unsigned int*>(c.d_flags + 8), tol, c.d_flags, happy_value, h0p, h1p, h2p,
+                         hsub, cdot_out, cdot2_out, cprevAC, z32, reinterpret_cast<unsigned int*>(c.d_flags + 10),
+                         c.d_flags + 3) != cudaSuccess)
+    return SW_ECUDA;
+  if (prof_on(c, PK_ORTH)) {
+    cudaEventRecord(e1, s);
+    prof_record(c, PK_ORTH, e0, e1);
+    prof_record(c, PK_ORTH, e1, e1);   // counted as the two passes of the other forms
+  }
+  c.launches++;
+  return cuda_status(cudaGetLastError());
 }
 
 int launch_orth_fused(Ctx& c, double* z, const double* VA, const double* VB, const double* h1, const double* h2,

@@ -173,7 +173,8 @@ __device__ __forceinline__ int update_norm_dev(double* __restrict__ z, const dou
                                                double tol, int* happy, int happy_value, const double* __restrict__ VC,
                                                const double* h0p) {
   if (__ldcg(happy)) return 0;
-  const double h1 = VA ? *h1p : 0.0, h2 = *h2p, h0 = VC ? *h0p : 0.0;
+  // through L2: in a fused launch another CTA has just written them
+  const double h1 = VA ? __ldcg(h1p) : 0.0, h2 = __ldcg(h2p), h0 = VC ? __ldcg(h0p) : 0.0;
   const double acc = mgs_update_range(z, VA, VB, h1, h2, (long long)blockIdx.x * blockDim.x + threadIdx.x, n,
                                       (long long)gridDim.x * blockDim.x, VC, h0);
   double b = block_sum(acc);
@@ -296,6 +297,176 @@ __device__ __forceinline__ void orth_fused_dev(double* __restrict__ z, const dou
   __syncthreads();
   if (gave_up) return;
   scale_dot_dev(z, VB, hsub, n, partials, ticket, c_out, happy, VA2, c2_out, z32);
+}
+
+// The window dots of the incomplete orthogonalisation as a pass of their own
+// (the complex64-bulk form, whose FP32 volume kernel forms none), over the N
+// entries of the augmented vectors (the tails included): z . V_{j-1}, z . V_j,
+// z . V_{j-2}, V_j . V_{j-1}, V_j . V_{j-2} into s[0..4] for one thread's
+// indices.  HA, HC: V_{j-1}, V_{j-2} present.
+template <bool HA, bool HC>
+__device__ __forceinline__ void orth_dots_range_t(const double* __restrict__ z, const double* __restrict__ VB,
+                                                  const double* __restrict__ VA, const double* __restrict__ VC,
+                                                  long long i, long long i1, long long stride, double s[5]) {
+  double da = 0.0, db = 0.0, dc = 0.0, dab = 0.0, dbc = 0.0;
+  for (; i + 3 * stride < i1; i += 4 * stride) {
+    double zz[4], b[4], a[4], c[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      zz[k] = __ldcg(z + i + k * stride);
+      b[k] = VB[i + k * stride];
+      if (HA) a[k] = VA[i + k * stride];
+      if (HC) c[k] = VC[i + k * stride];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      db = fma(zz[k], b[k], db);
+      if (HA) {
+        da = fma(zz[k], a[k], da);
+        dab = fma(b[k], a[k], dab);
+      }
+      if (HC) {
+        dc = fma(zz[k], c[k], dc);
+        dbc = fma(b[k], c[k], dbc);
+      }
+    }
+  }
+  for (; i < i1; i += stride) {
+    const double zz = __ldcg(z + i), b = VB[i];
+    db = fma(zz, b, db);
+    if (HA) {
+      const double a = VA[i];
+      da = fma(zz, a, da);
+      dab = fma(b, a, dab);
+    }
+    if (HC) {
+      const double c = VC[i];
+      dc = fma(zz, c, dc);
+      dbc = fma(b, c, dbc);
+    }
+  }
+  s[0] = da;
+  s[1] = db;
+  s[2] = dc;
+  s[3] = dab;
+  s[4] = dbc;
+}
+
+// The dot pass over a whole grid: the five sums above; the CTA that finishes
+// last forms the modified Gram-Schmidt coefficients from them exactly as the
+// volume epilogue does (h0 = z . V_{j-2}; h1 = z . V_{j-1} - h0 V_{j-1} . V_{j-2};
+// h2 = z . V_j - h0 V_j . V_{j-2} - h1 V_j . V_{j-1}, with the window's vectors
+// present) and stores V_j . V_{j-1}, V_j . V_{j-2} for the next iterations.
+// partials: 5 per CTA.  Returns 0 when the basis had already broken down
+// (nothing done), 2 in the CTA that finished last, else 1.
+__device__ __forceinline__ int orth_dots_dev(const double* __restrict__ z, const double* __restrict__ VB,
+                                             const double* __restrict__ VA, const double* __restrict__ VC,
+                                             long long n, double* partials, unsigned int* ticket, const int* happy,
+                                             double* h0_out, double* h1_out, double* h2_out, double* cdot_out,
+                                             double* cdot2_out, const double* cprevAC) {
+  if (__ldcg(happy)) return 0;
+  double s[5];
+  const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+  if (VC) {
+    if (VA)
+      orth_dots_range_t<true, true>(z, VB, VA, VC, i0, n, stride, s);
+    else
+      orth_dots_range_t<false, true>(z, VB, VA, VC, i0, n, stride, s);
+  } else if (VA) {
+    orth_dots_range_t<true, false>(z, VB, VA, VC, i0, n, stride, s);
+  } else {
+    orth_dots_range_t<false, false>(z, VB, VA, VC, i0, n, stride, s);
+  }
+  double b[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) b[k] = block_sum(s[k]);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) partials[5 * blockIdx.x + k] = b[k];
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return 1;
+  __threadfence();
+  double u[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) u[k] += __ldcg(partials + 5 * i + k);
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) u[k] = block_sum(u[k]);
+  if (threadIdx.x == 0) {
+    const double a = u[0], bb = u[1], c3 = u[2];
+    if (VA) *cdot_out = u[3];    // V_j . V_{j-1}
+    if (VC) *cdot2_out = u[4];   // V_j . V_{j-2}
+    if (VC) {
+      const double h0 = c3;
+      const double h1 = a - h0 * __ldcg(cprevAC);
+      *h0_out = h0;
+      *h1_out = h1;
+      *h2_out = bb - h0 * u[4] - h1 * u[3];
+    } else if (VA) {
+      *h1_out = a;
+      *h2_out = bb - a * u[3];
+    } else {
+      *h2_out = bb;
+    }
+    *ticket = 0u;
+  }
+  return 2;
+}
+
+// One grid-wide step of a cooperative launch (all CTAs call it, every thread):
+// the CTA that finished a phase last (`last`) advances *gen; the others wait,
+// bounded, until *gen has reached `target`.  False when the wait gave up (the
+// CTA then leaves its remaining phases undone and *err is set).
+__device__ __forceinline__ bool grid_step(unsigned int* gen, unsigned int target, bool last, int* err) {
+  __shared__ int gave_up;
+  if (threadIdx.x == 0) {
+    gave_up = 0;
+    if (last) {
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      unsigned int polls = 0;
+      while ((int)(*reinterpret_cast<volatile unsigned int*>(gen) - target) < 0) {
+        if (++polls > kOrthWaitPolls) {
+          gave_up = 1;
+          atomicExch(err, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+      __threadfence();
+    }
+  }
+  __syncthreads();
+  return !gave_up;
+}
+
+// The dot pass, the update pass and the scale pass of the complex64-bulk form
+// in one cooperative launch (two grid-wide steps); the same arithmetic in the
+// same order as orth_dots_dev, update_norm_dev and scale_dot_dev on the same
+// grid.  The H entries and the norm pass between the phases through L2.
+__device__ __forceinline__ void orth3_fused_dev(double* __restrict__ z, const double* __restrict__ VA,
+                                                const double* __restrict__ VB, const double* __restrict__ VC,
+                                                long long n, double* partials, unsigned int* ticket, double tol,
+                                                int* happy, int happy_value, double* h0p, double* h1p, double* h2p,
+                                                double* hsub, double* cdot_out, double* cdot2_out,
+                                                const double* cprevAC, float* __restrict__ z32, unsigned int* gen,
+                                                int* err) {
+  __shared__ unsigned int g0;
+  // read before this CTA's first ticket (ordered by the fence ahead of it)
+  if (threadIdx.x == 0) g0 = *reinterpret_cast<volatile unsigned int*>(gen);
+  int st = orth_dots_dev(z, VB, VA, VC, n, partials, ticket, happy, h0p, h1p, h2p, cdot_out, cdot2_out, cprevAC);
+  if (st == 0) return;   // uniform over the grid
+  if (!grid_step(gen, g0 + 1u, st == 2, err)) return;
+  st = update_norm_dev(z, VA, VB, h1p, h2p, n, partials, ticket, hsub, tol, happy, happy_value, VC, h0p);
+  if (st == 0) return;
+  if (!grid_step(gen, g0 + 2u, st == 2, err)) return;
+  scale_dot_dev(z, VB, hsub, n, partials, ticket, nullptr, happy, nullptr, nullptr, z32);
 }
 
 // ------------------------------------------------------------ expm

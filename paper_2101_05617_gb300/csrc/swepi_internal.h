@@ -305,6 +305,18 @@ int launch_to_float(Ctx& c, const double* src, float* dst, long long n, cudaStre
 // c_out, VA2, c2_out, z32) in one cooperative launch, where the GPU holds its
 // whole grid at once (orth_fused_available); a wait past its bound sets d_flags[3]
 int orth_fused_available(Ctx& c);
+// the complex64-bulk form's window dots as a pass of their own (its FP32
+// volume kernel forms none): the five sums over the augmented vectors, the
+// modified Gram-Schmidt coefficients into the H entries, V_j . V_{j-1} and
+// V_j . V_{j-2} into cdot_out, cdot2_out (orth_dots_dev)
+int launch_orth_dots(Ctx& c, const double* z, const double* VB, const double* VA, const double* VC, long long N,
+                     double* h0_out, double* h1_out, double* h2_out, double* cdot_out, double* cdot2_out,
+                     const double* cprevAC, cudaStream_t s);
+// that pass, the update pass and the scale pass (no dots, the FP32 copy z32)
+// in one cooperative launch, where orth_fused_available
+int launch_orth3_fused(Ctx& c, double* z, const double* VA, const double* VB, const double* VC, long long N,
+                       double tol, int happy_value, double* h0p, double* h1p, double* h2p, double* hsub,
+                       double* cdot_out, double* cdot2_out, const double* cprevAC, float* z32, cudaStream_t s);
 int launch_orth_fused(Ctx& c, double* z, const double* VA, const double* VB, const double* h1, const double* h2,
                       long long N, double* hsub, double tol, int happy_value, const double* VC, const double* h0,
                       double* c_out, const double* VA2, double* c2_out, float* z32, cudaStream_t s);
