@@ -68,9 +68,12 @@ struct TileLayout {
   static constexpr size_t b32 = ln + up16(sizeof(float) * LN_COUNT * TN);   // float [KMAXB][3][TN]
   static constexpr size_t fb = b32 + up16(sizeof(float) * KMAXB * 3 * TN);  // float [EPB][4][3][NS]
   static constexpr size_t stage = fb + up16(sizeof(float) * EPB * 12 * NS);
-  // scratch and barriers after the two stages
-  static constexpr size_t flux = 2 * stage;                                 // float [EPB][2][3][NN]
-  static constexpr size_t dmat = flux + up16(sizeof(float) * EPB * 6 * NN); // float [NS][NS + 3]
+  // scratch and barriers after the two stages: the flux scratch twice (tile k
+  // uses buffer k mod 2, so the next tile's fluxes can be written while slow
+  // warps still read this tile's)
+  static constexpr size_t flux = 2 * stage;                                 // float [2][EPB][2][3][NN]
+  static constexpr size_t flux_bytes = up16(sizeof(float) * EPB * 6 * NN);
+  static constexpr size_t dmat = flux + 2 * flux_bytes;                     // float [NS][NS + 3]
   static constexpr size_t mbar = dmat + up16(sizeof(float) * NS * (NS + 3)); // two mbarriers
   static constexpr size_t bytes = mbar + 16;
 };
@@ -153,8 +156,10 @@ __device__ __forceinline__ void issue_tile(const TanVolArgs<float>& a, long long
 }
 
 // Persistent: CTA b takes tiles b, b + G, b + 2G, ... (G CTAs); stage s = k mod
-// 2 of its k-th tile is refilled with tile k + 2 as soon as tile k is done, so
-// the copies of the next tile are in flight while the current one computes.
+// 2 holds its k-th tile, and once every thread is past tile k - 1 (the first
+// barrier of tile k) that tile's stage takes tile k + 1's copies, so the copies
+// of the next tile are in flight while the current one computes.  Two barriers
+// per tile: after the stage has landed, after the fluxes are written.
 // Each thread accumulates its window dots over all its tiles; one block
 // reduction per CTA then feeds the shared epilogue.
 template <int NS, bool W3, bool DOTS>
@@ -162,7 +167,6 @@ __device__ __forceinline__ void tile_body(const TanVolArgs<float>& a, const DfrC
                                           unsigned char* sm) {
   using L = TileLayout<NS, DOTS>;
   constexpr int NN = NS * NS, TN = TileShape<NS>::TN;
-  float (*sF)[2][3][NN] = reinterpret_cast<float (*)[2][3][NN]>(sm + L::flux);
   float (*sD)[NS + 3] = reinterpret_cast<float (*)[NS + 3]>(sm + L::dmat);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + L::mbar);
 
@@ -217,8 +221,13 @@ __device__ __forceinline__ void tile_body(const TanVolArgs<float>& a, const DfrC
       atomicExch(err, 1);
       mbar_wait_bounded(mbar + s, (unsigned)((k >> 1) & 1));   // do not leave with copies still landing
     }
-    ok = __syncthreads_and(got) != 0;   // also orders the coefficient tables written above
+    // also orders the coefficient tables written above, and every thread is
+    // done with tile k - 1: its stage takes tile k + 1's copies now
+    ok = __syncthreads_and(got) != 0;
     if (!ok) break;
+    if (threadIdx.x == 0 && k >= 1 && tile + G < ntiles)
+      issue_tile<NS, W3, DOTS>(a, tile + G, sm + (s ^ 1) * L::stage, mbar + (s ^ 1));
+    float (*sF)[2][3][NN] = reinterpret_cast<float (*)[2][3][NN]>(sm + L::flux + s * L::flux_bytes);
     const bool active = t < tn;
     float S1 = 0.f, S2 = 0.f;
     if (active) {
@@ -288,9 +297,8 @@ __device__ __forceinline__ void tile_body(const TanVolArgs<float>& a, const DfrC
         }
       }
     }
-    __syncthreads();   // stage s and the flux scratch are free again
-    if (threadIdx.x == 0 && tile + 2 * G < ntiles) issue_tile<NS, W3, DOTS>(a, tile + 2 * G, st, mbar + s);
   }
+  __syncthreads();   // every thread is done with the last tile's stage
   // a CTA that gave up contributes zeros; the reduction protocol still completes
   if (!ok) da = db = dcc = dab = dbc = 0.0;
   // the stage buffers are free after the last tile (every copy issued was
