@@ -43,6 +43,35 @@ __device__ __forceinline__ double block_sum(double v) {
   return r;
 }
 
+// K block sums at once (K <= the block's warps): every thread stores its K
+// values, warp k sums value k exactly as block_sum does (a stride of 32, then a
+// shuffle tree; the same result bit for bit), so the sums run side by side on
+// the SM's warp schedulers instead of one after another in warp 0.  Results
+// valid in thread 0.
+template <int K, int THREADS = kPassThreads>
+__device__ __forceinline__ void block_sums_k(double v[K]) {
+  static_assert(K >= 1 && K <= THREADS / 32, "one warp per value");
+  __shared__ double sb[K * THREADS];
+  __shared__ double res[K];
+  __syncthreads();   // an earlier call's readers are done with sb
+#pragma unroll
+  for (int k = 0; k < K; ++k) sb[k * THREADS + threadIdx.x] = v[k];
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w < K) {
+    double r = sb[w * THREADS + lane];
+#pragma unroll
+    for (int i = lane + 32; i < THREADS; i += 32) r += sb[w * THREADS + i];
+    r = warp_sum(r);
+    if (lane == 0) res[w] = r;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = res[k];
+  }
+}
+
 // ------------------------------------------------------------ orthogonalisation passes
 // The two vector passes of the window-2 modified Gram-Schmidt step over the
 // indices i0, i0 + stride, ... < i1 of one thread, four elements in flight
@@ -377,13 +406,11 @@ __device__ __forceinline__ int orth_dots_dev(const double* __restrict__ z, const
   } else {
     orth_dots_range_t<false, false>(z, VB, VA, VC, i0, n, stride, s);
   }
-  double b[5];
-#pragma unroll
-  for (int k = 0; k < 5; ++k) b[k] = block_sum(s[k]);
+  block_sums_k<5>(s);
   __shared__ bool last;
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < 5; ++k) partials[5 * blockIdx.x + k] = b[k];
+    for (int k = 0; k < 5; ++k) partials[5 * blockIdx.x + k] = s[k];
     __threadfence();
     last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
   }
@@ -395,8 +422,7 @@ __device__ __forceinline__ int orth_dots_dev(const double* __restrict__ z, const
 #pragma unroll
     for (int k = 0; k < 5; ++k) u[k] += __ldcg(partials + 5 * i + k);
   }
-#pragma unroll
-  for (int k = 0; k < 5; ++k) u[k] = block_sum(u[k]);
+  block_sums_k<5>(u);
   if (threadIdx.x == 0) {
     const double a = u[0], bb = u[1], c3 = u[2];
     if (VA) *cdot_out = u[3];    // V_j . V_{j-1}
