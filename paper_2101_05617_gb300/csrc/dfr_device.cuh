@@ -223,25 +223,31 @@ __device__ __forceinline__ void volume_epilogue(const AugEpilogue& ep, bool acti
 }
 
 // Sums of K values over the block in a fixed order, through shared scratch of
-// K * THREADS doubles: every thread stores its values, warp 0 sums them with a
-// stride of 32 and a shuffle tree; the result is valid in thread 0.  (On this
-// GPU a shuffle tree in every warp would cost each thread 5 K FP64 adds, more
-// than the dots themselves.)
+// K * THREADS doubles: every thread stores its values, warp k sums value k with
+// a stride of 32 and a shuffle tree; the results are valid in thread 0.  (On
+// this GPU a shuffle tree in every warp would cost each thread 5 K FP64 adds,
+// more than the dots themselves.)
 template <int THREADS, int K>
 __device__ __forceinline__ void block_sums(double v[K], double* sbuf) {
-  static_assert(THREADS >= 32, "block smaller than a warp");
+  static_assert(THREADS >= 32 * K, "one warp per value");
+  __shared__ double res[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) sbuf[k * THREADS + threadIdx.x] = v[k];
   __syncthreads();
-  if (threadIdx.x < 32) {
+  // warp k sums value k (a stride of 32, then a shuffle tree): the K sums run
+  // side by side on the SM's schedulers, each in the order one warp gave it
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w < K) {
+    double a = 0.0;
+    for (int i = lane; i < THREADS; i += 32) a += sbuf[w * THREADS + i];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      double a = 0.0;
-      for (int i = threadIdx.x; i < THREADS; i += 32) a += sbuf[k * THREADS + i];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if (lane == 0) res[w] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-      v[k] = a;
-    }
+    for (int k = 0; k < K; ++k) v[k] = res[k];
   }
 }
 
