@@ -74,7 +74,7 @@ __device__ __forceinline__ void block_sums_k(double v[K]) {
 
 // ------------------------------------------------------------ orthogonalisation passes
 // The two vector passes of the window-2 modified Gram-Schmidt step over the
-// indices i0, i0 + stride, ... < i1 of one thread, four elements in flight
+// indices i0, i0 + stride, ... < i1 of one thread, eight elements in flight
 // (z was written by another kernel or CTA: read through L2).
 //   z -= h0 VC + h1 VA + h2 VB (VC, VA may be null; oldest first); returns the
 //   thread's sum of z_i^2
@@ -86,17 +86,17 @@ __device__ __forceinline__ double mgs_update_range_t(double* __restrict__ z, con
                                                      long long i1, long long stride, const double* __restrict__ VC,
                                                      double h0) {
   double acc = 0.0;
-  for (; i + 3 * stride < i1; i += 4 * stride) {
-    double v[4], b[4], a[4], c[4];
+  for (; i + 7 * stride < i1; i += 8 * stride) {
+    double v[8], b[8], a[8], c[8];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 8; ++k) {
       v[k] = __ldcg(z + i + k * stride);
       b[k] = VB[i + k * stride];
       if (HA) a[k] = VA[i + k * stride];
       if (HC) c[k] = VC[i + k * stride];
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 8; ++k) {
       if (HC) v[k] = fma(-h0, c[k], v[k]);
       if (HA) v[k] = fma(-h1, a[k], v[k]);
       v[k] = fma(-h2, b[k], v[k]);
