@@ -37,6 +37,8 @@
 #ifndef SWEPI_H
 #define SWEPI_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -253,6 +255,35 @@ int sw_epi_set_history(sw_ctx_t ctx, int i, const double* q_dev, const double* F
  * warm start, so that the next sw_epi_step starts again with the EPI2 start-up
  * of Sec. 4 (the paragraph after Eq. 38). */
 int sw_epi_reset(sw_ctx_t ctx);
+
+/* Checkpoint and resume of the multistep state.  Besides q itself, the next
+ * sw_epi_step reads the history pairs (q_{n-i}, F(q_{n-i})) of Eq. 33-38 (Sec.
+ * 4: the previous steps' states and right-hand sides that the remainders
+ * R(q_{n-i}) need), the KIOPS warm start (the previous phi-function call's
+ * final Krylov size) and the previous call's features of the learned Krylov
+ * controller.  A context restored from a checkpoint and given the saved q, the
+ * same options, JVP mode and controller continues bit for bit as the saved one
+ * would have.
+ *
+ * sw_epi_checkpoint_size: *bytes = the size of the checkpoint of the current
+ * state (a header of 144 bytes plus 2 n doubles per history entry; n = 3 nodes).
+ * Host only.
+ *
+ * sw_epi_checkpoint_save: writes it to buf_host (caller-owned host memory,
+ * pageable or pinned, at least that many bytes): the header (format tag, grid,
+ * rotation and constants, counts, warm start, controller features, an FNV-1a
+ * checksum of the payload), then the entries from the most recent back, each
+ * q then F, FP64 in the canonical layout.  Copies on `stream` and waits for it.
+ *
+ * sw_epi_checkpoint_load: replaces the context's multistep state by the one in
+ * buf_host (`bytes` must be its exact size).  SW_EINVAL, before any CUDA call,
+ * for a buffer that is not a checkpoint of this grid (format tag, n_e, p,
+ * rotation, constants, size) or whose checksum fails.  After a CUDA failure
+ * the context holds no history, as after sw_epi_reset.  Copies on `stream` and
+ * waits for it. */
+int sw_epi_checkpoint_size(sw_ctx_t ctx, size_t* bytes);
+int sw_epi_checkpoint_save(sw_ctx_t ctx, void* buf_host, size_t bytes, void* stream);
+int sw_epi_checkpoint_load(sw_ctx_t ctx, const void* buf_host, size_t bytes, void* stream);
 
 /* The EPI coefficient matrix of order 3..6 as sw_epi_step uses it (Eq. 30,
  * 36-38; alpha_{m,i} of Eq. 35): *M rows (phi_1 .. phi_M) by *P columns

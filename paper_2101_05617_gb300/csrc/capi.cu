@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <stdexcept>
@@ -428,6 +429,123 @@ int sw_epi_set_history(sw_ctx_t c, int i, const double* q, const double* F, void
     return rc;
   }
   if (c->hist_count < i) c->hist_count = i;
+  return SW_OK;
+}
+
+// ---- checkpoint of the multistep state (the history pairs of Eq. 33-38, the
+// KIOPS warm start, the learned controller's previous-call features)
+namespace {
+constexpr char kCkMagic[8] = {'S', 'W', 'E', 'P', 'I', 'C', 'K', '1'};
+
+struct CkHeader {
+  char magic[8];
+  int32_t version, ne, p, count;
+  int64_t n;
+  double geom[6];          // radius, gravity, omega, lambda0, phi0, alpha0
+  int32_t m_warm, pad;
+  float prev_call[8];
+  float prev_h[4];
+  uint64_t checksum;       // FNV-1a 64 over the payload that follows the header
+};
+static_assert(sizeof(CkHeader) == 144, "the header size the C ABI states; payload doubles stay aligned");
+
+uint64_t fnv1a(const unsigned char* p, size_t len, uint64_t h) {
+  for (size_t i = 0; i < len; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+constexpr uint64_t kFnvBasis = 14695981039346656037ull;
+
+size_t ck_bytes(const Ctx& c, int count) { return sizeof(CkHeader) + sizeof(double) * 2 * (size_t)c.n * count; }
+
+void ck_geom(const Ctx& c, double g[6]) {
+  g[0] = c.prm.radius;
+  g[1] = c.prm.gravity;
+  g[2] = c.prm.omega;
+  g[3] = c.prm.lambda0;
+  g[4] = c.prm.phi0;
+  g[5] = c.prm.alpha0;
+}
+}  // namespace
+
+int sw_epi_checkpoint_size(sw_ctx_t c, size_t* bytes) {
+  if (!c || !bytes) return SW_EINVAL;
+  *bytes = ck_bytes(*c, c->hist_count);
+  return SW_OK;
+}
+
+int sw_epi_checkpoint_save(sw_ctx_t c, void* buf, size_t bytes, void* stream) {
+  if (!c || !buf) return SW_EINVAL;
+  if (bytes < ck_bytes(*c, c->hist_count)) return SW_EINVAL;
+  if (int rc = check_device(*c)) return rc;
+  cudaStream_t s = as_stream(stream);
+  CkHeader hd{};
+  std::memcpy(hd.magic, kCkMagic, sizeof(kCkMagic));
+  hd.version = 1;
+  hd.ne = c->ne;
+  hd.p = c->ns - 1;
+  hd.count = c->hist_count;
+  hd.n = c->n;
+  ck_geom(*c, hd.geom);
+  hd.m_warm = c->m_warm;
+  std::memcpy(hd.prev_call, c->prev_call, sizeof(hd.prev_call));
+  std::memcpy(hd.prev_h, c->prev_h, sizeof(hd.prev_h));
+  unsigned char* out = static_cast<unsigned char*>(buf);
+  double* pay = reinterpret_cast<double*>(out + sizeof(CkHeader));
+  const size_t vb = sizeof(double) * c->n;
+  // entry i (1 = most recent): q_{n-i} then F(q_{n-i})
+  for (int i = 1; i <= c->hist_count; ++i) {
+    const int slot = hist_slot(*c, i);
+    if (cudaMemcpyAsync(pay + (size_t)(2 * (i - 1)) * c->n, c->d_hq[slot], vb, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(pay + (size_t)(2 * (i - 1) + 1) * c->n, c->d_hF[slot], vb, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess)
+      return SW_ECUDA;
+  }
+  if (int rc = cuda_status(cudaStreamSynchronize(s))) return rc;
+  hd.checksum = fnv1a(reinterpret_cast<const unsigned char*>(pay), 2 * vb * c->hist_count, kFnvBasis);
+  std::memcpy(out, &hd, sizeof(hd));
+  return SW_OK;
+}
+
+int sw_epi_checkpoint_load(sw_ctx_t c, const void* buf, size_t bytes, void* stream) {
+  if (!c || !buf || bytes < sizeof(CkHeader)) return SW_EINVAL;
+  CkHeader hd;
+  std::memcpy(&hd, buf, sizeof(hd));
+  double g[6];
+  ck_geom(*c, g);
+  if (std::memcmp(hd.magic, kCkMagic, sizeof(kCkMagic)) != 0 || hd.version != 1 || hd.ne != c->ne ||
+      hd.p != c->ns - 1 || hd.n != c->n || hd.count < 0 || hd.count > MAX_HIST ||
+      std::memcmp(hd.geom, g, sizeof(g)) != 0 || bytes != ck_bytes(*c, hd.count))
+    return SW_EINVAL;
+  const unsigned char* in = static_cast<const unsigned char*>(buf);
+  const double* pay = reinterpret_cast<const double*>(in + sizeof(CkHeader));
+  const size_t vb = sizeof(double) * c->n;
+  if (fnv1a(reinterpret_cast<const unsigned char*>(pay), 2 * vb * hd.count, kFnvBasis) != hd.checksum)
+    return SW_EINVAL;
+  if (int rc = check_device(*c)) return rc;
+  if (int rc = ensure_epi(*c)) return rc;
+  cudaStream_t s = as_stream(stream);
+  // until every copy has landed the context holds no history: a failure here
+  // leaves it as after sw_epi_reset
+  c->hist_count = 0;
+  c->hist_head = 0;
+  c->m_warm = 0;
+  for (int i = 1; i <= hd.count; ++i) {
+    const int slot = hist_slot(*c, i);
+    if (cudaMemcpyAsync(c->d_hq[slot], pay + (size_t)(2 * (i - 1)) * c->n, vb, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(c->d_hF[slot], pay + (size_t)(2 * (i - 1) + 1) * c->n, vb, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+      return SW_ECUDA;
+  }
+  if (int rc = cuda_status(cudaStreamSynchronize(s))) return rc;
+  c->hist_count = hd.count;
+  c->m_warm = hd.m_warm;
+  std::memcpy(c->prev_call, hd.prev_call, sizeof(hd.prev_call));
+  std::memcpy(c->prev_h, hd.prev_h, sizeof(hd.prev_h));
   return SW_OK;
 }
 

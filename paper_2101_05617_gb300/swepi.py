@@ -116,6 +116,9 @@ def lib():
     ipp = ctypes.POINTER(ctypes.c_int)
     L.sw_interface_transform.argtypes = [ip, ctypes.c_double, ipp, ipp, ipp, ipp, ipp, dp]
     L.sw_epi_reset.argtypes = [vp]
+    L.sw_epi_checkpoint_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.sw_epi_checkpoint_save.argtypes = [vp, vp, ctypes.c_size_t, vp]
+    L.sw_epi_checkpoint_load.argtypes = [vp, vp, ctypes.c_size_t, vp]
     L.sw_kernel_launches.argtypes = [vp]
     L.sw_kernel_launches.restype = ll
     L.sw_profile.argtypes = [vp, ip]
@@ -157,7 +160,8 @@ def lib():
 EXPORTED = ["sw_init", "sw_free", "sw_num_unknowns", "sw_grid_info", "sw_node_xyz", "sw_state_from_fields",
             "sw_set_bottom", "sw_set_bottom_host", "sw_rhs", "sw_jvp", "sw_jvp_static_scratch", "sw_linearize", "sw_jvp_linearized",
             "sw_set_jvp_mode", "sw_set_kiops_driver", "sw_set_orth_fused", "sw_kiops_phi", "sw_epi_step", "sw_epi_step_host", "sw_epi_set_history",
-            "sw_epi_reset", "sw_epi_coefficients", "sw_dfr_operators", "sw_node_coefficients",
+            "sw_epi_reset", "sw_epi_checkpoint_size", "sw_epi_checkpoint_save", "sw_epi_checkpoint_load",
+            "sw_epi_coefficients", "sw_dfr_operators", "sw_node_coefficients",
             "sw_interface_transform", "sw_kernel_launches", "sw_profile", "sw_profile_kinds", "sw_profile_read", "sw_fp64_fma_peak",
             "sw_status_str", "sw_mlp_create", "sw_mlp_free", "sw_mlp_set_params", "sw_mlp_get_params",
             "sw_mlp_forward", "sw_mlp_gradient", "sw_mlp_train", "sw_set_controller", "sw_kiops_log",
@@ -381,6 +385,27 @@ def sw_epi_set_history(ctx, i, q, F=None, stream=None):
 
 def sw_epi_reset(ctx):
     _check("sw_epi_reset", lib().sw_epi_reset(ctx))
+
+
+def sw_epi_checkpoint_size(ctx):
+    nb = ctypes.c_size_t(0)
+    _check("sw_epi_checkpoint_size", lib().sw_epi_checkpoint_size(ctx, ctypes.byref(nb)))
+    return int(nb.value)
+
+
+def sw_epi_checkpoint_save(ctx, stream=None):
+    """The multistep state as a host byte array (sw_epi_checkpoint_save)."""
+    buf = np.zeros(sw_epi_checkpoint_size(ctx), dtype=np.uint8)
+    _check("sw_epi_checkpoint_save", lib().sw_epi_checkpoint_save(ctx, ctypes.c_void_p(buf.ctypes.data), buf.size,
+                                                                  _stream(stream)))
+    return buf
+
+
+def sw_epi_checkpoint_load(ctx, buf, stream=None):
+    buf = np.ascontiguousarray(np.frombuffer(bytes(buf), dtype=np.uint8) if not isinstance(buf, np.ndarray) else buf,
+                               dtype=np.uint8).reshape(-1)
+    _check("sw_epi_checkpoint_load", lib().sw_epi_checkpoint_load(ctx, ctypes.c_void_p(buf.ctypes.data), buf.size,
+                                                                  _stream(stream)))
 
 
 def sw_kernel_launches(ctx):
@@ -704,6 +729,13 @@ class SWContext:
 
     def epi_reset(self):
         sw_epi_reset(self.handle)
+
+    def epi_checkpoint(self, stream=None):
+        """Host copy (uint8 array) of the multistep state: history pairs, KIOPS warm start, controller features."""
+        return sw_epi_checkpoint_save(self.handle, stream)
+
+    def epi_restore(self, buf, stream=None):
+        sw_epi_checkpoint_load(self.handle, buf, stream)
 
     def kernel_launches(self):
         return sw_kernel_launches(self.handle)

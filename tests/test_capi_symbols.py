@@ -68,6 +68,10 @@ def test_argument_checks_without_gpu():
     assert L.sw_epi_step_host(None, 4, 900.0, x, ctypes.byref(o), ctypes.byref(st), None) == EINVAL
     assert L.sw_epi_set_history(None, 1, x, x, None) == EINVAL
     assert L.sw_epi_reset(None) == EINVAL
+    nb = ctypes.c_size_t(0)
+    assert L.sw_epi_checkpoint_size(None, ctypes.byref(nb)) == EINVAL
+    assert L.sw_epi_checkpoint_save(None, x, 1 << 20, None) == EINVAL
+    assert L.sw_epi_checkpoint_load(None, x, 1 << 20, None) == EINVAL
     assert L.sw_set_jvp_mode(None, 1) == EINVAL and L.sw_set_kiops_driver(None, 1) == EINVAL
     assert L.sw_set_orth_fused(None, 1, None) == EINVAL
     assert L.sw_set_bottom(None, x) == EINVAL and L.sw_set_bottom_host(None, x) == EINVAL
