@@ -53,6 +53,10 @@ def flops_per_jvp(ne, ns, p=4, dots=True):
 # while the kernel has changed since its last capture.
 TRAFFIC_BYTES = {"ne60_p5": 187.29e6}   # 174.60 MB read + 12.69 MB written
 
+# the timed region brackets every PROFILE_EVERY-th launch of the dominant kernel
+# with CUDA events (its average launch duration for the roofline)
+PROFILE_EVERY = 16
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -777,8 +781,11 @@ def main():
         pg.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    # the dominant kernel alone is bracketed by events in the timed region (one
-    # pair per Krylov iteration); the other families are timed in a separate step
+    # the dominant kernel alone is bracketed by events in the timed region, one
+    # launch in PROFILE_EVERY (an event pair between kernels keeps the next from
+    # overlapping the previous one's tail); the other families are timed in a
+    # separate step
+    ctx.profile_every(PROFILE_EVERY)
     ctx.profile_kinds("volume_jvp")
     launches0 = ctx.kernel_launches()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -862,6 +869,7 @@ def main():
                               if args.jvp_mode == 1 else f"{dominant} kernel<cs,{ns}> (full complex-step JVP)",
                     "peak_source": "FP64 FMA throughput measured live by sw_fp64_fma_peak (nominal 1.25)",
                     "per_kernel": {"volume": {"flops": fv, "avg_ms": t_vol * 1e3, "launches": vj["count"],
+                                              "bracketed_every": PROFILE_EVERY,
                                               "tflops": fv / t_vol / 1e12 if t_vol else None},
                                    "face": {"flops": ff, "avg_ms": t_face * 1e3, "launches": fj["count"],
                                             "tflops": ff / t_face / 1e12 if t_face else None},

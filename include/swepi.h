@@ -446,6 +446,12 @@ typedef struct {
 int sw_profile(sw_ctx_t ctx, int enable);
 /* time only the kinds whose bit (1 << kind) is set in mask (0 = off); resets the counts */
 int sw_profile_kinds(sw_ctx_t ctx, unsigned mask);
+/* bracket only every `every`-th launch (every >= 1; 1 = all, the default) of
+ * each timed JVP or RHS kernel family (kinds 0-3), so that a timed run is
+ * perturbed less: an event pair between two kernels keeps the second from
+ * starting under the first's tail (programmatic dependent launch).  Counts
+ * then report the bracketed launches.  Resets the counts. */
+int sw_profile_every(sw_ctx_t ctx, int every);
 int sw_profile_read(sw_ctx_t ctx, sw_profile_stats* out);
 
 /* Measured FP64 fused-multiply-add throughput of the current device in

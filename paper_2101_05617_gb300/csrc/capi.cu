@@ -198,6 +198,18 @@ int sw_profile_kinds(sw_ctx_t c, unsigned mask) {
   return SW_OK;
 }
 
+int sw_profile_every(sw_ctx_t c, int every) {
+  if (!c || every < 1) return SW_EINVAL;
+  prof_drain(*c);
+  c->prof_every = every;
+  for (int k = 0; k < SW_PROF_KINDS; ++k) {
+    c->prof_seen[k] = 0;
+    c->prof_count[k] = 0;
+    c->prof_ms[k] = 0.0;
+  }
+  return SW_OK;
+}
+
 int sw_profile_read(sw_ctx_t c, sw_profile_stats* out) {
   if (!c || !out) return SW_EINVAL;
   prof_drain(*c);

@@ -185,7 +185,7 @@ static int launch_ns(Ctx& c, const double* q, const double* v, double eps, doubl
   long long fblocks = (c.nfacepts + fthreads - 1) / fthreads;
   const bool jvp = v != nullptr;
   const int kf = jvp ? PK_FACE_JVP : PK_FACE_RHS, kv = jvp ? PK_VOL_JVP : PK_VOL_RHS;
-  const bool pf = prof_on(c, kf), pv = prof_on(c, kv);
+  const bool pf = prof_take(c, kf), pv = prof_take(c, kv);
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
   if (pf) {
     e0 = prof_event(c);

@@ -211,7 +211,7 @@ int linearize_ns(Ctx& c, const double* q, cudaStream_t s) {
 template <typename T, int NS>
 int tangent_ns(Ctx& c, const double* v, double* out, const AugEpilogue& ep, const T* ln, const T* lf, T* fb,
                cudaStream_t s) {
-  const bool pf = prof_on(c, PK_FACE_JVP), pv = prof_on(c, PK_VOL_JVP);
+  const bool pf = prof_take(c, PK_FACE_JVP), pv = prof_take(c, PK_VOL_JVP);
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
   if (pf) {
     e0 = prof_event(c);

@@ -162,6 +162,8 @@ struct Ctx {
   struct ProfRec { int kind; cudaEvent_t a, b; };
   std::vector<ProfRec> prof_pending;
   std::vector<cudaEvent_t> prof_pool;
+  int prof_every = 1;               // bracket every prof_every-th launch of a JVP/RHS family (sw_profile_every)
+  long long prof_seen[SW_PROF_KINDS] = {};
   long long prof_count[SW_PROF_KINDS] = {};
   double prof_ms[SW_PROF_KINDS] = {};
 };
@@ -186,6 +188,14 @@ enum ProfKind {
   PK_FACE_JVP = 0, PK_VOL_JVP = 1, PK_FACE_RHS = 2, PK_VOL_RHS = 3, PK_EXPM = 4, PK_LIN = 5, PK_ORTH = 6
 };
 inline bool prof_on(const Ctx& c, int kind) { return (c.prof >> kind) & 1u; }
+// whether this launch of a JVP or RHS kernel family is bracketed: every
+// prof_every-th launch of the family while it is timed (an event pair between
+// two kernels keeps the second from overlapping the first's tail, so a timed
+// run that brackets fewer launches is closer to an untimed one)
+inline bool prof_take(Ctx& c, int kind) {
+  if (!prof_on(c, kind)) return false;
+  return (c.prof_seen[kind]++ % c.prof_every) == 0;
+}
 
 // ---- multistep EPI driver pieces (capi.cu), shared with the ensemble driver
 constexpr int EPI_STARTUP_SUBSTEPS = 8;   // EPI2 substeps of a start-up step (Sec. 4)

@@ -123,6 +123,7 @@ def lib():
     L.sw_kernel_launches.restype = ll
     L.sw_profile.argtypes = [vp, ip]
     L.sw_profile_kinds.argtypes = [vp, ctypes.c_uint]
+    L.sw_profile_every.argtypes = [vp, ip]
     L.sw_profile_read.argtypes = [vp, ctypes.POINTER(sw_profile_stats)]
     L.sw_fp64_fma_peak.argtypes = [dp]
     fp = ctypes.POINTER(ctypes.c_float)
@@ -162,7 +163,7 @@ EXPORTED = ["sw_init", "sw_free", "sw_num_unknowns", "sw_grid_info", "sw_node_xy
             "sw_set_jvp_mode", "sw_set_kiops_driver", "sw_set_orth_fused", "sw_kiops_phi", "sw_epi_step", "sw_epi_step_host", "sw_epi_set_history",
             "sw_epi_reset", "sw_epi_checkpoint_size", "sw_epi_checkpoint_save", "sw_epi_checkpoint_load",
             "sw_epi_coefficients", "sw_dfr_operators", "sw_node_coefficients",
-            "sw_interface_transform", "sw_kernel_launches", "sw_profile", "sw_profile_kinds", "sw_profile_read", "sw_fp64_fma_peak",
+            "sw_interface_transform", "sw_kernel_launches", "sw_profile", "sw_profile_kinds", "sw_profile_every", "sw_profile_read", "sw_fp64_fma_peak",
             "sw_status_str", "sw_mlp_create", "sw_mlp_free", "sw_mlp_set_params", "sw_mlp_get_params",
             "sw_mlp_forward", "sw_mlp_gradient", "sw_mlp_train", "sw_set_controller", "sw_kiops_log",
             "sw_kiops_log_clear", "sw_diagnostics", "sw_error_norms", "sw_ens_create", "sw_ens_free",
@@ -418,6 +419,10 @@ def sw_profile(ctx, enable=True):
 
 def sw_profile_kinds(ctx, mask):
     _check("sw_profile_kinds", lib().sw_profile_kinds(ctx, int(mask)))
+
+
+def sw_profile_every(ctx, every):
+    _check("sw_profile_every", lib().sw_profile_every(ctx, int(every)))
 
 
 def sw_profile_read(ctx):
@@ -737,6 +742,10 @@ class SWContext:
     def epi_restore(self, buf, stream=None):
         sw_epi_checkpoint_load(self.handle, buf, stream)
 
+    def diagnostics(self, q, zeta=None, stream=None):
+        """(mass, energy, potential enstrophy, max |zeta|) of q (sw_diagnostics)."""
+        return sw_diagnostics(self.handle, q, zeta, stream)
+
     def kernel_launches(self):
         return sw_kernel_launches(self.handle)
 
@@ -749,6 +758,10 @@ class SWContext:
         for k in kinds:
             mask |= 1 << sw_profile_stats.KINDS.index(k)
         sw_profile_kinds(self.handle, mask)
+
+    def profile_every(self, every):
+        """Bracket only every `every`-th launch of each timed JVP/RHS kernel family."""
+        sw_profile_every(self.handle, every)
 
     def profile_read(self):
         return sw_profile_read(self.handle)

@@ -80,6 +80,7 @@ def test_argument_checks_without_gpu():
     assert L.sw_diagnostics(None, x, x, None, None) == EINVAL
     assert L.sw_error_norms(None, x, x, x, None) == EINVAL
     assert L.sw_profile(None, 1) == EINVAL and L.sw_profile_kinds(None, 1) == EINVAL
+    assert L.sw_profile_every(None, 4) == EINVAL
     assert L.sw_fp64_fma_peak(None) == EINVAL
     assert L.sw_set_controller(None, None) == EINVAL
     assert L.sw_kiops_log(None, None, 0) == EINVAL

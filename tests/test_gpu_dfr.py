@@ -246,3 +246,32 @@ def test_set_bottom_device_equals_host():
         host = np.ascontiguousarray(hB.reshape(-1))
         rc = swepi.lib().sw_set_bottom(a.handle, host.ctypes.data_as(swepi.ctypes.c_void_p))
         swepi._check("sw_set_bottom", rc)
+
+
+def test_profile_brackets_every_nth_launch():
+    """sw_profile_every(ctx, k): of the timed JVP kernel family only every k-th
+    launch is bracketed by events (the counts say how many); the results of the
+    JVPs are those of an unprofiled run bit for bit."""
+    _, g, q, _ = oracle_case(4, 4, seed=0)
+    ctx, ref_ctx = _ctx(g), _ctx(g)
+    qd = torch.tensor(q.reshape(-1), device="cuda")
+    vd = torch.tensor(scaled_direction(q, 3).reshape(-1), device="cuda")
+    ctx.linearize(qd)
+    ref_ctx.linearize(qd)
+    ctx.profile_every(4)
+    ctx.profile_kinds("volume_jvp")
+    for _ in range(10):
+        out = ctx.jvp_linearized(vd)
+    st = ctx.profile_read()
+    assert st["volume_jvp"]["count"] == 3 and st["volume_jvp"]["ms"] > 0     # launches 1, 5 and 9
+    assert st["face_jvp"]["count"] == 0
+    assert torch.equal(out, ref_ctx.jvp_linearized(vd))
+    ctx.profile_every(1)
+    ctx.profile_kinds("volume_jvp", "face_jvp")
+    for _ in range(5):
+        ctx.jvp_linearized(vd)
+    st = ctx.profile_read()
+    assert st["volume_jvp"]["count"] == 5 and st["face_jvp"]["count"] == 5
+    from paper_2101_05617_gb300.swepi import SWError
+    with pytest.raises(SWError):
+        ctx.profile_every(0)
