@@ -454,6 +454,26 @@ int sw_profile_kinds(sw_ctx_t ctx, unsigned mask);
 int sw_profile_every(sw_ctx_t ctx, int every);
 int sw_profile_read(sw_ctx_t ctx, sw_profile_stats* out);
 
+/* Bounds-checked builds (a debugging aid with no paper counterpart; the
+ * library built with -DSW_CHECK, libswepi_check.so).  There the kernels that
+ * index through the grid tables or issue bulk copies from computed ranges test
+ * those indices first: an interface line's element and edge numbers (every
+ * face kernel), a staged tile's copy ranges and alignment (the complex64-bulk
+ * volume kernel), a batched task's member, range and basis index (the
+ * ensemble kernel).  A failed test records a code (1 interface line, 2 tile
+ * copy, 3 ensemble task) and the access it guards is skipped, so the kernel
+ * neither traps nor reads or writes out of range; the results of that launch
+ * are then not valid.  Returns the first code recorded since the last call (0
+ * none) and clears the record, or SW_ECUDA when it cannot be read; *checked
+ * (may be NULL) = 1 in a checked build, else 0.  In the default build the
+ * tests compile to nothing, it returns 0 and makes no CUDA call. */
+int sw_check_status(int* checked);
+/* Checked builds only (SW_EINVAL otherwise): what = 1 moves the first
+ * interface line's owner element one grid past the last element in the
+ * context's device table, so that the next face kernel's check fires (the
+ * test of the checks); what = 0 moves it back. */
+int sw_check_inject(sw_ctx_t ctx, int what);
+
 /* Measured FP64 fused-multiply-add throughput of the current device in
  * TFLOP/s (2 flops per FMA), from a register-resident FMA-chain kernel: the
  * ALU roofline of the FP64 path (the paper has no counterpart). */

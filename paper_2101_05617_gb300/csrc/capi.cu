@@ -10,6 +10,7 @@
 #include <stdexcept>
 #include <vector>
 
+#include "check.cuh"
 #include "swepi_internal.h"
 
 using namespace swepi;
@@ -218,6 +219,28 @@ int sw_profile_read(sw_ctx_t c, sw_profile_stats* out) {
     out->ms[k] = c->prof_ms[k];
   }
   return SW_OK;
+}
+
+int sw_check_status(int* checked) {
+  if (checked) *checked = kChecked ? 1 : 0;
+  const unsigned w[4] = {check_word_dfr(), check_word_split(), check_word_tile(), check_word_ensemble()};
+  int first = 0;
+  for (unsigned v : w) {
+    if (v == ~0u) return SW_ECUDA;
+    if (!first && v) first = (int)v;
+  }
+  return first;
+}
+
+int sw_check_inject(sw_ctx_t c, int what) {
+  if (!c || !kChecked || what < 0 || what > 1) return SW_EINVAL;
+  if (int rc = check_device(*c)) return rc;
+  FaceLine L;
+  if (cudaMemcpy(&L, c->d_lines, sizeof(L), cudaMemcpyDeviceToHost) != cudaSuccess) return SW_ECUDA;
+  // 1: the first interface line's owner moved past the last element; 0: moved back
+  if (what == 1 && L.owner < c->nelem) L.owner += (int)c->nelem;
+  if (what == 0 && L.owner >= c->nelem) L.owner -= (int)c->nelem;
+  return cudaMemcpy(c->d_lines, &L, sizeof(L), cudaMemcpyHostToDevice) == cudaSuccess ? SW_OK : SW_ECUDA;
 }
 
 int sw_fp64_fma_peak(double* tflops) {
@@ -530,7 +553,7 @@ int sw_epi_checkpoint_load(sw_ctx_t c, const void* buf, size_t bytes, void* stre
   ck_geom(*c, g);
   if (std::memcmp(hd.magic, kCkMagic, sizeof(kCkMagic)) != 0 || hd.version != 1 || hd.ne != c->ne ||
       hd.p != c->ns - 1 || hd.n != c->n || hd.count < 0 || hd.count > MAX_HIST ||
-      std::memcmp(hd.geom, g, sizeof(g)) != 0 || bytes != ck_bytes(*c, hd.count))
+      std::memcmp(hd.geom, g, sizeof(g)) != 0 || bytes != ck_bytes(*c, hd.count) || hd.m_warm < 0)
     return SW_EINVAL;
   const unsigned char* in = static_cast<const unsigned char*>(buf);
   const double* pay = reinterpret_cast<const double*>(in + sizeof(CkHeader));

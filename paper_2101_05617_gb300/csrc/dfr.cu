@@ -26,6 +26,7 @@
 // (AUSM's |M| <= 1, max/min) test the real part, ties going to the <= 0 side.
 #include <cuda_runtime.h>
 
+#include "check.cuh"
 #include "dfr_device.cuh"
 #include "swepi_internal.h"
 
@@ -51,6 +52,7 @@ __global__ void __launch_bounds__(128) face_flux_kernel(FaceArgs a, DfrConst dc)
   if (t >= a.nfacepts) return;
   const int line = (int)(t / NS), i = (int)(t % NS);
   const FaceLine L = a.lines[line];
+  if (!face_line_ok<NS>(L, a.nodes)) return;
   const int in = L.reversed ? NS - 1 - i : i;
   T qo[3], qn[3];
   trace<T, NS>(a.q, a.v, a.eps, a.nodes, L.owner, L.owner_edge, i, dc, qo);
@@ -267,5 +269,8 @@ int launch_jvp(Ctx& c, const double* q, const double* v, double eps, double* out
                cudaStream_t s) {
   return launch_any<cs>(c, q, v, eps, out, ep, s);
 }
+
+// this translation unit's check word (bounds-checked builds; sw_check_status)
+SW_CHECK_READER(check_word_dfr)
 
 }  // namespace swepi

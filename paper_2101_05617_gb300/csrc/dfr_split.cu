@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(128) lin_face_kernel(LinFaceArgs a, DfrConst d
   if (t >= a.nfacepts) return;
   const int line = (int)(t / NS), i = (int)(t % NS);
   const FaceLine L = a.lines[line];
+  if (!face_line_ok<NS>(L, a.nodes)) return;
   const int in = L.reversed ? NS - 1 - i : i;
   double qo[3], qn[3];
   trace<double, NS>(a.q, nullptr, 0.0, a.nodes, L.owner, L.owner_edge, i, dc, qo);
@@ -394,5 +395,8 @@ int launch_jvp_lin(Ctx& c, const double* v, double* out, const AugEpilogue& ep, 
     default: return SW_EINVAL;
   }
 }
+
+// this translation unit's check word (bounds-checked builds; sw_check_status)
+SW_CHECK_READER(check_word_split)
 
 }  // namespace swepi

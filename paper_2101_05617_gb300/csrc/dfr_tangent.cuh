@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include "check.cuh"
 #include "convert.cuh"
 #include "dfr_device.cuh"
 #include "swepi_internal.h"
@@ -59,6 +60,7 @@ __device__ __forceinline__ void face_tangent_body(const TanFaceArgs<T>& a, const
   if (t >= a.nfacepts) return;
   const int line = (int)(t / NS), i = (int)(t % NS);
   const FaceLine L = a.lines[line];
+  if (!face_line_ok<NS>(L, a.nodes)) return;
   const int in = L.reversed ? NS - 1 - i : i;
   T vo[3], vn[3];
   trace_tan<T, NS>(a.v, a.v32, a.nodes, L.owner, L.owner_edge, i, dc, vo);

@@ -112,6 +112,29 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, unsigned parit
   return false;
 }
 
+// checked build: every copy of a tile (tile0 .. tile0 + tn of the N solution
+// points, whole elements) lies inside its arrays, starts on a 16-byte boundary
+// and moves a multiple of 16 bytes
+template <int NS, bool W3, bool DOTS>
+__device__ __forceinline__ bool tile_copies_ok(const TanVolArgs<float>& a, long long tile0, int tn,
+                                               const double* const dsrc[3]) {
+  constexpr int NN = NS * NS;
+  const long long N = a.nodes;
+  if (tile0 < 0 || tn <= 0 || tn % NN != 0 || tile0 + tn > N || N != a.nelem * NN) return false;
+  const AugEpilogue& ep = a.ep;
+  auto al = [](const void* p) { return (reinterpret_cast<unsigned long long>(p) & 15ull) == 0ull; };
+  const bool b16 = (sizeof(double) * tn) % 16 == 0 && (sizeof(float) * tn) % 16 == 0;
+  bool ok = b16 && al(a.ln + tile0) && al(a.ln + N) && al(a.fb + tile0 / NN * 12 * NS) &&
+            (sizeof(float) * (tn / NN) * 12 * NS) % 16 == 0;
+  if (ep.v32) ok = ok && al(ep.v32 + tile0) && al(ep.v32 + N);
+  else ok = ok && al(a.v + tile0) && al(a.v + N);
+  for (int k = 0; k < 3; ++k)
+    if (dsrc[k]) ok = ok && al(dsrc[k] + tile0) && al(dsrc[k] + N);
+  for (int l = 0; l < ep.p && l < KMAXB; ++l)
+    if (ep.b32[l]) ok = ok && al(ep.b32[l] + tile0) && al(ep.b32[l] + N);
+  return ok;
+}
+
 // issue the bulk copies of tile `tile` into stage buffer `st` (one thread)
 template <int NS, bool W3, bool DOTS>
 __device__ __forceinline__ void issue_tile(const TanVolArgs<float>& a, long long tile, unsigned char* st,
@@ -129,6 +152,13 @@ __device__ __forceinline__ void issue_tile(const TanVolArgs<float>& a, long long
     if (dsrc[k]) tx += 3 * bd;
   for (int l = 0; l < ep.p && l < KMAXB; ++l)
     if (ep.b32[l]) tx += 3 * bf;
+  if (kChecked && !tile_copies_ok<NS, W3, DOTS>(a, tile0, tn, dsrc)) {
+    // checked build: no copy from a range outside the arrays; the phase
+    // completes without data and the tile's results are not valid
+    check_fail(CHK_TILE_RANGE);
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mbar)) : "memory");
+    return;
+  }
   // the stage was last read through the generic proxy: order that before the copies
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(tx) : "memory");
@@ -472,5 +502,8 @@ template int launch_volume_tile_f32<5>(Ctx&, const double*, double*, const AugEp
 template int launch_volume_tile_f32<6>(Ctx&, const double*, double*, const AugEpilogue&, cudaStream_t);
 template int launch_volume_tile_f32<7>(Ctx&, const double*, double*, const AugEpilogue&, cudaStream_t);
 template int launch_volume_tile_f32<8>(Ctx&, const double*, double*, const AugEpilogue&, cudaStream_t);
+
+// this translation unit's check word (bounds-checked builds; sw_check_status)
+SW_CHECK_READER(check_word_tile)
 
 }  // namespace swepi

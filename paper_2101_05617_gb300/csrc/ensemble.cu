@@ -102,7 +102,8 @@ struct EnsEntry {
 struct EnsList {
   unsigned int base[5];   // first task of each phase; base[4] = all tasks
   int count;
-  int pad[2];
+  int members;            // members of the ensemble (entries of the descriptor array)
+  int pad;
   EnsEntry e[ENS_MAX + 1];
 };
 
@@ -353,6 +354,21 @@ struct VolBytes {
   static constexpr size_t value = (a > b ? (a > c ? a : c) : (b > c ? b : c));
 };
 
+// checked build: the task a CTA decoded names a listed member of the
+// ensemble, lies inside that member's tasks of its phase, and the member's
+// basis index leaves room for V_{j+1}
+__device__ __forceinline__ bool ens_task_ok(const EnsList& L, int lo, int ph, unsigned int rel,
+                                            const EnsDesc* desc, const EnsDyn* dyn) {
+  if (lo < 0 || lo >= L.count || ph < 0 || ph > 3) return false;
+  const int m = L.e[lo].member;
+  if (m < 0 || m >= L.members || rel < L.e[lo].off[ph]) return false;
+  const EnsDesc& d = desc[m];
+  const unsigned int local = rel - L.e[lo].off[ph];
+  const unsigned int n = ph == 0 ? d.n_face : (ph == 1 ? d.n_vol : d.n_vec);
+  const int j = dyn[m].j;
+  return local < n && j >= 0 && j + 1 <= d.ldh - 2;
+}
+
 // one Krylov iteration of every listed member (persistent, graph-captured);
 // 64 registers per thread at most (1024 threads per SM), as the single-grid
 // volume kernel
@@ -377,6 +393,15 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) ens_iter_kernel(const Ens
       const int mid = (lo + hi + 1) >> 1;
       if (list->e[mid].off[ph] <= rel) lo = mid;
       else hi = mid - 1;
+    }
+    if (kChecked) {   // checked build: thread 0 decides for the CTA; a bad task is skipped
+      __shared__ int s_ok;
+      if (threadIdx.x == 0) {
+        s_ok = ens_task_ok(*list, lo, ph, rel, desc, dyn);
+        if (!s_ok) check_fail(CHK_ENS_TASK);
+      }
+      __syncthreads();
+      if (!s_ok) continue;
     }
     const int m = list->e[lo].member;
     const unsigned int local = rel - list->e[lo].off[ph];
@@ -646,6 +671,7 @@ int launch_iteration(Ens& e, const std::vector<int>& ids, cudaStream_t s) {
   if (ids != e.last_ids || e.list_dirty || e.last_block != e.block) {
     EnsList& L = e.hlist;
     L.count = (int)ids.size();
+    L.members = e.count;
     unsigned int tot[4] = {0, 0, 0, 0};
     for (int k = 0; k < L.count; ++k) {
       const EnsDesc& d = e.hdesc[ids[k]];
@@ -1503,3 +1529,8 @@ int sw_ens_stats_read(sw_ens_t e, sw_ens_stats* out) {
 }
 
 }  // extern "C"
+
+namespace swepi {
+// this translation unit's check word (bounds-checked builds; sw_check_status)
+SW_CHECK_READER(check_word_ensemble)
+}  // namespace swepi

@@ -15,7 +15,10 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libswepi.so")
+# SWEPI_CHECKED=1 loads the bounds-checked build instead (libswepi_check.so, from
+# build.build(checked=True); see sw_check_status)
+CHECKED = os.environ.get("SWEPI_CHECKED") == "1"
+LIB_PATH = os.path.join(_HERE, "libswepi_check.so" if CHECKED else "libswepi.so")
 
 SW_OK = 0
 STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA error",
@@ -82,7 +85,8 @@ def lib():
     if _lib is not None:
         return _lib
     if not os.path.exists(LIB_PATH):
-        raise ImportError(f"libswepi.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        how = "paper_2101_05617_gb300.build.build(checked=True)" if CHECKED else "__graft_entry__.build()"
+        raise ImportError(f"{os.path.basename(LIB_PATH)} not built ({LIB_PATH}); run {how}")
     L = ctypes.CDLL(LIB_PATH)
     vp, dp, ip, ll = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_longlong
     L.sw_init.argtypes = [ip, ip, ctypes.POINTER(sw_params), ctypes.POINTER(vp)]
@@ -124,6 +128,8 @@ def lib():
     L.sw_profile.argtypes = [vp, ip]
     L.sw_profile_kinds.argtypes = [vp, ctypes.c_uint]
     L.sw_profile_every.argtypes = [vp, ip]
+    L.sw_check_status.argtypes = [ctypes.POINTER(ctypes.c_int)]
+    L.sw_check_inject.argtypes = [vp, ip]
     L.sw_profile_read.argtypes = [vp, ctypes.POINTER(sw_profile_stats)]
     L.sw_fp64_fma_peak.argtypes = [dp]
     fp = ctypes.POINTER(ctypes.c_float)
@@ -163,7 +169,7 @@ EXPORTED = ["sw_init", "sw_free", "sw_num_unknowns", "sw_grid_info", "sw_node_xy
             "sw_set_jvp_mode", "sw_set_kiops_driver", "sw_set_orth_fused", "sw_kiops_phi", "sw_epi_step", "sw_epi_step_host", "sw_epi_set_history",
             "sw_epi_reset", "sw_epi_checkpoint_size", "sw_epi_checkpoint_save", "sw_epi_checkpoint_load",
             "sw_epi_coefficients", "sw_dfr_operators", "sw_node_coefficients",
-            "sw_interface_transform", "sw_kernel_launches", "sw_profile", "sw_profile_kinds", "sw_profile_every", "sw_profile_read", "sw_fp64_fma_peak",
+            "sw_interface_transform", "sw_kernel_launches", "sw_profile", "sw_profile_kinds", "sw_profile_every", "sw_profile_read", "sw_check_status", "sw_check_inject", "sw_fp64_fma_peak",
             "sw_status_str", "sw_mlp_create", "sw_mlp_free", "sw_mlp_set_params", "sw_mlp_get_params",
             "sw_mlp_forward", "sw_mlp_gradient", "sw_mlp_train", "sw_set_controller", "sw_kiops_log",
             "sw_kiops_log_clear", "sw_diagnostics", "sw_error_norms", "sw_ens_create", "sw_ens_free",
@@ -423,6 +429,19 @@ def sw_profile_kinds(ctx, mask):
 
 def sw_profile_every(ctx, every):
     _check("sw_profile_every", lib().sw_profile_every(ctx, int(every)))
+
+
+def sw_check_status():
+    """(first check code since the last call, 0 = none; whether the library is the checked build)."""
+    checked = ctypes.c_int(0)
+    rc = lib().sw_check_status(ctypes.byref(checked))
+    if rc < 0:
+        raise SWError("sw_check_status", rc)
+    return rc, bool(checked.value)
+
+
+def sw_check_inject(ctx, what):
+    _check("sw_check_inject", lib().sw_check_inject(ctx, int(what)))
 
 
 def sw_profile_read(ctx):

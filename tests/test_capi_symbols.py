@@ -81,6 +81,9 @@ def test_argument_checks_without_gpu():
     assert L.sw_error_norms(None, x, x, x, None) == EINVAL
     assert L.sw_profile(None, 1) == EINVAL and L.sw_profile_kinds(None, 1) == EINVAL
     assert L.sw_profile_every(None, 4) == EINVAL
+    assert L.sw_check_inject(None, 1) == EINVAL
+    checked = ctypes.c_int(-1)
+    assert L.sw_check_status(ctypes.byref(checked)) == 0 and checked.value == 0   # default build: no checks
     assert L.sw_fp64_fma_peak(None) == EINVAL
     assert L.sw_set_controller(None, None) == EINVAL
     assert L.sw_kiops_log(None, None, 0) == EINVAL
