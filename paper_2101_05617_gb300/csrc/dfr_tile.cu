@@ -385,8 +385,8 @@ int set_tile_smem() {
 }
 
 int persistent_ctas(const Ctx& c, long long tiles, int per_sm) {
-  static int sms = 0;
-  if (!sms && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess) return -1;
+  int sms = 0;   // per call: a process may hold contexts on GPUs of different sizes
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess || sms < 1) return -1;
   return (int)std::min<long long>(tiles, (long long)per_sm * sms);
 }
 
