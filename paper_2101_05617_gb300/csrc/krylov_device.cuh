@@ -75,6 +75,8 @@ __device__ __forceinline__ void block_sums_k(double v[K]) {
 // ------------------------------------------------------------ orthogonalisation passes
 // The two vector passes of the window-2 modified Gram-Schmidt step over the
 // indices i0, i0 + stride, ... < i1 of one thread, eight elements in flight
+// with two window vectors, four with three (the 64-register budget of the
+// cooperative grid); the order of the operations is the same either way
 // (z was written by another kernel or CTA: read through L2).
 //   z -= h0 VC + h1 VA + h2 VB (VC, VA may be null; oldest first); returns the
 //   thread's sum of z_i^2
@@ -85,18 +87,19 @@ __device__ __forceinline__ double mgs_update_range_t(double* __restrict__ z, con
                                                      const double* __restrict__ VB, double h1, double h2, long long i,
                                                      long long i1, long long stride, const double* __restrict__ VC,
                                                      double h0) {
+  constexpr int D = HC ? 4 : 8;   // entries in flight per thread
   double acc = 0.0;
-  for (; i + 7 * stride < i1; i += 8 * stride) {
-    double v[8], b[8], a[8], c[8];
+  for (; i + (D - 1) * stride < i1; i += D * stride) {
+    double v[D], b[D], a[D], c[D];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < D; ++k) {
       v[k] = __ldcg(z + i + k * stride);
       b[k] = VB[i + k * stride];
       if (HA) a[k] = VA[i + k * stride];
       if (HC) c[k] = VC[i + k * stride];
     }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < D; ++k) {
       if (HC) v[k] = fma(-h0, c[k], v[k]);
       if (HA) v[k] = fma(-h1, a[k], v[k]);
       v[k] = fma(-h2, b[k], v[k]);
